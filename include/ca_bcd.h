@@ -1,0 +1,156 @@
+/*
+ * ca_bcd.h -- C ABI of the GB300 (sm_103a) CA-BCD / CA-BDCD library.
+ *
+ * The library solves the ridge-regression problem of Sec. 2.2 of
+ * Devarakonda, Fountoulakis, Demmel and Mahoney, "Avoiding communication in
+ * primal and dual block coordinate descent methods" (arXiv 1612.04003):
+ *
+ *     argmin_w  lambda/2 ||w||^2 + 1/(2n) ||X^T w - y||^2          (eq. "primal")
+ *
+ * with X in R^{d x n} (rows = features, columns = samples), either by the
+ * primal s-step method CA-BCD (Algorithm 2; Algorithm 1 when s = 1) or by the
+ * dual s-step method CA-BDCD (Algorithm 4; Algorithm 3 when s = 1) on
+ *
+ *     argmin_alpha  lambda/2 ||X alpha/(lambda n)||^2 + 1/(2n) ||alpha + y||^2  (eq. "6")
+ *
+ * with w = -X alpha/(lambda n) (eq. "3").
+ *
+ * One outer step of either method (s inner block updates) is:
+ *   a1  draw the s blocks of b indices (Alg. 2/4, inner sampling loop);
+ *   a2  gather the s*b sampled rows (primal) / columns (dual) of X into Y;
+ *   a3  form the Gram matrix and the projection of Y on the residual (primal)
+ *       or on w (dual) in one pass over Y (Alg. 2/4, "compute the Gram matrix");
+ *   a4  run the s unrolled b x b solves (eq. "recur" / its dual analogue);
+ *   a5  apply the deferred vector update (Sec. 3.1 / 3.2, the s-step updates);
+ *   a6  every `recompute_every` outer steps, rebuild the auxiliary vector from
+ *       its definition (z = X^T w, Sec. 3.1; w = -X alpha/(lambda n), eq. "3").
+ *
+ * Conventions for every entry point:
+ *   - Status: CA_OK (0) or a negative ca_status; nothing is thrown across the
+ *     ABI.  ca_status_str() names a status.
+ *   - Pointers: all arrays are caller-owned.  Array arguments of the solve
+ *     calls may be device memory (used in place) or host memory (pinned or
+ *     pageable; staged through device buffers the context owns, with the
+ *     copies on the context's stream).  The library never frees caller memory.
+ *   - Streams: work is issued on the stream given to ca_bcd_init.  A solve
+ *     returns after its last kernel and copies finished (it synchronises the
+ *     stream to read the device error word).
+ *   - Sampling: block h (0-based global inner-iteration index, h0 .. h0+H-1)
+ *     draws b distinct indices of [0, N) (N = d primal, n dual) by Floyd's
+ *     algorithm fed by Philox4x64-10 with key (seed, 0) and counter
+ *     (h, m/4, 0, 0), word m%4 for draw m, mapped to [0, J] as
+ *     floor(u*(J+1)/2^64).  The same (seed, h) draws the same block for every
+ *     s, so CA-BCD reproduces the s = 1 iterates in exact arithmetic (Sec. 3).
+ */
+#ifndef CA_BCD_H
+#define CA_BCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  CA_OK = 0,
+  CA_ERR_ARG = -1,        /* invalid argument (sizes, b > N, lambda <= 0, ...) */
+  CA_ERR_CUDA = -2,       /* a CUDA runtime call failed                        */
+  CA_ERR_NOT_SPD = -3,    /* a b x b diagonal block had a non-positive pivot   */
+  CA_ERR_NONFINITE = -4,  /* a non-finite value appeared in a Gram or solve    */
+  CA_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up                */
+  CA_ERR_OOM = -6,        /* scratch would exceed the context's budget         */
+  CA_ERR_UNSUPPORTED = -7 /* valid input outside what this build implements    */
+} ca_status;
+
+/* Storage of X. */
+typedef enum {
+  CA_DENSE_F64 = 0, /* dense, FP64                                              */
+  CA_DENSE_F32 = 1, /* dense, FP32                                              */
+  CA_CSR_F32 = 2    /* dual only: CSR of X^T (row i = sample i), FP32 values    */
+} ca_xfmt;
+
+/* Arithmetic of the Gram matrix (step a3).  The projection, the solves and
+ * all vectors are FP64-accurate in every mode. */
+typedef enum {
+  CA_GRAM_F64 = 0,        /* FP64 on CUDA cores (any dense X)                   */
+  CA_GRAM_FP32_EXACT = 1, /* FP32 X: 3xTF32 split products on tcgen05, FP32 acc. */
+  CA_GRAM_TF32 = 2,       /* FP32 X: TF32 tcgen05 products, FP32 accumulate     */
+  CA_GRAM_BF16X3 = 3,     /* reserved                                           */
+  CA_GRAM_FP16_SCALED = 4 /* reserved                                           */
+} ca_prec;
+
+/* Solve options. */
+typedef struct {
+  int b;                /* block size b (primal) or b' (dual); 1 <= b <= N     */
+  int s;                /* unrolling depth s >= 1 (s = 1: Algorithm 1 / 3)      */
+  long long H;          /* number of inner iterations (block updates), H >= 1  */
+  double lam;           /* regularisation lambda > 0                           */
+  unsigned long long seed; /* sampler seed                                      */
+  int prec;             /* ca_prec for the Gram of dense FP32 X                */
+  int recompute_every;  /* a6 period in outer steps; 0 = never                  */
+  long long h0;         /* index of the first block (resume point), >= 0      */
+} ca_opts;
+
+/* Dual CSR input: CSR of X^T with n rows (samples) and d columns (features).
+ * rowptr has n+1 entries (int64), col and val have rowptr[n] entries; column
+ * indices inside a row must be strictly increasing. */
+typedef struct {
+  const long long* rowptr;
+  const int* col;
+  const float* val;
+} ca_csr;
+
+typedef struct ca_ctx ca_ctx;
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  scratch_bytes_max
+ * bounds the device memory the context may allocate for its scratch
+ * (sampled indices, Gram partials, staging of host inputs); 0 = no bound.
+ * Writes the new context to *ctx.  Errors: CA_ERR_ARG, CA_ERR_CUDA. */
+int ca_bcd_init(ca_ctx** ctx, int device, void* cuda_stream, size_t scratch_bytes_max);
+
+/* Primal CA-BCD (Algorithm 2; Algorithm 1 when s = 1).
+ *   xfmt  CA_DENSE_F64 or CA_DENSE_F32.
+ *   X     d x n row-major (row f = feature f), leading dimension ld >= n
+ *         elements.  For the tcgen05 Gram modes, X and ld*4 bytes must be
+ *         16-byte aligned.
+ *   y     n labels (FP64).
+ *   w     d (FP64): w0 on entry, w_H on return.
+ *   z     NULL, or n (FP64): receives X^T w_H computed by a final full pass.
+ * Errors: CA_ERR_ARG (b > d, s < 1, H < 1, lambda <= 0, ld < n, bad format),
+ * CA_ERR_UNSUPPORTED (s*b or b beyond this build's limits), CA_ERR_NOT_SPD,
+ * CA_ERR_NONFINITE, CA_ERR_TIMEOUT, CA_ERR_OOM, CA_ERR_CUDA.  On error w and
+ * z hold unspecified intermediate values. */
+int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n, long long ld,
+                 const double* y, const ca_opts* opts, double* w, double* z);
+
+/* Dual CA-BDCD (Algorithm 4; Algorithm 3 when s = 1).
+ *   xfmt  CA_DENSE_F64 / CA_DENSE_F32: XT is X^T, n x d row-major (row i =
+ *         sample i = column x_i of X), leading dimension ld >= d.
+ *         CA_CSR_F32: XT points to a ca_csr (ld is ignored).
+ *   y     n labels (FP64).
+ *   alpha n (FP64): alpha0 on entry, alpha_H on return.
+ *   w     d (FP64): receives w_H (w0 = -X alpha0/(lambda n) is formed first,
+ *         as Algorithms 3-4 initialise it).
+ * Errors as ca_bcd_solve, with b <= n. */
+int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long n, long long ld,
+                  const double* y, const ca_opts* opts, double* alpha, double* w);
+
+/* The sampler alone: writes blocks h0 .. h0+H-1 (H x b int32, row-major) of
+ * b distinct indices of [0, N) to out, computed on the context's device.
+ * out may be host or device memory.  Errors: CA_ERR_ARG, CA_ERR_CUDA. */
+int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long long H, int b,
+                      long long N, int* out);
+
+/* Name of a status code (static string). */
+const char* ca_status_str(int status);
+
+/* Release the context and its scratch (caller memory is untouched). */
+void ca_bcd_destroy(ca_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CA_BCD_H */
