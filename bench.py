@@ -1,0 +1,337 @@
+"""Benchmark: CA-BCD block updates per second on one GB300 (or N replicas).
+
+Workload (the dense primal FP32 configuration): X 4096 x 262144 FP32 with
+geometrically scaled rows (condition 1e3), y = X^T w_true + 1% noise,
+lambda = 1e-4, b = 8, s = 32, H = 4096 block updates, TF32 tensor-core Gram,
+FP64 solves.  One step = one full solve (sampling, H/s outer steps of
+gather+Gram+projection, inner solves, deferred update, and the final
+z = X^T w_H pass) with X resident in HBM.  X (4 GiB) is larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas (one per
+GPU, launched by torchrun); value = total block updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CA-BCD block-updates/s"
+UNIT = "block-updates/s"
+D, N_SAMPLES, COND, LAM, B, S, H = 4096, 262144, 1e3, 1e-4, 8, 32, 4096
+PREC = "tf32"
+
+
+def workload_config(d=D, n=N_SAMPLES, b=B, s=S, h=H, prec=PREC):
+    return {
+        "workload": f"dense primal CA-BCD, FP32 X {d}x{n} (cond 1e3 geometric rows), "
+                    f"lambda 1e-4, b={b}, s={s}, H={h}, {prec} tcgen05 Gram, FP64 solves",
+        "d": d, "n": n, "b": b, "s": s, "H": h, "lambda": LAM, "gram": prec,
+        "l2": "inputs larger than L2 (X is 4 GiB, L2 129 MB); no flush needed",
+        "step": "one full solve of H block updates incl. sampling and final z = X^T w_H",
+    }
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _traffic_record(kernel_src: str):
+    """Per-launch DRAM traffic of the Gram kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "gram_tc_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(kernel_src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        if rec.get("src_sha") == sha:
+            return rec
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"],
+                    "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(self.rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in self.rows)}
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Maximum of a per-rank float over the process group (identity at N = 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def time_solves(ctx, X, y, w, z, steps, stream, b=B, s=S, h=H, prec=PREC):
+    """Device time (ms) of `steps` back-to-back solves, CUDA events on the
+    library's stream."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        w.zero_()
+        ctx.ca_bcd_solve(X, y, w, z, b=b, s=s, H=h, lam=LAM, seed=42, prec=prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def cpu_baseline(X_host_f32, y_host, budget_s: float = 30.0):
+    """The FP64 oracle as it stands (single thread) on a bounded sample of the
+    workload: the first outer step (s = 32 block updates) of the same solve."""
+    import numpy as np
+    import oracle
+    X64 = X_host_f32.astype(np.float64)
+    h_sample = S
+    t0 = time.perf_counter()
+    oracle.ca_bcd(X64, y_host, LAM, b=B, s=S, H=h_sample, seed=42)
+    dt = time.perf_counter() - t0
+    return {"value": h_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first outer step ({h_sample} block updates, b={B}, s={S}) of the same "
+                      f"{D}x{N_SAMPLES} solve, FP64 C oracle, single thread; {dt:.2f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    """--impl reference: the FP64 oracle on the host cores, each step the first
+    outer step (s block updates) of the workload."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    import oracle
+    import synth
+    oracle.build()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    X, y, _ = synth.dense_primal_torch(D, N_SAMPLES, cond=COND, seed=1, device=dev)
+    X64 = X.cpu().numpy().astype(np.float64)
+    yh = y.cpu().numpy()
+    del X
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.ca_bcd(X64, yh, LAM, b=B, s=S, H=S, seed=42)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = S / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: first outer step ({S} block updates) of the "
+                                   f"workload, FP64 C oracle, single thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import paper_1612_04003_gb300 as ca
+    import synth
+
+    ca.build()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    X, y, _ = synth.dense_primal_torch(D, N_SAMPLES, cond=COND, seed=1, device="cuda")
+    w = torch.zeros(D, dtype=torch.float64, device="cuda")
+    z = torch.zeros(N_SAMPLES, dtype=torch.float64, device="cuda")
+    ctx = ca.Context(local_rank, stream=stream.cuda_stream)
+
+    # warm-up
+    time_solves(ctx, X, y, w, z, args.warmup, stream)
+    # timed region
+    ctx.ca_profile_enable(True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier(world)
+    ms = time_solves(ctx, X, y, w, z, args.steps, stream)
+    barrier(world)
+    clocks.stop()
+    prof = ctx.ca_profile_read()
+    ctx.ca_profile_enable(False)
+    ms_step = max_over_ranks(ms / args.steps, world)
+    value = world * H / (ms_step * 1e-3)
+
+    # roofline of the dominant kernel (the tcgen05 Gram pass, one launch per outer step)
+    peaks, peak_kind = _peaks()
+    sb = S * B
+    gram_ms = prof["gram_ms"] / max(1, prof["gram_launches"])
+    alg_bytes = sb * N_SAMPLES * 4 + N_SAMPLES * 8          # Y rows + the projection vector
+    achieved = alg_bytes / (gram_ms * 1e-3) / 1e9
+    trec = _traffic_record(os.path.join(ROOT, "paper_1612_04003_gb300", "csrc", "ca_gram_tc.cu"))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"],
+            "traffic": trec["traffic_bytes_per_launch"] if trec else None,
+            "kernel": "k_gram_tc<256,tf32> (gather + Gram + projection)",
+            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": gram_ms,
+            "launches": prof["gram_launches"], "peak_source": f"hbm_gbs ({peak_kind})",
+            "gram_share_of_step": prof["gram_ms"] / max(ms, 1e-9)}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    Xh = torch.empty((D, N_SAMPLES), dtype=torch.float32, pin_memory=True)
+    Xh.copy_(X)
+    yh = torch.empty(N_SAMPLES, dtype=torch.float64, pin_memory=True)
+    yh.copy_(y)
+    wh = torch.zeros(D, dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=S, H=H, lam=LAM, seed=42, prec=PREC)  # warm
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        wh.zero_()
+        ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=S, H=H, lam=LAM, seed=42, prec=PREC)
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    e2e = {"value": world * H / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8 + wh.numel() * 8),
+           "d2h_bytes_per_step": int(wh.numel() * 8), "ms_per_step": t_e2e * 1e3,
+           "how": "ca_bcd_solve on pinned host X, y, w: the library copies them to the device "
+                  "and w_H back inside each call; wall clock, synchronous call"}
+    del Xh
+
+    # s sweep (same data, fewer steps): s-step against s = 1
+    sweep = []
+    if not args.no_sweep:
+        for (b_, s_) in [(8, 1), (8, 4), (8, 8), (8, 16), (8, 32), (32, 1), (32, 4), (32, 8)]:
+            nst = 2 if s_ == 1 else 4
+            time_solves(ctx, X, y, w, z, 1, stream, b=b_, s=s_)
+            t = time_solves(ctx, X, y, w, z, nst, stream, b=b_, s=s_) / nst
+            sweep.append({"b": b_, "s": s_, "ms_per_step": t, "block_updates_per_s": H / (t * 1e-3)})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(X.cpu().numpy(), y.cpu().numpy())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32", "data": "synthetic", "config": workload_config(),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(prof["kernel_launches"]),
+            "clocks": clocks.summary(), "sweep": sweep,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

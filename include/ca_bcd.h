@@ -143,8 +143,38 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
 int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long long H, int b,
                       long long N, int* out);
 
+/* Steps a2+a3 alone for given sampled rows (Alg. 2 / 4, "compute the Gram
+ * matrix"): for the sb rows idx[0..sb) of the N x K row-major matrix A
+ * (leading dimension ld), writes G = Y Y^T (sb x sb, row-major, FP64, full
+ * symmetric, no scaling and no lambda) and p = Y v (sb, FP64), where v has K
+ * entries.  A, idx, v, G and p must be device memory.  xfmt and prec as for
+ * the solves (TF32 / 3xTF32 need FP32 A, 16-byte aligned rows, sb <= 256).
+ * Errors: CA_ERR_ARG, CA_ERR_UNSUPPORTED, CA_ERR_OOM, CA_ERR_CUDA. */
+int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N, long long K,
+                    long long ld, const int* idx, int sb, const double* v, double* G, double* p);
+
+/* Text of the last failing CUDA call seen by an entry point on this context
+ * (empty if none); owned by the context, valid until the next call. */
+const char* ca_last_error(ca_ctx* ctx);
+
 /* Name of a status code (static string). */
 const char* ca_status_str(int status);
+
+/* Measurement hooks.  With profiling on, every following solve records a CUDA
+ * event pair on the context's stream around each Gram launch (step a2+a3);
+ * ca_profile_read returns the summed event time (ms) and the launch counts
+ * (Gram launches, and all kernel launches the solves issued) since the last
+ * ca_profile_enable.  Errors: CA_ERR_ARG for a NULL context. */
+int ca_profile_enable(ca_ctx* ctx, int on);
+int ca_profile_read(ca_ctx* ctx, double* gram_ms_total, long long* gram_launches,
+                    long long* kernel_launches);
+
+/* Diagnostic: runs one kernel whose thread waits on a device barrier that
+ * nothing completes, through the same bounded wait the Gram kernel uses,
+ * with a limit of limit_ns nanoseconds (1 .. 1e9).  Returns CA_ERR_TIMEOUT
+ * when the wait gave up as designed (the context stays usable), CA_OK if it
+ * did not, CA_ERR_ARG / CA_ERR_CUDA on bad input or a CUDA failure. */
+int ca_selftest_wait_timeout(ca_ctx* ctx, long long limit_ns);
 
 /* Release the context and its scratch (caller memory is untouched). */
 void ca_bcd_destroy(ca_ctx* ctx);

@@ -1,0 +1,246 @@
+"""GB300 (sm_103a) CA-BCD / CA-BDCD: Python binding of the C ABI in include/ca_bcd.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libcabcd.so``.  There is no CPU path; importing the binding without
+the built library raises.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they are passed by
+pointer.  CUDA tensors are used in place; host arrays are staged by the
+library through device buffers it owns.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from .buildlib import LIB, INCLUDE, build  # noqa: F401
+
+CA_OK = 0
+CA_ERR_ARG = -1
+CA_ERR_CUDA = -2
+CA_ERR_NOT_SPD = -3
+CA_ERR_NONFINITE = -4
+CA_ERR_TIMEOUT = -5
+CA_ERR_OOM = -6
+CA_ERR_UNSUPPORTED = -7
+
+CA_DENSE_F64 = 0
+CA_DENSE_F32 = 1
+CA_CSR_F32 = 2
+
+CA_GRAM_F64 = 0
+CA_GRAM_FP32_EXACT = 1
+CA_GRAM_TF32 = 2
+CA_GRAM_BF16X3 = 3
+CA_GRAM_FP16_SCALED = 4
+
+PREC = {"f64": CA_GRAM_F64, "fp32_exact": CA_GRAM_FP32_EXACT, "3xtf32": CA_GRAM_FP32_EXACT,
+        "tf32": CA_GRAM_TF32}
+
+
+class ca_opts(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int), ("s", ctypes.c_int), ("H", ctypes.c_longlong),
+                ("lam", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("prec", ctypes.c_int),
+                ("recompute_every", ctypes.c_int), ("h0", ctypes.c_longlong)]
+
+
+class ca_csr(ctypes.Structure):
+    _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class CaError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        extra = f" [{detail}]" if detail else ""
+        super().__init__(f"{what}: {status_str(status)} ({status}){extra}")
+
+
+_lib = None
+
+
+def load():
+    """Load libcabcd.so (built by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"CUDA library not built: {LIB} is missing (run "
+                           "paper_1612_04003_gb300.build.build())")
+    lib = ctypes.CDLL(LIB)
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_ulonglong, \
+        ctypes.c_double
+    lib.ca_bcd_init.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.c_size_t]
+    lib.ca_bcd_init.restype = i32
+    lib.ca_bcd_solve.argtypes = [vp, i32, vp, i64, i64, i64, vp, ctypes.POINTER(ca_opts), vp, vp]
+    lib.ca_bcd_solve.restype = i32
+    lib.ca_bdcd_solve.argtypes = [vp, i32, vp, i64, i64, i64, vp, ctypes.POINTER(ca_opts), vp, vp]
+    lib.ca_bdcd_solve.restype = i32
+    lib.ca_sample_indices.argtypes = [vp, u64, i64, i64, i32, i64, vp]
+    lib.ca_sample_indices.restype = i32
+    lib.ca_status_str.argtypes = [i32]
+    lib.ca_status_str.restype = ctypes.c_char_p
+    lib.ca_bcd_destroy.argtypes = [vp]
+    lib.ca_bcd_destroy.restype = None
+    lib.ca_profile_enable.argtypes = [vp, i32]
+    lib.ca_profile_enable.restype = i32
+    lib.ca_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ca_profile_read.restype = i32
+    lib.ca_last_error.argtypes = [vp]
+    lib.ca_last_error.restype = ctypes.c_char_p
+    lib.ca_gram_project.argtypes = [vp, i32, i32, vp, i64, i64, i64, vp, i32, vp, vp, vp]
+    lib.ca_gram_project.restype = i32
+    lib.ca_selftest_wait_timeout.argtypes = [vp, i64]
+    lib.ca_selftest_wait_timeout.restype = i32
+    _lib = lib
+    return lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/*.h."""
+    names = []
+    for fn in sorted(os.listdir(INCLUDE)):
+        if fn.endswith(".h"):
+            text = open(os.path.join(INCLUDE, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ca_\w+)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+def status_str(status: int) -> str:
+    return load().ca_status_str(int(status)).decode()
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _xfmt(X) -> int:
+    name = str(X.dtype)
+    if name.endswith("float64"):
+        return CA_DENSE_F64
+    if name.endswith("float32"):
+        return CA_DENSE_F32
+    raise TypeError(f"X must be float32 or float64, got {X.dtype}")
+
+
+def _dtype_is_f64(a) -> bool:
+    return str(a.dtype).endswith("float64")
+
+
+class Context:
+    """ca_bcd_init / ca_bcd_destroy around an opaque ca_ctx."""
+
+    def __init__(self, device: int = 0, stream=None, scratch_bytes_max: int = 0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        s = stream if isinstance(stream, int) or stream is None else getattr(
+            stream, "cuda_stream", stream)
+        st = self._lib.ca_bcd_init(ctypes.byref(h), device, s, scratch_bytes_max)
+        if st != CA_OK:
+            raise CaError(st, "ca_bcd_init")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ca_bcd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self._lib.ca_last_error(self.handle).decode()
+
+    @staticmethod
+    def _opts(b, s, H, lam, seed, prec, recompute_every, h0):
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        return ca_opts(int(b), int(s), int(H), float(lam), int(seed), p, int(recompute_every),
+                       int(h0))
+
+    def ca_bcd_solve(self, X, y, w, z=None, *, b, s=1, H, lam, seed=42, prec="tf32",
+                     recompute_every=0, h0=0, n=None, ld=None):
+        """Primal CA-BCD: w (in: w0, out: w_H) and optionally z = X^T w_H.
+        X is d x ld (ld = X.shape[1]); n (default ld) columns are used."""
+        d, cols = X.shape
+        n = cols if n is None else int(n)
+        ld = cols if ld is None else int(ld)
+        for a in (y, w) + ((z,) if z is not None else ()):
+            if not _dtype_is_f64(a):
+                raise TypeError("y, w, z must be float64")
+        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0)
+        st = self._lib.ca_bcd_solve(self.handle, _xfmt(X), _ptr(X), d, n, ld,
+                                    _ptr(y), ctypes.byref(o), _ptr(w), _ptr(z))
+        if st != CA_OK:
+            raise CaError(st, "ca_bcd_solve", self.last_error())
+        return w, z
+
+    def ca_bdcd_solve(self, XT, y, alpha, w, *, b, s=1, H, lam, seed=42, prec="tf32",
+                      recompute_every=0, h0=0, d=None, ld=None):
+        """Dual CA-BDCD.  XT is X^T (n x d, dense) or a (rowptr, col, val) CSR
+        triple of X^T (then d must be given)."""
+        for a in (y, alpha, w):
+            if not _dtype_is_f64(a):
+                raise TypeError("y, alpha, w must be float64")
+        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0)
+        if isinstance(XT, (tuple, list)):
+            rowptr, col, val = XT
+            csr = ca_csr(_ptr(rowptr), _ptr(col), _ptr(val))
+            n = int(rowptr.shape[0]) - 1
+            st = self._lib.ca_bdcd_solve(self.handle, CA_CSR_F32, ctypes.addressof(csr), int(d), n,
+                                         0, _ptr(y), ctypes.byref(o), _ptr(alpha), _ptr(w))
+        else:
+            n, dd = XT.shape
+            st = self._lib.ca_bdcd_solve(self.handle, _xfmt(XT), _ptr(XT), dd, n,
+                                         dd if ld is None else ld, _ptr(y), ctypes.byref(o),
+                                         _ptr(alpha), _ptr(w))
+        if st != CA_OK:
+            raise CaError(st, "ca_bdcd_solve", self.last_error())
+        return alpha, w
+
+    def ca_sample_indices(self, seed, h0, H, b, N, out):
+        st = self._lib.ca_sample_indices(self.handle, int(seed), int(h0), int(H), int(b), int(N),
+                                         _ptr(out))
+        if st != CA_OK:
+            raise CaError(st, "ca_sample_indices", self.last_error())
+        return out
+
+    def ca_gram_project(self, A, idx, v, G, p, *, prec="tf32", ld=None):
+        """G = Y Y^T and p = Y v for the rows idx of A (all device arrays)."""
+        N, K = A.shape
+        pr = PREC[prec] if isinstance(prec, str) else int(prec)
+        st = self._lib.ca_gram_project(self.handle, _xfmt(A), pr, _ptr(A), N, K,
+                                       K if ld is None else ld, _ptr(idx), int(idx.shape[0]),
+                                       _ptr(v), _ptr(G), _ptr(p))
+        if st != CA_OK:
+            raise CaError(st, "ca_gram_project", self.last_error())
+        return G, p
+
+    def ca_selftest_wait_timeout(self, limit_ns: int) -> int:
+        return int(self._lib.ca_selftest_wait_timeout(self.handle, int(limit_ns)))
+
+    def ca_profile_enable(self, on: bool = True):
+        st = self._lib.ca_profile_enable(self.handle, 1 if on else 0)
+        if st != CA_OK:
+            raise CaError(st, "ca_profile_enable")
+
+    def ca_profile_read(self):
+        ms, g, k = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        st = self._lib.ca_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(g), ctypes.byref(k))
+        if st != CA_OK:
+            raise CaError(st, "ca_profile_read")
+        return {"gram_ms": ms.value, "gram_launches": g.value, "kernel_launches": k.value}

@@ -1,0 +1,677 @@
+// ca_api.cu -- the C ABI (include/ca_bcd.h): contexts, scratch, staging of
+// host buffers and the outer-step loops of CA-BCD (Alg. 2) and CA-BDCD (Alg. 4).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ca_bcd.h"
+#include "ca_kernels.cuh"
+
+namespace {
+
+constexpr int kMaxB = 128;          // b x b block held in shared memory by the solve
+constexpr int kMaxSB = 1024;        // s*b right-hand sides held in shared memory
+constexpr int kSolveSmemMax = 200 * 1024;
+
+struct Profile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;      // pairs around each Gram launch
+  double gram_ms = 0.0;
+  long long gram_launches = 0;
+  long long kernel_launches = 0;
+};
+
+}  // namespace
+
+struct ca_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t scratch_max = 0;
+  int num_sms = 0;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  unsigned* d_err = nullptr;     // device error word
+  unsigned* d_ticket = nullptr;  // last-CTA ticket of the reduce/solve kernel
+  unsigned* h_err = nullptr;     // pinned copy
+  Profile prof;
+  char last_error[256] = {0};    // text of the last failing CUDA call
+};
+
+namespace {
+
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+thread_local ca_ctx* t_cur_ctx = nullptr;  // context of the running entry point
+
+int cuda_fail(cudaError_t e, int line) {
+  if (t_cur_ctx)
+    snprintf(t_cur_ctx->last_error, sizeof(t_cur_ctx->last_error), "ca_api.cu:%d: %s (%s)", line,
+             cudaGetErrorName(e), cudaGetErrorString(e));
+  return CA_ERR_CUDA;
+}
+
+#define cuda_status(expr) cuda_status_at((expr), __LINE__)
+int cuda_status_at(cudaError_t e, int line) { return e == cudaSuccess ? CA_OK : cuda_fail(e, line); }
+
+#define CA_TRY_CUDA(call)                              \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, __LINE__); \
+  } while (0)
+
+#define CA_TRY(call)        \
+  do {                      \
+    int s_ = (call);        \
+    if (s_ != CA_OK) return s_; \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure_arena(ca_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->arena_bytes) return CA_OK;
+  if (ctx->scratch_max && bytes > ctx->scratch_max) return CA_ERR_OOM;
+  if (ctx->arena) {
+    CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->arena_bytes = 0;
+  }
+  if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return CA_ERR_OOM;
+  }
+  ctx->arena_bytes = bytes;
+  return CA_OK;
+}
+
+int status_from_err(unsigned e) {
+  if (e & CA_DEV_ERR_TIMEOUT) return CA_ERR_TIMEOUT;
+  if (e & CA_DEV_ERR_NONFINITE) return CA_ERR_NONFINITE;
+  if (e & CA_DEV_ERR_NOT_SPD) return CA_ERR_NOT_SPD;
+  if (e & CA_DEV_ERR_ARG) return CA_ERR_ARG;
+  return CA_OK;
+}
+
+int finish(ca_ctx* ctx) {
+  CA_TRY_CUDA(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                              ctx->stream));
+  CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->prof.on) {
+    for (size_t i = 0; i + 1 < ctx->prof.ev.size(); i += 2) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->prof.ev[i], ctx->prof.ev[i + 1]);
+      ctx->prof.gram_ms += ms;
+      ctx->prof.gram_launches += 1;
+    }
+    for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
+    ctx->prof.ev.clear();
+  }
+  return status_from_err(*ctx->h_err);
+}
+
+void prof_mark(ca_ctx* ctx) {
+  if (!ctx->prof.on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, ctx->stream);
+  ctx->prof.ev.push_back(e);
+}
+
+int check_opts(const ca_opts* o, long long N) {
+  if (!o) return CA_ERR_ARG;
+  if (o->b < 1 || (long long)o->b > N || o->s < 1 || o->H < 1 || o->h0 < 0) return CA_ERR_ARG;
+  if (!(o->lam > 0.0) || !std::isfinite(o->lam)) return CA_ERR_ARG;
+  if (o->recompute_every < 0) return CA_ERR_ARG;
+  if (o->prec < CA_GRAM_F64 || o->prec > CA_GRAM_FP16_SCALED) return CA_ERR_ARG;
+  if (N > 2147483647LL) return CA_ERR_UNSUPPORTED;
+  if (o->b > kMaxB) return CA_ERR_UNSUPPORTED;
+  const long long sbm = (long long)std::min<long long>(o->s, o->H) * o->b;
+  if (sbm > kMaxSB) return CA_ERR_UNSUPPORTED;
+  return CA_OK;
+}
+
+// The dense outer-step loop shared by both methods.
+struct DenseProblem {
+  int xfmt;                 // CA_DENSE_F64 / CA_DENSE_F32
+  const void* A;            // N x K row-major, leading dim lda (device)
+  long long N, K, lda;
+  double* v;                // K: projection vector (rho or w), device
+  double* x;                // N: variable updated by the solves (w or alpha), device
+  const double* yv;         // dual: y (device), primal: nullptr
+  double cG, cI, cP, cY, cU;
+  // recompute of v: v = c0 * y0 + c1 * sum_r A[r] x[r]
+  const double* y0;
+  double c0, c1;
+};
+
+int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const double* y0,
+                     double c0, double c1) {
+  const long long K = pb.K, N = pb.N;
+  k_axpby_init<<<(unsigned)((K + 255) / 256), 256, 0, ctx->stream>>>(y0, c0, K, vout);
+  const long long gx = (K + 1023) / 1024;
+  long long ysplit = (2LL * ctx->num_sms + gx - 1) / gx;
+  ysplit = std::max(1LL, std::min(ysplit, (N + 63) / 64));
+  const long long rps = (N + ysplit - 1) / ysplit;
+  ysplit = (N + rps - 1) / rps;
+  dim3 grid((unsigned)gx, (unsigned)ysplit);
+  launch_recompute_dense(pb.xfmt == CA_DENSE_F64, grid, ctx->stream, pb.A, pb.lda, N, K, pb.x, c1,
+                         rps, vout);
+  ctx->prof.kernel_launches += 2;
+  return cuda_status(cudaGetLastError());
+}
+
+// Split-K plan of the a2+a3 pass for a given s*b bound.
+struct GramPlan {
+  bool tc;
+  int three, sbp, P, ntiles;
+  long long chunks_per_split;
+};
+
+GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
+  GramPlan g{};
+  g.tc = (xfmt == CA_DENSE_F32) && (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT);
+  g.three = (prec == CA_GRAM_FP32_EXACT) ? 1 : 0;
+  if (g.tc) {
+    g.sbp = sbm <= 128 ? 128 : 256;
+    g.P = (int)std::min<long long>(ctx->num_sms, (K + 31) / 32);
+  } else {
+    g.sbp = (sbm + 63) / 64 * 64;
+    const int t = g.sbp / 64;
+    g.ntiles = t * (t + 1) / 2;
+    const long long nchunks = (K + 31) / 32;
+    long long Pm = std::max(1LL, (long long)(2 * ctx->num_sms) / g.ntiles);
+    Pm = std::min(Pm, nchunks);
+    const long long cap = std::max(1LL, (long long)((256ull << 20) / ((size_t)g.sbp * g.sbp * 8)));
+    Pm = std::min(Pm, cap);
+    g.chunks_per_split = (nchunks + Pm - 1) / Pm;
+    g.P = (int)((nchunks + g.chunks_per_split - 1) / g.chunks_per_split);
+  }
+  return g;
+}
+
+// a2+a3: split-K partials of Y Y^T and Y v for the sampled rows idx[0..sb).
+int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long long lda, long long N,
+                long long K, const int* idx, int sb, const double* v, void* part, double* ppart) {
+  if (g.tc) {
+    const int e = launch_gram_tc(static_cast<const float*>(A), lda, N, K, idx, sb, v, g.P, g.sbp,
+                                 static_cast<float*>(part), ppart, ctx->d_err, g.three, ctx->stream);
+    return e == 0 ? CA_OK : CA_ERR_CUDA;
+  }
+  launch_gram_simt(xfmt == CA_DENSE_F64, dim3(g.P, g.ntiles), ctx->stream, A, lda, N, K, idx, sb, v,
+                   g.chunks_per_split, g.sbp, static_cast<double*>(part), ppart, ctx->d_err);
+  return cuda_status(cudaGetLastError());
+}
+
+// a4 entry: reduce the partials to R, p, then (s_cur > 0) the inner solves.
+void launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const double* ppart,
+                         double* R, double* pvec, const SolveArgs& sa) {
+  const long long entries = (long long)sa.sb * (sa.sb + 1) / 2 + sa.sb;
+  const int G = (int)std::max(1LL, std::min<long long>((entries + 255) / 256, 2LL * ctx->num_sms));
+  const size_t ssm = (size_t)(sa.sb + sa.b * sa.b + sa.b) * sizeof(double);
+  launch_reduce_solve_k(g.tc, G, ssm, ctx->stream, part, ppart, g.P, g.sbp, R, pvec, sa,
+                        ctx->d_ticket, ctx->d_err);
+}
+
+int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_all, char* work,
+              size_t work_bytes) {
+  const long long K = pb.K;
+  const int b = o->b, s = o->s;
+  const long long H = o->H;
+  const int sbm = (int)(std::min<long long>(s, H) * b);
+  Carve cv{work};
+  (void)work_bytes;
+  const GramPlan g = gram_plan(ctx, pb.xfmt, o->prec, sbm, K);
+  const int sbp = g.sbp, P = g.P;
+  void* part = g.tc ? (void*)cv.take<float>((size_t)P * sbp * sbp)
+                    : (void*)cv.take<double>((size_t)P * sbp * sbp);
+  double* ppart = cv.take<double>((size_t)P * sbp);
+  double* R = cv.take<double>((size_t)sbp * sbp);
+  double* pvec = cv.take<double>((size_t)sbp);
+  double* delta = cv.take<double>((size_t)sbp);
+
+  const long long n_outer = (H + s - 1) / s;
+  for (long long k = 0; k < n_outer; ++k) {
+    const int sk = (int)std::min<long long>(s, H - (long long)s * k);
+    const int sb = sk * b;
+    const int* idx = idx_all + (size_t)s * k * b;
+    // a2 + a3
+    prof_mark(ctx);
+    CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, part, ppart));
+    prof_mark(ctx);
+    // a4 (reduce of the split-K partials, then the s unrolled solves)
+    SolveArgs sa{idx, pb.N, b, sk, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, delta};
+    launch_reduce_solve(ctx, g, part, ppart, R, pvec, sa);
+    // a5
+    const size_t usm = align256((size_t)sb * 4) + (size_t)sb * 8;  // sidx | delta
+    const unsigned ug = (unsigned)((K + 1023) / 1024);
+    launch_update_dense(pb.xfmt == CA_DENSE_F64, ug, usm, ctx->stream, pb.A, pb.lda, pb.N, K, idx, sb,
+                        delta, pb.cU, pb.v, ctx->d_err);
+    ctx->prof.kernel_launches += 3;
+    CA_TRY_CUDA(cudaGetLastError());
+    // a6
+    if (o->recompute_every > 0 && (k + 1) % o->recompute_every == 0)
+      CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
+  }
+  return CA_OK;
+}
+
+size_t dense_work_bytes(ca_ctx* ctx, const ca_opts* o, long long K, int xfmt) {
+  const int sbm = (int)(std::min<long long>(o->s, o->H) * o->b);
+  const bool tc = (xfmt == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
+  size_t sbp, P, el;
+  if (tc) {
+    sbp = sbm <= 128 ? 128 : 256;
+    P = (size_t)std::min<long long>(ctx->num_sms, (K + 31) / 32);
+    el = 4;
+  } else {
+    sbp = (size_t)(sbm + 63) / 64 * 64;
+    P = (size_t)std::max<long long>(1, 2 * ctx->num_sms);  // upper bound of the split count
+    const size_t cap = std::max<size_t>(1, (256ull << 20) / (sbp * sbp * 8));
+    P = std::min(P, cap);
+    el = 8;
+  }
+  return align256(P * sbp * sbp * el) + align256(P * sbp * 8) + align256(sbp * sbp * 8) +
+         2 * align256(sbp * 8) + 4096;
+}
+
+// Stage a caller array on the device (copy in when `in`), return the device pointer.
+template <typename T>
+T* stage(ca_ctx* ctx, Carve& cv, const T* p, size_t count, bool in, bool* staged) {
+  if (is_device_ptr(p)) {
+    *staged = false;
+    return const_cast<T*>(p);
+  }
+  *staged = true;
+  T* d = cv.take<T>(count);
+  if (in && count) cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+  return d;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* ca_status_str(int status) {
+  switch (status) {
+    case CA_OK: return "CA_OK";
+    case CA_ERR_ARG: return "CA_ERR_ARG: invalid argument";
+    case CA_ERR_CUDA: return "CA_ERR_CUDA: CUDA runtime error";
+    case CA_ERR_NOT_SPD: return "CA_ERR_NOT_SPD: a diagonal block is not positive definite";
+    case CA_ERR_NONFINITE: return "CA_ERR_NONFINITE: non-finite value in a Gram block or solve";
+    case CA_ERR_TIMEOUT: return "CA_ERR_TIMEOUT: a bounded device wait gave up";
+    case CA_ERR_OOM: return "CA_ERR_OOM: scratch exceeds the context budget";
+    case CA_ERR_UNSUPPORTED: return "CA_ERR_UNSUPPORTED: outside this build's limits";
+    default: return "unknown ca_status";
+  }
+}
+
+int ca_bcd_init(ca_ctx** out, int device, void* cuda_stream, size_t scratch_bytes_max) {
+  if (!out) return CA_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return ndev == 0 ? CA_ERR_CUDA : CA_ERR_ARG;
+  }
+  CA_TRY_CUDA(cudaSetDevice(device));
+  ca_ctx* ctx = new ca_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->scratch_max = scratch_bytes_max;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess || cudaMallocHost(&ctx->h_err, 64) != cudaSuccess) {
+    cudaGetLastError();
+    ca_bcd_destroy(ctx);
+    return CA_ERR_CUDA;
+  }
+  ctx->d_ticket = ctx->d_err + 32;
+  cudaMemset(ctx->d_err, 0, 256);
+  if (set_solve_smem_limit(kSolveSmemMax) != 0) {
+    cudaGetLastError();
+    ca_bcd_destroy(ctx);
+    return CA_ERR_CUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    ca_bcd_destroy(ctx);
+    return CA_ERR_CUDA;
+  }
+  *out = ctx;
+  return CA_OK;
+}
+
+void ca_bcd_destroy(ca_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->h_err) cudaFreeHost(ctx->h_err);
+  delete ctx;
+}
+
+int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long long H, int b,
+                      long long N, int* out) {
+  t_cur_ctx = ctx;
+  if (!ctx || !out || H < 0 || h0 < 0 || b < 1 || N < 1 || b > N || N > 2147483647LL)
+    return CA_ERR_ARG;
+  if (H == 0) return CA_OK;
+  CA_TRY_CUDA(cudaSetDevice(ctx->device));
+  const size_t bytes = (size_t)H * b * sizeof(int);
+  int* d = out;
+  const bool host = !is_device_ptr(out);
+  if (host) {
+    CA_TRY(ensure_arena(ctx, align256(bytes)));
+    d = static_cast<int*>(ctx->arena);
+  }
+  k_sample<<<(unsigned)((H + 7) / 8), 256, 0, ctx->stream>>>(seed, h0, H, b, N, d);
+  CA_TRY_CUDA(cudaGetLastError());
+  if (host) CA_TRY_CUDA(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+  return CA_OK;
+}
+
+int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n, long long ld,
+                 const double* y, const ca_opts* o, double* w, double* z) {
+  t_cur_ctx = ctx;
+  if (!ctx || !X || !y || !w || d < 1 || n < 1 || ld < n) return CA_ERR_ARG;
+  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32) return CA_ERR_ARG;
+  CA_TRY(check_opts(o, d));
+  const bool tc = (xfmt == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
+  if (o->prec == CA_GRAM_BF16X3 || o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
+  if (tc) {
+    if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return CA_ERR_ARG;
+    if (std::min<long long>(o->s, o->H) * o->b > gram_tc_max_sb()) return CA_ERR_UNSUPPORTED;
+  }
+  CA_TRY_CUDA(cudaSetDevice(ctx->device));
+  const size_t el = xfmt == CA_DENSE_F64 ? 8 : 4;
+  const bool x_host = !is_device_ptr(X), y_host = !is_device_ptr(y), w_host = !is_device_ptr(w);
+  const bool z_host = z && !is_device_ptr(z);
+  const size_t xbytes = (size_t)(d - 1) * ld * el + (size_t)n * el;
+  size_t need = dense_work_bytes(ctx, o, n, xfmt) + align256((size_t)n * 8) /* rho */ +
+                align256((size_t)o->H * o->b * 4) /* idx */;
+  if (x_host) need += align256(xbytes) + 256;
+  if (y_host) need += align256((size_t)n * 8);
+  if (w_host) need += align256((size_t)d * 8);
+  if (z_host) need += align256((size_t)n * 8);
+  need += 8 * 256;
+  CA_TRY(ensure_arena(ctx, need));
+  Carve cv{static_cast<char*>(ctx->arena)};
+  bool st;
+  const void* Xd = X;
+  if (x_host) {
+    void* p = cv.take<char>(xbytes);
+    CA_TRY_CUDA(cudaMemcpyAsync(p, X, xbytes, cudaMemcpyHostToDevice, ctx->stream));
+    Xd = p;
+  }
+  const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
+  double* wd = stage(ctx, cv, w, (size_t)d, true, &st);
+  double* zd = z ? stage(ctx, cv, z, (size_t)n, false, &st) : nullptr;
+  double* rho = cv.take<double>((size_t)n);
+  int* idx = cv.take<int>((size_t)o->H * o->b);
+  char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+
+  DenseProblem pb;
+  pb.xfmt = xfmt;
+  pb.A = Xd;
+  pb.N = d;
+  pb.K = n;
+  pb.lda = ld;
+  pb.v = rho;
+  pb.x = wd;
+  pb.yv = nullptr;
+  pb.cG = 1.0 / (double)n;
+  pb.cI = o->lam;
+  pb.cP = 1.0 / (double)n;
+  pb.cY = 0.0;
+  pb.cU = 1.0;
+  pb.y0 = yd;
+  pb.c0 = 1.0;
+  pb.c1 = -1.0;
+  // rho_0 = y - X^T w_0  (z_0 = X^T w_0, Alg. 1-2)
+  CA_TRY(launch_recompute(ctx, pb, rho, yd, 1.0, -1.0));
+  // a1 for all H blocks at once (counter-based, independent of the iterates)
+  k_sample<<<(unsigned)((o->H + 7) / 8), 256, 0, ctx->stream>>>(o->seed, o->h0, o->H, o->b, d, idx);
+  ctx->prof.kernel_launches += 1;
+  CA_TRY_CUDA(cudaGetLastError());
+  CA_TRY(run_dense(ctx, pb, o, idx, work, ctx->arena_bytes - (size_t)(work - (char*)ctx->arena)));
+  if (zd) CA_TRY(launch_recompute(ctx, pb, zd, nullptr, 0.0, 1.0));  // z = X^T w_H
+  if (w_host)
+    CA_TRY_CUDA(cudaMemcpyAsync(w, wd, (size_t)d * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (z_host)
+    CA_TRY_CUDA(cudaMemcpyAsync(z, zd, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  return finish(ctx);
+}
+
+int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long n, long long ld,
+                  const double* y, const ca_opts* o, double* alpha, double* w) {
+  t_cur_ctx = ctx;
+  if (!ctx || !XT || !y || !alpha || !w || d < 1 || n < 1) return CA_ERR_ARG;
+  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32 && xfmt != CA_CSR_F32) return CA_ERR_ARG;
+  CA_TRY(check_opts(o, n));
+  CA_TRY_CUDA(cudaSetDevice(ctx->device));
+  const double ln = o->lam * (double)n;
+  const bool y_host = !is_device_ptr(y), a_host = !is_device_ptr(alpha), w_host = !is_device_ptr(w);
+  size_t need = align256((size_t)o->H * o->b * 4) + 8 * 256;
+  if (y_host) need += align256((size_t)n * 8);
+  if (a_host) need += align256((size_t)n * 8);
+  if (w_host) need += align256((size_t)d * 8);
+
+  if (xfmt == CA_CSR_F32) {
+    const ca_csr* csr = static_cast<const ca_csr*>(XT);
+    if (!csr->rowptr || !csr->col || !csr->val) return CA_ERR_ARG;
+    const bool r_host = !is_device_ptr(csr->rowptr);
+    long long nnz = 0;
+    if (r_host) nnz = csr->rowptr[n];
+    else CA_TRY_CUDA(cudaMemcpy(&nnz, csr->rowptr + n, sizeof(long long), cudaMemcpyDeviceToHost));
+    if (nnz < 0) return CA_ERR_ARG;
+    const bool c_host = !is_device_ptr(csr->col), v_host = !is_device_ptr(csr->val);
+    if (r_host) need += align256((size_t)(n + 1) * 8);
+    if (c_host) need += align256((size_t)nnz * 4);
+    if (v_host) need += align256((size_t)nnz * 4);
+    const int sbm = (int)(std::min<long long>(o->s, o->H) * o->b);
+    const size_t sbp = (size_t)sbm;
+    need += align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + 4096;
+    CA_TRY(ensure_arena(ctx, need));
+    Carve cv{static_cast<char*>(ctx->arena)};
+    bool st;
+    const long long* rp = stage(ctx, cv, csr->rowptr, (size_t)(n + 1), true, &st);
+    const int* col = stage(ctx, cv, csr->col, (size_t)nnz, true, &st);
+    const float* val = stage(ctx, cv, csr->val, (size_t)nnz, true, &st);
+    const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
+    double* ad = stage(ctx, cv, alpha, (size_t)n, true, &st);
+    double* wd = stage(ctx, cv, w, (size_t)d, false, &st);
+    int* idx = cv.take<int>((size_t)o->H * o->b);
+    double* R = cv.take<double>(sbp * sbp);
+    double* pvec = cv.take<double>(sbp);
+    double* delta = cv.take<double>(sbp);
+    CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+    auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
+      k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
+      k_scatter_csr<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, nullptr, n, d,
+                                                                       n, ad, -1.0 / ln, wd,
+                                                                       ctx->d_err);
+      ctx->prof.kernel_launches += 2;
+    };
+    recompute();
+    k_sample<<<(unsigned)((o->H + 7) / 8), 256, 0, ctx->stream>>>(o->seed, o->h0, o->H, o->b, n, idx);
+    CA_TRY_CUDA(cudaGetLastError());
+    const int b = o->b, s = o->s;
+    const long long n_outer = (o->H + s - 1) / s;
+    for (long long k = 0; k < n_outer; ++k) {
+      const int sk = (int)std::min<long long>(s, o->H - (long long)s * k);
+      const int sb = sk * b;
+      const int* ik = idx + (size_t)s * k * b;
+      const long long npairs = (long long)sb * (sb + 1) / 2;
+      const int gg = (int)std::max(1LL, std::min<long long>((npairs + 7) / 8, 8LL * ctx->num_sms));
+      prof_mark(ctx);
+      k_gram_csr<<<gg, 256, 0, ctx->stream>>>(rp, col, val, ik, n, sb, (int)sbp, R, ctx->d_err);
+      k_proj_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb, wd,
+                                                                     pvec, ctx->d_err);
+      prof_mark(ctx);
+      SolveArgs sa{ik, n, b, sk, sb, (int)sbp, 1.0 / ln, 1.0, 1.0, 1.0, ad, yd, delta};
+      k_solve<<<1, 256, (size_t)(sb + b * b + b) * 8, ctx->stream>>>(R, pvec, sa, ctx->d_err);
+      k_scatter_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb,
+                                                                        delta, -1.0 / ln, wd,
+                                                                        ctx->d_err);
+      ctx->prof.kernel_launches += 4;
+      CA_TRY_CUDA(cudaGetLastError());
+      if (o->recompute_every > 0 && (k + 1) % o->recompute_every == 0) recompute();
+    }
+    if (a_host)
+      CA_TRY_CUDA(cudaMemcpyAsync(alpha, ad, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (w_host) CA_TRY_CUDA(cudaMemcpyAsync(w, wd, (size_t)d * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    return finish(ctx);
+  }
+
+  // dense dual: XT is n x d row-major (row i = sample i)
+  if (ld < d) return CA_ERR_ARG;
+  const bool tc = (xfmt == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
+  if (o->prec == CA_GRAM_BF16X3 || o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
+  if (tc) {
+    if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(XT) & 15) != 0) return CA_ERR_ARG;
+    if (std::min<long long>(o->s, o->H) * o->b > gram_tc_max_sb()) return CA_ERR_UNSUPPORTED;
+  }
+  const size_t el = xfmt == CA_DENSE_F64 ? 8 : 4;
+  const bool x_host = !is_device_ptr(XT);
+  const size_t xbytes = (size_t)(n - 1) * ld * el + (size_t)d * el;
+  need += dense_work_bytes(ctx, o, d, xfmt);
+  if (x_host) need += align256(xbytes) + 256;
+  CA_TRY(ensure_arena(ctx, need));
+  Carve cv{static_cast<char*>(ctx->arena)};
+  bool st;
+  const void* Xd = XT;
+  if (x_host) {
+    void* p = cv.take<char>(xbytes);
+    CA_TRY_CUDA(cudaMemcpyAsync(p, XT, xbytes, cudaMemcpyHostToDevice, ctx->stream));
+    Xd = p;
+  }
+  const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
+  double* ad = stage(ctx, cv, alpha, (size_t)n, true, &st);
+  double* wd = stage(ctx, cv, w, (size_t)d, false, &st);
+  int* idx = cv.take<int>((size_t)o->H * o->b);
+  char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  DenseProblem pb;
+  pb.xfmt = xfmt;
+  pb.A = Xd;
+  pb.N = n;
+  pb.K = d;
+  pb.lda = ld;
+  pb.v = wd;
+  pb.x = ad;
+  pb.yv = yd;
+  pb.cG = 1.0 / ln;
+  pb.cI = 1.0;
+  pb.cP = 1.0;
+  pb.cY = 1.0;
+  pb.cU = 1.0 / ln;
+  pb.y0 = nullptr;
+  pb.c0 = 0.0;
+  pb.c1 = -1.0 / ln;
+  CA_TRY(launch_recompute(ctx, pb, wd, nullptr, 0.0, -1.0 / ln));  // w_0 = -X alpha_0/(lambda n)
+  k_sample<<<(unsigned)((o->H + 7) / 8), 256, 0, ctx->stream>>>(o->seed, o->h0, o->H, o->b, n, idx);
+  CA_TRY_CUDA(cudaGetLastError());
+  CA_TRY(run_dense(ctx, pb, o, idx, work, ctx->arena_bytes - (size_t)(work - (char*)ctx->arena)));
+  if (a_host)
+    CA_TRY_CUDA(cudaMemcpyAsync(alpha, ad, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  if (w_host) CA_TRY_CUDA(cudaMemcpyAsync(w, wd, (size_t)d * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  return finish(ctx);
+}
+
+// Profiling of the Gram launches (CUDA events on the context's stream around
+// every a2+a3 launch of the following solves).
+const char* ca_last_error(ca_ctx* ctx) { return ctx ? ctx->last_error : "no context"; }
+
+int ca_profile_enable(ca_ctx* ctx, int on) {
+  if (!ctx) return CA_ERR_ARG;
+  ctx->prof.on = on != 0;
+  ctx->prof.gram_ms = 0.0;
+  ctx->prof.gram_launches = 0;
+  ctx->prof.kernel_launches = 0;
+  return CA_OK;
+}
+
+int ca_profile_read(ca_ctx* ctx, double* gram_ms_total, long long* gram_launches,
+                    long long* kernel_launches) {
+  if (!ctx) return CA_ERR_ARG;
+  if (gram_ms_total) *gram_ms_total = ctx->prof.gram_ms;
+  if (gram_launches) *gram_launches = ctx->prof.gram_launches;
+  if (kernel_launches) *kernel_launches = ctx->prof.kernel_launches;
+  return CA_OK;
+}
+
+int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N, long long K,
+                    long long ld, const int* idx, int sb, const double* v, double* G, double* p) {
+  t_cur_ctx = ctx;
+  if (!ctx || !A || !idx || !v || !G || !p || N < 1 || K < 1 || ld < K || sb < 1 ||
+      sb > kMaxSB)
+    return CA_ERR_ARG;
+  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32) return CA_ERR_ARG;
+  if (prec < CA_GRAM_F64 || prec > CA_GRAM_TF32) return CA_ERR_ARG;
+  const bool tc = (xfmt == CA_DENSE_F32) && (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT);
+  if (tc) {
+    if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return CA_ERR_ARG;
+    if (sb > gram_tc_max_sb()) return CA_ERR_UNSUPPORTED;
+  }
+  for (const void* q : {(const void*)A, (const void*)idx, (const void*)v, (const void*)G,
+                        (const void*)p})
+    if (!is_device_ptr(q)) return CA_ERR_ARG;
+  CA_TRY_CUDA(cudaSetDevice(ctx->device));
+  const GramPlan g = gram_plan(ctx, xfmt, prec, sb, K);
+  const size_t el = g.tc ? 4 : 8;
+  const size_t need = align256((size_t)g.P * g.sbp * g.sbp * el) + align256((size_t)g.P * g.sbp * 8) +
+                      align256((size_t)g.sbp * g.sbp * 8) + align256((size_t)g.sbp * 8) + 1024;
+  CA_TRY(ensure_arena(ctx, need));
+  Carve cv{static_cast<char*>(ctx->arena)};
+  void* part = g.tc ? (void*)cv.take<float>((size_t)g.P * g.sbp * g.sbp)
+                    : (void*)cv.take<double>((size_t)g.P * g.sbp * g.sbp);
+  double* ppart = cv.take<double>((size_t)g.P * g.sbp);
+  double* R = cv.take<double>((size_t)g.sbp * g.sbp);
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, part, ppart));
+  SolveArgs sa{idx, N, 1, 0, sb, g.sbp, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
+  launch_reduce_solve(ctx, g, part, ppart, R, p, sa);
+  k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(R, g.sbp, sb, G);
+  CA_TRY_CUDA(cudaGetLastError());
+  return finish(ctx);
+}
+
+int ca_selftest_wait_timeout(ca_ctx* ctx, long long limit_ns) {
+  t_cur_ctx = ctx;
+  if (!ctx || limit_ns < 1 || limit_ns > 1000000000LL) return CA_ERR_ARG;
+  CA_TRY_CUDA(cudaSetDevice(ctx->device));
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  k_selftest_wait<<<1, 32, 0, ctx->stream>>>((unsigned long long)limit_ns, ctx->d_err);
+  CA_TRY_CUDA(cudaGetLastError());
+  return finish(ctx);
+}
+
+}  // extern "C"

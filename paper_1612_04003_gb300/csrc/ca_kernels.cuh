@@ -1,0 +1,50 @@
+// ca_kernels.cuh -- declarations of the CA-BCD / CA-BDCD device kernels.
+#pragma once
+#include "ca_common.cuh"
+
+__global__ void k_sample(unsigned long long seed, long long h0, long long H, int b, long long N,
+                         int* out);
+
+// Host launchers of the templated kernels (defined in ca_kernels.cu; the
+// templates are launched only from their own translation unit).
+void launch_gram_simt(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
+                      long long N, long long K, const int* idx, int sb, const double* v,
+                      long long chunks_per_split, int sbp, double* part, double* ppart,
+                      unsigned* err);
+void launch_reduce_solve_k(bool f32_partials, int grid, size_t smem, cudaStream_t st,
+                           const void* part, const double* ppart, int P, int sbp, double* R,
+                           double* pvec, const SolveArgs& sa, unsigned* ticket, unsigned* err);
+void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
+                         long long lda, long long N, long long K, const int* idx, int sb,
+                         const double* delta, double cU, double* v, unsigned* err);
+void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
+                            long long N, long long K, const double* x, double c1,
+                            long long rows_per_split, double* v);
+int set_solve_smem_limit(int bytes);
+
+__global__ void k_solve(const double* R, const double* pvec, SolveArgs sa, unsigned* err);
+
+__global__ void k_axpby_init(const double* y0, double c0, long long K, double* v);
+
+__global__ void k_gram_csr(const long long* rowptr, const int* col, const float* val,
+                           const int* idx, long long nrows, int sb, int ldr, double* R,
+                           unsigned* err);
+__global__ void k_proj_csr(const long long* rowptr, const int* col, const float* val,
+                           const int* idx, long long nrows, long long ncols, int sb,
+                           const double* w, double* pvec, unsigned* err);
+__global__ void k_scatter_csr(const long long* rowptr, const int* col, const float* val,
+                              const int* idx, long long nrows_total, long long ncols,
+                              long long nlist, const double* coef, double c, double* v,
+                              unsigned* err);
+
+__global__ void k_selftest_wait(unsigned long long limit_ns, unsigned* err);
+__global__ void k_symmetrize(const double* R, int ldr, int sb, double* G);
+
+// tcgen05 Gram (ca_gram_tc.cu): host-side launcher.  Returns a cudaError_t.
+// Computes FP32 partials part[c][i][j] (c < P, row stride sbp) of
+// sum_{k in split c} Y[i][k] Y[j][k] for the tiles covering j <= i, and FP64
+// partials ppart[c][i] of sum_k Y[i][k] v[k].  sbp is 128 (sb <= 128) or 256.
+int launch_gram_tc(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
+                   const double* v, int P, int sbp, float* part, double* ppart, unsigned* err,
+                   int three_pass, cudaStream_t stream);
+int gram_tc_max_sb();

@@ -1,0 +1,354 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GB300).
+
+Element-wise comparisons on the same seeded inputs.  Tolerances (relative
+2-norm error of the iterates after H block updates):
+  * 1e-10 for FP64 X with the FP64 Gram;
+  * 1e-5  for FP32 X (TF32 or 3xTF32 tensor-core Gram, FP32 products in the
+    projection / update, FP64 vectors and solves).
+Sampled indices must match bit for bit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+def _rel(a, b):
+    a = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1612_04003_gb300 as ca
+    ca.build()
+    c = ca.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda().contiguous()
+
+
+# ---------------------------------------------------------------------------
+# a1 sampler: bit-exact against the oracle's implementation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,h0,H,b,N", [
+    (42, 0, 200, 4, 64), (1, 12345, 64, 8, 4096), (7, 2**40, 16, 3, 10), (9, 0, 5, 64, 64),
+    (3, 5, 40, 37, 100), (11, 0, 3, 1, 1), (2024, 77, 50, 128, 131072), (5, 0, 4, 300, 301)])
+def test_sampler_bit_exact(ctx, seed, h0, H, b, N):
+    out = torch.empty((H, b), dtype=torch.int32, device="cuda")
+    ctx.ca_sample_indices(seed, h0, H, b, N, out)
+    ref = oracle.sample_blocks(seed, h0, H, b, N)
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_sampler_host_output(ctx):
+    out = np.zeros((10, 8), dtype=np.int32)
+    ctx.ca_sample_indices(42, 3, 10, 8, 4096, out)
+    assert np.array_equal(out, oracle.sample_blocks(42, 3, 10, 8, 4096))
+
+
+# ---------------------------------------------------------------------------
+# Primal CA-BCD, FP64 X (tiny dense workload: X 64 x 1024, lambda 1e-3, b 4, H 200)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.tiny_primal(d=64, n=1024, seed=1)
+
+
+@pytest.mark.parametrize("s", [1, 4, 7, 16])
+def test_primal_f64_tiny(ctx, tiny, s):
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    z = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w, z, b=4, s=s, H=200, lam=1e-3, seed=42, prec="f64")
+    w_ref, z_ref = oracle.ca_bcd(tiny.X, tiny.y, 1e-3, b=4, s=s, H=200, seed=42)
+    assert _rel(w, w_ref) < TOL64
+    assert _rel(z, z_ref) < TOL64
+
+
+def test_primal_f64_full_block_is_closed_form(ctx, tiny):
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w, b=64, s=1, H=1, lam=1e-3, seed=42, prec="f64")
+    assert _rel(w, oracle.closed_form(tiny.X, tiny.y, 1e-3)) < 1e-10
+
+
+def test_primal_f64_repeats_short_last_step_resume(ctx, tiny):
+    """Indices repeating across blocks (b = 40 of d = 64), H not a multiple of
+    s, a non-zero w0 / h0, and periodic recomputation."""
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    w0 = np.random.default_rng(3).standard_normal(64)
+    w = _dev(w0)
+    ctx.ca_bcd_solve(X, y, w, b=40, s=6, H=31, lam=1e-3, seed=3, h0=17, prec="f64",
+                     recompute_every=2)
+    w_ref, _ = oracle.ca_bcd(tiny.X, tiny.y, 1e-3, b=40, s=6, H=31, seed=3, h0=17, w0=w0,
+                             recompute_every=2)
+    assert _rel(w, w_ref) < TOL64
+
+
+def test_primal_f64_ragged_ld(ctx):
+    """n not a multiple of the 32-column chunk, leading dimension > n, sb
+    spanning several 64-row tiles."""
+    p = synth.dense_primal(d=200, n=1500, cond=1e2, seed=4, dtype=np.float64)
+    ld = 1537
+    Xp = np.zeros((200, ld))
+    Xp[:, :1500] = p.X
+    X = _dev(Xp)
+    y = _dev(p.y)
+    w = torch.zeros(200, dtype=torch.float64, device="cuda")
+    z = torch.zeros(1500, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X[:, :1500].contiguous(), y, w, z, b=10, s=15, H=120, lam=1e-3, seed=8,
+                     prec="f64")
+    w_ref, z_ref = oracle.ca_bcd(p.X, p.y, 1e-3, b=10, s=15, H=120, seed=8)
+    assert _rel(w, w_ref) < TOL64 and _rel(z, z_ref) < TOL64
+    # the same through an explicit leading dimension
+    w2 = torch.zeros(200, dtype=torch.float64, device="cuda")
+    import paper_1612_04003_gb300 as ca
+    o = ca.Context._opts(10, 15, 120, 1e-3, 8, "f64", 0, 0)
+    import ctypes
+    st = ctx._lib.ca_bcd_solve(ctx.handle, ca.CA_DENSE_F64, X.data_ptr(), 200, 1500, ld,
+                               y.data_ptr(), ctypes.byref(o), w2.data_ptr(), None)
+    assert st == 0
+    assert _rel(w2, w_ref) < TOL64
+
+
+# ---------------------------------------------------------------------------
+# Primal CA-BCD, FP32 X, tensor-core Gram (TF32 and 3xTF32)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def mid32():
+    """Dense primal, geometric row scaling (cond 1e3), lambda 1e-4; n with a
+    ragged 32-column tail."""
+    return synth.dense_primal(d=512, n=8205, cond=1e3, seed=2)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
+@pytest.mark.parametrize("b,s", [(8, 1), (8, 4), (8, 13), (8, 16), (8, 17), (8, 32), (32, 4),
+                                 (32, 8), (3, 7)])
+def test_primal_f32_tc(ctx, mid32, prec, b, s):
+    X64 = mid32.X.astype(np.float64)
+    d, n = mid32.X.shape
+    # keep the leading dimension a multiple of 4 (16-byte rows for cp.async)
+    ld = (n + 3) // 4 * 4
+    Xp = np.zeros((d, ld), dtype=np.float32)
+    Xp[:, :n] = mid32.X
+    X = _dev(Xp)
+    y = _dev(mid32.y)
+    w = torch.zeros(d, dtype=torch.float64, device="cuda")
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    H = 256
+    ctx.ca_bcd_solve(X, y, w, z, b=b, s=s, H=H, lam=1e-4, seed=42, prec=prec, n=n)
+    w_ref, z_ref = oracle.ca_bcd(X64, mid32.y, 1e-4, b=b, s=s, H=H, seed=42)
+    assert _rel(w, w_ref) < TOL32
+    assert _rel(z, z_ref) < TOL32
+
+
+def test_primal_f32_simt_f64_gram(ctx, mid32):
+    X = _dev(mid32.X)
+    d, n = mid32.X.shape
+    y = _dev(mid32.y)
+    w = torch.zeros(d, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w, b=8, s=8, H=128, lam=1e-4, seed=42, prec="f64")
+    w_ref, _ = oracle.ca_bcd(mid32.X.astype(np.float64), mid32.y, 1e-4, b=8, s=8, H=128, seed=42)
+    assert _rel(w, w_ref) < TOL32
+
+
+def test_primal_tc_s_equals_1_iterates(ctx, mid32):
+    """Sec. 3.1: CA-BCD (s = 16) and BCD (s = 1) give the same iterates up to
+    rounding on the device as well."""
+    X = _dev(mid32.X[:, :8192])
+    y = _dev(mid32.y[:8192])
+    outs = []
+    for s in (1, 16):
+        w = torch.zeros(512, dtype=torch.float64, device="cuda")
+        ctx.ca_bcd_solve(X, y, w, b=8, s=s, H=256, lam=1e-4, seed=5, prec="3xtf32")
+        outs.append(w.cpu().numpy())
+    assert _rel(outs[1], outs[0]) < TOL32
+
+
+def test_primal_host_buffers_match_device(ctx, mid32):
+    """Host (numpy) arrays are staged by the library: same result."""
+    Xh = np.ascontiguousarray(mid32.X[:, :8192])
+    yh = np.ascontiguousarray(mid32.y[:8192])
+    wh = np.zeros(512)
+    zh = np.zeros(8192)
+    ctx.ca_bcd_solve(Xh, yh, wh, zh, b=8, s=8, H=128, lam=1e-4, seed=5, prec="tf32")
+    w = torch.zeros(512, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(_dev(Xh), _dev(yh), w, b=8, s=8, H=128, lam=1e-4, seed=5, prec="tf32")
+    assert np.array_equal(wh, w.cpu().numpy())
+    w_ref, z_ref = oracle.ca_bcd(Xh.astype(np.float64), yh, 1e-4, b=8, s=8, H=128, seed=5)
+    assert _rel(wh, w_ref) < TOL32 and _rel(zh, z_ref) < TOL32
+
+
+# ---------------------------------------------------------------------------
+# Dual CA-BDCD
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def wide():
+    return synth.dense_dual(d=300, n=120, seed=4)
+
+
+@pytest.mark.parametrize("s", [1, 5, 13])
+def test_dual_dense_f64(ctx, wide, s):
+    XT = _dev(wide.X.T)
+    y = _dev(wide.y)
+    a = torch.zeros(120, dtype=torch.float64, device="cuda")
+    w = torch.zeros(300, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(XT, y, a, w, b=6, s=s, H=150, lam=1e-2, seed=9, prec="f64")
+    a_ref, w_ref = oracle.ca_bdcd(wide.X, wide.y, 1e-2, b=6, s=s, H=150, seed=9)
+    assert _rel(a, a_ref) < TOL64 and _rel(w, w_ref) < TOL64
+
+
+def test_dual_dense_f64_full_block(ctx, wide):
+    XT = _dev(wide.X.T)
+    y = _dev(wide.y)
+    a = torch.zeros(120, dtype=torch.float64, device="cuda")
+    w = torch.zeros(300, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(XT, y, a, w, b=120, s=1, H=1, lam=1e-2, seed=1, prec="f64")
+    X = wide.X
+    wstar = np.linalg.solve(X @ X.T / 120 + 1e-2 * np.eye(300), X @ wide.y / 120)
+    assert _rel(w, wstar) < 1e-9
+    assert _rel(a, X.T @ wstar - wide.y) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
+def test_dual_dense_f32_tc(ctx, prec):
+    p = synth.dense_dual(d=1028, n=400, seed=6)
+    X32 = p.X.astype(np.float32)
+    XT = _dev(np.ascontiguousarray(X32.T))
+    y = _dev(p.y)
+    a = torch.zeros(400, dtype=torch.float64, device="cuda")
+    w = torch.zeros(1028, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(XT, y, a, w, b=8, s=16, H=256, lam=1e-2, seed=2, prec=prec)
+    a_ref, w_ref = oracle.ca_bdcd(X32.astype(np.float64), p.y, 1e-2, b=8, s=16, H=256, seed=2)
+    assert _rel(a, a_ref) < TOL32 and _rel(w, w_ref) < TOL32
+
+
+@pytest.fixture(scope="module")
+def sparse_small():
+    return synth.sparse_dual(d=4000, n=600, density=0.01, seed=3)
+
+
+@pytest.mark.parametrize("b,s", [(8, 1), (8, 8), (8, 32), (5, 3)])
+def test_dual_csr(ctx, sparse_small, b, s):
+    sp = sparse_small
+    rp, col, val = _dev(sp.rowptr), _dev(sp.col), _dev(sp.val)
+    y = _dev(sp.y)
+    a = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(sp.d, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve((rp, col, val), y, a, w, b=b, s=s, H=96, lam=1e-3, seed=4, d=sp.d)
+    A = oracle.CSR(sp.rowptr, sp.col, sp.val.astype(np.float64), sp.d)
+    a_ref, w_ref = oracle.ca_bdcd(A, sp.y, 1e-3, b=b, s=s, H=96, seed=4)
+    assert _rel(a, a_ref) < TOL64 and _rel(w, w_ref) < TOL64
+
+
+def test_dual_csr_host_arrays_and_recompute(ctx, sparse_small):
+    sp = sparse_small
+    a = np.zeros(sp.n)
+    w = np.zeros(sp.d)
+    ctx.ca_bdcd_solve((sp.rowptr, sp.col, sp.val), sp.y, a, w, b=8, s=8, H=96, lam=1e-3, seed=4,
+                      d=sp.d, recompute_every=3)
+    A = oracle.CSR(sp.rowptr, sp.col, sp.val.astype(np.float64), sp.d)
+    a_ref, w_ref = oracle.ca_bdcd(A, sp.y, 1e-3, b=8, s=8, H=96, seed=4, recompute_every=3)
+    assert _rel(a, a_ref) < TOL64 and _rel(w, w_ref) < TOL64
+
+
+# ---------------------------------------------------------------------------
+# Error paths
+# ---------------------------------------------------------------------------
+def test_errors(ctx, tiny):
+    import paper_1612_04003_gb300 as ca
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(ca.CaError) as e:
+        ctx.ca_bcd_solve(X, y, w, b=65, s=1, H=10, lam=1e-3)
+    assert e.value.status == ca.CA_ERR_ARG
+    with pytest.raises(ca.CaError) as e:
+        ctx.ca_bcd_solve(X, y, w, b=4, s=1, H=10, lam=0.0)
+    assert e.value.status == ca.CA_ERR_ARG
+    with pytest.raises(ca.CaError) as e:
+        ctx.ca_bcd_solve(X, y, w, b=4, s=1, H=0, lam=1e-3)
+    assert e.value.status == ca.CA_ERR_ARG
+    X32 = X.float().contiguous()
+    with pytest.raises(ca.CaError) as e:  # s*b beyond the tensor-core tile
+        ctx.ca_bcd_solve(X32, y, w, b=32, s=9, H=288, lam=1e-3, prec="tf32")
+    assert e.value.status == ca.CA_ERR_UNSUPPORTED
+    Xbad = X.clone()
+    Xbad[:, 5] = float("nan")
+    with pytest.raises(ca.CaError) as e:
+        ctx.ca_bcd_solve(Xbad, y, w, b=64, s=1, H=1, lam=1e-3, prec="f64")
+    assert e.value.status in (ca.CA_ERR_NONFINITE, ca.CA_ERR_NOT_SPD)
+    # the context stays usable after errors
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w, b=4, s=4, H=200, lam=1e-3, seed=42, prec="f64")
+    w_ref, _ = oracle.ca_bcd(tiny.X, tiny.y, 1e-3, b=4, s=4, H=200, seed=42)
+    assert _rel(w, w_ref) < TOL64
+
+
+def test_bounded_wait_times_out_and_context_survives(ctx, tiny):
+    import paper_1612_04003_gb300 as ca
+    assert ctx.ca_selftest_wait_timeout(50_000_000) == ca.CA_ERR_TIMEOUT
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w, b=4, s=4, H=40, lam=1e-3, seed=42, prec="f64")
+    w_ref, _ = oracle.ca_bcd(tiny.X, tiny.y, 1e-3, b=4, s=4, H=40, seed=42)
+    assert _rel(w, w_ref) < TOL64
+
+
+# ---------------------------------------------------------------------------
+# a2+a3 alone: Gram matrix and projection of given rows vs a float64 reference
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def gram_data():
+    rng = np.random.default_rng(17)
+    N, K = 700, 8205                      # K has a ragged 32-column tail
+    ld = 8208
+    A = np.zeros((N, ld), dtype=np.float32)
+    A[:, :K] = (rng.standard_normal((N, K)) * (10.0 ** rng.uniform(-2, 1, size=(N, 1)))).astype(
+        np.float32)
+    v = rng.standard_normal(K)
+    return A, K, ld, v
+
+
+@pytest.mark.parametrize("prec,tolG,tolp", [("f64", 1e-13, 1e-13), ("3xtf32", 2e-6, 1e-6),
+                                            ("tf32", 3e-3, 1e-6)])
+@pytest.mark.parametrize("sb", [1, 8, 32, 100, 128, 129, 136, 256])
+def test_gram_project_kernel(ctx, gram_data, prec, tolG, tolp, sb):
+    A, K, ld, v = gram_data
+    rng = np.random.default_rng(sb)
+    idx = rng.integers(0, A.shape[0], size=sb).astype(np.int32)  # repeats allowed
+    if sb > 4:
+        idx[3] = idx[1]
+    Ad = _dev(A)
+    G = torch.zeros((sb, sb), dtype=torch.float64, device="cuda")
+    p = torch.zeros(sb, dtype=torch.float64, device="cuda")
+    import paper_1612_04003_gb300 as ca
+    import ctypes
+    st = ctx._lib.ca_gram_project(ctx.handle, ca.CA_DENSE_F32, ca.PREC[prec], Ad.data_ptr(),
+                                  A.shape[0], K, ld, _dev(idx).data_ptr(), sb,
+                                  _dev(v).data_ptr(), G.data_ptr(), p.data_ptr())
+    assert st == 0, ca.status_str(st)
+    Y = A[idx, :K].astype(np.float64)
+    G_ref = Y @ Y.T
+    p_ref = Y @ v
+    nrm = np.sqrt(np.diag(G_ref))
+    Gerr = np.abs(G.cpu().numpy() - G_ref) / np.outer(nrm, nrm)
+    assert Gerr.max() < tolG, Gerr.max()
+    perr = np.abs(p.cpu().numpy() - p_ref) / (nrm * np.linalg.norm(v))
+    assert perr.max() < tolp, perr.max()
