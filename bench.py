@@ -2,8 +2,8 @@
 
 Workload (the dense primal FP32 configuration): X 4096 x 262144 FP32 with
 geometrically scaled rows (condition 1e3), y = X^T w_true + 1% noise,
-lambda = 1e-4, b = 8, s = 32, H = 4096 block updates, TF32 tensor-core Gram,
-FP64 solves.  One step = one full solve (sampling, H/s outer steps of
+lambda = 1e-4, b = 8, s = 32, H = 4096 block updates, FP32-faithful Gram on
+the tensor cores (3xTF32 split products, FP32 accumulation), FP64 solves.  One step = one full solve (sampling, H/s outer steps of
 gather+Gram+projection, inner solves, deferred update, and the final
 z = X^T w_H pass) with X resident in HBM.  X (4 GiB) is larger than L2.
 
@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 METRIC = "CA-BCD block-updates/s"
 UNIT = "block-updates/s"
 D, N_SAMPLES, COND, LAM, B, S, H = 4096, 262144, 1e3, 1e-4, 8, 32, 4096
-PREC = "tf32"
+PREC = "3xtf32"
 
 
 def workload_config(d=D, n=N_SAMPLES, b=B, s=S, h=H, prec=PREC):
@@ -269,16 +269,20 @@ def main():
     peaks, peak_kind = _peaks()
     sb = S * B
     gram_ms = prof["gram_ms"] / max(1, prof["gram_launches"])
+    breakdown = {c: {"ms_per_step": prof[f"{c}_ms"] / args.steps,
+                     "share": prof[f"{c}_ms"] / max(ms, 1e-9)}
+                 for c in ("gram", "solve", "update", "other")}
     alg_bytes = sb * N_SAMPLES * 4 + N_SAMPLES * 8          # Y rows + the projection vector
     achieved = alg_bytes / (gram_ms * 1e-3) / 1e9
     trec = _traffic_record(os.path.join(ROOT, "paper_1612_04003_gb300", "csrc", "ca_gram_tc.cu"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"],
             "traffic": trec["traffic_bytes_per_launch"] if trec else None,
-            "kernel": "k_gram_tc<256,tf32> (gather + Gram + projection)",
+            "kernel": f"k_gram_tc<256,{PREC}> (gather + Gram + projection)",
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": gram_ms,
             "launches": prof["gram_launches"], "peak_source": f"hbm_gbs ({peak_kind})",
             "gram_share_of_step": prof["gram_ms"] / max(ms, 1e-9)}
+    roof["breakdown"] = breakdown
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     Xh = torch.empty((D, N_SAMPLES), dtype=torch.float32, pin_memory=True)
@@ -304,11 +308,13 @@ def main():
     # s sweep (same data, fewer steps): s-step against s = 1
     sweep = []
     if not args.no_sweep:
-        for (b_, s_) in [(8, 1), (8, 4), (8, 8), (8, 16), (8, 32), (32, 1), (32, 4), (32, 8)]:
-            nst = 2 if s_ == 1 else 4
-            time_solves(ctx, X, y, w, z, 1, stream, b=b_, s=s_)
-            t = time_solves(ctx, X, y, w, z, nst, stream, b=b_, s=s_) / nst
-            sweep.append({"b": b_, "s": s_, "ms_per_step": t, "block_updates_per_s": H / (t * 1e-3)})
+        for prec_ in ("3xtf32", "tf32"):
+            for (b_, s_) in [(8, 1), (8, 4), (8, 8), (8, 16), (8, 32), (32, 1), (32, 4), (32, 8)]:
+                nst = 2 if s_ == 1 else 4
+                time_solves(ctx, X, y, w, z, 1, stream, b=b_, s=s_, prec=prec_)
+                t = time_solves(ctx, X, y, w, z, nst, stream, b=b_, s=s_, prec=prec_) / nst
+                sweep.append({"gram": prec_, "b": b_, "s": s_, "ms_per_step": t,
+                              "block_updates_per_s": H / (t * 1e-3)})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -319,7 +325,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "tf32", "data": "synthetic", "config": workload_config(),
+            "dtype": "3xtf32 (fp32-faithful)", "data": "synthetic", "config": workload_config(),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(prof["kernel_launches"]),
             "clocks": clocks.summary(), "sweep": sweep,

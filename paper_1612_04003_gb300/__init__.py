@@ -84,7 +84,8 @@ def load():
     lib.ca_bcd_destroy.restype = None
     lib.ca_profile_enable.argtypes = [vp, i32]
     lib.ca_profile_enable.restype = i32
-    lib.ca_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ca_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i64)]
     lib.ca_profile_read.restype = i32
     lib.ca_last_error.argtypes = [vp]
     lib.ca_last_error.restype = ctypes.c_char_p
@@ -238,9 +239,17 @@ class Context:
         if st != CA_OK:
             raise CaError(st, "ca_profile_enable")
 
+    PROFILE_CLASSES = ("gram", "solve", "update", "other")
+
     def ca_profile_read(self):
-        ms, g, k = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
-        st = self._lib.ca_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(g), ctypes.byref(k))
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_longlong * 4)()
+        k = ctypes.c_longlong()
+        st = self._lib.ca_profile_read(self.handle, ms, n, ctypes.byref(k))
         if st != CA_OK:
             raise CaError(st, "ca_profile_read")
-        return {"gram_ms": ms.value, "gram_launches": g.value, "kernel_launches": k.value}
+        out = {"kernel_launches": k.value}
+        for i, name in enumerate(self.PROFILE_CLASSES):
+            out[f"{name}_ms"] = ms[i]
+            out[f"{name}_launches"] = n[i]
+        return out

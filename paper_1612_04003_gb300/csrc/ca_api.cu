@@ -16,11 +16,14 @@ constexpr int kMaxB = 128;          // b x b block held in shared memory by the 
 constexpr int kMaxSB = 1024;        // s*b right-hand sides held in shared memory
 constexpr int kSolveSmemMax = 200 * 1024;
 
+// Kernel classes timed by the profiling hooks.
+enum { PC_GRAM = 0, PC_SOLVE = 1, PC_UPDATE = 2, PC_OTHER = 3, PC_N = 4 };
+
 struct Profile {
   bool on = false;
-  std::vector<cudaEvent_t> ev;      // pairs around each Gram launch
-  double gram_ms = 0.0;
-  long long gram_launches = 0;
+  std::vector<std::pair<int, cudaEvent_t>> ev;  // (class, start) / (class, stop) pairs
+  double ms[PC_N] = {0, 0, 0, 0};
+  long long launches[PC_N] = {0, 0, 0, 0};
   long long kernel_launches = 0;
 };
 
@@ -122,22 +125,23 @@ int finish(ca_ctx* ctx) {
   if (ctx->prof.on) {
     for (size_t i = 0; i + 1 < ctx->prof.ev.size(); i += 2) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ctx->prof.ev[i], ctx->prof.ev[i + 1]);
-      ctx->prof.gram_ms += ms;
-      ctx->prof.gram_launches += 1;
+      cudaEventElapsedTime(&ms, ctx->prof.ev[i].second, ctx->prof.ev[i + 1].second);
+      ctx->prof.ms[ctx->prof.ev[i].first] += ms;
+      ctx->prof.launches[ctx->prof.ev[i].first] += 1;
     }
-    for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
+    for (auto& e : ctx->prof.ev) cudaEventDestroy(e.second);
     ctx->prof.ev.clear();
   }
   return status_from_err(*ctx->h_err);
 }
 
-void prof_mark(ca_ctx* ctx) {
+// Record an event of class cls on the context's stream (profiling only).
+void prof_mark(ca_ctx* ctx, int cls) {
   if (!ctx->prof.on) return;
   cudaEvent_t e;
   if (cudaEventCreate(&e) != cudaSuccess) return;
   cudaEventRecord(e, ctx->stream);
-  ctx->prof.ev.push_back(e);
+  ctx->prof.ev.emplace_back(cls, e);
 }
 
 int check_opts(const ca_opts* o, long long N) {
@@ -159,7 +163,9 @@ struct DenseProblem {
   const void* A;            // N x K row-major, leading dim lda (device)
   long long N, K, lda;
   double* v;                // K: projection vector (rho or w), device
+  float2* v2;               // its (hi, lo) FP32 split, zero-padded to a multiple of 32
   double* x;                // N: variable updated by the solves (w or alpha), device
+  float2* x2;               // N: scratch for the (hi, lo) FP32 split of x (recompute)
   const double* yv;         // dual: y (device), primal: nullptr
   double cG, cI, cP, cY, cU;
   // recompute of v: v = c0 * y0 + c1 * sum_r A[r] x[r]
@@ -170,16 +176,27 @@ struct DenseProblem {
 int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const double* y0,
                      double c0, double c1) {
   const long long K = pb.K, N = pb.N;
-  k_axpby_init<<<(unsigned)((K + 255) / 256), 256, 0, ctx->stream>>>(y0, c0, K, vout);
   const long long gx = (K + 1023) / 1024;
   long long ysplit = (2LL * ctx->num_sms + gx - 1) / gx;
   ysplit = std::max(1LL, std::min(ysplit, (N + 63) / 64));
   const long long rps = (N + ysplit - 1) / ysplit;
   ysplit = (N + rps - 1) / rps;
   dim3 grid((unsigned)gx, (unsigned)ysplit);
-  launch_recompute_dense(pb.xfmt == CA_DENSE_F64, grid, ctx->stream, pb.A, pb.lda, N, K, pb.x, c1,
-                         rps, vout);
+  prof_mark(ctx, PC_OTHER);
+  k_axpby_init<<<(unsigned)((K + 255) / 256), 256, 0, ctx->stream>>>(y0, c0, K, vout);
+  if (pb.xfmt == CA_DENSE_F32) {
+    k_split<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(pb.x, N, N, pb.x2);
+    ctx->prof.kernel_launches += 1;
+  }
+  launch_recompute_dense(pb.xfmt == CA_DENSE_F64, grid, ctx->stream, pb.A, pb.lda, N, K, pb.x, pb.x2,
+                         c1, rps, vout);
   ctx->prof.kernel_launches += 2;
+  if (vout == pb.v && pb.v2) {
+    const long long Kp = (K + 31) / 32 * 32;
+    k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, ctx->stream>>>(pb.v, K, Kp, pb.v2);
+    ctx->prof.kernel_launches += 1;
+  }
+  prof_mark(ctx, PC_OTHER);
   return cuda_status(cudaGetLastError());
 }
 
@@ -214,9 +231,10 @@ GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
 
 // a2+a3: split-K partials of Y Y^T and Y v for the sampled rows idx[0..sb).
 int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long long lda, long long N,
-                long long K, const int* idx, int sb, const double* v, void* part, double* ppart) {
+                long long K, const int* idx, int sb, const double* v, const float2* v2, void* part,
+                double* ppart) {
   if (g.tc) {
-    const int e = launch_gram_tc(static_cast<const float*>(A), lda, N, K, idx, sb, v, g.P, g.sbp,
+    const int e = launch_gram_tc(static_cast<const float*>(A), lda, N, K, idx, sb, v2, g.P, g.sbp,
                                  static_cast<float*>(part), ppart, ctx->d_err, g.three, ctx->stream);
     return e == 0 ? CA_OK : CA_ERR_CUDA;
   }
@@ -225,14 +243,39 @@ int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long lo
   return cuda_status(cudaGetLastError());
 }
 
-// a4 entry: reduce the partials to R, p, then (s_cur > 0) the inner solves.
+bool fast_solve(int b, int sb) { return b <= CA_FAST_B && sb <= CA_FAST_SB; }
+
+size_t chain_smem(int b, int sb) { return (size_t)sb * b * 8 + (size_t)sb * 16 + 32 * 8 + (size_t)sb * 4 + 64; }
+
+// a4: the chain (fast form) or the general block forward substitution, from R, p (and Ginv).
+void launch_solve(ca_ctx* ctx, const double* R, const double* pvec, const double* Ginv,
+                  const SolveArgs& sa) {
+  if (fast_solve(sa.b, sa.sb)) {
+    const int rw = (sa.b + 7) / 8;
+    launch_chain(rw <= 1 ? 1 : (rw <= 2 ? 2 : 4), chain_smem(sa.b, sa.sb), ctx->stream, R, pvec, Ginv,
+                 sa, ctx->d_err);
+  } else {
+    k_solve<<<1, 256, (size_t)(sa.sb + sa.b * sa.b + sa.b) * sizeof(double), ctx->stream>>>(
+        R, pvec, sa, ctx->d_err);
+  }
+}
+
+// a4 entry: reduce the partials to R, p (+ the inverted diagonal blocks), then
+// (s_cur > 0) the inner solves.
 void launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const double* ppart,
-                         double* R, double* pvec, const SolveArgs& sa) {
+                         double* R, double* pvec, double* Ginv, const SolveArgs& sa) {
+  const bool fast = sa.s_cur > 0 && fast_solve(sa.b, sa.sb);
+  const int ndiag = fast ? sa.s_cur : 0;
   const long long entries = (long long)sa.sb * (sa.sb + 1) / 2 + sa.sb;
-  const int G = (int)std::max(1LL, std::min<long long>((entries + 255) / 256, 2LL * ctx->num_sms));
-  const size_t ssm = (size_t)(sa.sb + sa.b * sa.b + sa.b) * sizeof(double);
-  launch_reduce_solve_k(g.tc, G, ssm, ctx->stream, part, ppart, g.P, g.sbp, R, pvec, sa,
-                        ctx->d_ticket, ctx->d_err);
+  const int G = ndiag + (int)std::max(1LL, std::min<long long>((entries + 31) / 32, 4LL * ctx->num_sms));
+  const size_t rsm = fast ? (size_t)2 * sa.b * sa.b * sizeof(double) : 0;
+  launch_reduce(g.tc, G, rsm, ctx->stream, part, ppart, g.P, g.sbp, R, pvec, Ginv, ndiag, sa,
+                ctx->d_err);
+  ctx->prof.kernel_launches += 1;
+  if (sa.s_cur > 0) {
+    launch_solve(ctx, R, pvec, Ginv, sa);
+    ctx->prof.kernel_launches += 1;
+  }
 }
 
 int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_all, char* work,
@@ -251,6 +294,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   double* R = cv.take<double>((size_t)sbp * sbp);
   double* pvec = cv.take<double>((size_t)sbp);
   double* delta = cv.take<double>((size_t)sbp);
+  double* Ginv = cv.take<double>((size_t)sbp * CA_FAST_B);
 
   const long long n_outer = (H + s - 1) / s;
   for (long long k = 0; k < n_outer; ++k) {
@@ -258,18 +302,22 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     const int sb = sk * b;
     const int* idx = idx_all + (size_t)s * k * b;
     // a2 + a3
-    prof_mark(ctx);
-    CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, part, ppart));
-    prof_mark(ctx);
+    prof_mark(ctx, PC_GRAM);
+    CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart));
+    prof_mark(ctx, PC_GRAM);
     // a4 (reduce of the split-K partials, then the s unrolled solves)
     SolveArgs sa{idx, pb.N, b, sk, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, delta};
-    launch_reduce_solve(ctx, g, part, ppart, R, pvec, sa);
+    prof_mark(ctx, PC_SOLVE);
+    launch_reduce_solve(ctx, g, part, ppart, R, pvec, Ginv, sa);
+    prof_mark(ctx, PC_SOLVE);
     // a5
     const size_t usm = align256((size_t)sb * 4) + (size_t)sb * 8;  // sidx | delta
-    const unsigned ug = (unsigned)((K + 1023) / 1024);
+    const unsigned ug = (unsigned)((K + 255) / 256);
+    prof_mark(ctx, PC_UPDATE);
     launch_update_dense(pb.xfmt == CA_DENSE_F64, ug, usm, ctx->stream, pb.A, pb.lda, pb.N, K, idx, sb,
-                        delta, pb.cU, pb.v, ctx->d_err);
-    ctx->prof.kernel_launches += 3;
+                        delta, pb.cU, pb.v, pb.v2, ctx->d_err);
+    prof_mark(ctx, PC_UPDATE);
+    ctx->prof.kernel_launches += 2;
     CA_TRY_CUDA(cudaGetLastError());
     // a6
     if (o->recompute_every > 0 && (k + 1) % o->recompute_every == 0)
@@ -294,7 +342,7 @@ size_t dense_work_bytes(ca_ctx* ctx, const ca_opts* o, long long K, int xfmt) {
     el = 8;
   }
   return align256(P * sbp * sbp * el) + align256(P * sbp * 8) + align256(sbp * sbp * 8) +
-         2 * align256(sbp * 8) + 4096;
+         2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
 }
 
 // Stage a caller array on the device (copy in when `in`), return the device pointer.
@@ -369,7 +417,7 @@ void ca_bcd_destroy(ca_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (cudaEvent_t e : ctx->prof.ev) cudaEventDestroy(e);
+  for (auto& e : ctx->prof.ev) cudaEventDestroy(e.second);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -415,6 +463,8 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   const bool z_host = z && !is_device_ptr(z);
   const size_t xbytes = (size_t)(d - 1) * ld * el + (size_t)n * el;
   size_t need = dense_work_bytes(ctx, o, n, xfmt) + align256((size_t)n * 8) /* rho */ +
+                align256((size_t)(n + 31) / 32 * 32 * 8) /* rho split */ +
+                align256((size_t)d * 8) /* w split */ +
                 align256((size_t)o->H * o->b * 4) /* idx */;
   if (x_host) need += align256(xbytes) + 256;
   if (y_host) need += align256((size_t)n * 8);
@@ -434,6 +484,8 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   double* wd = stage(ctx, cv, w, (size_t)d, true, &st);
   double* zd = z ? stage(ctx, cv, z, (size_t)n, false, &st) : nullptr;
   double* rho = cv.take<double>((size_t)n);
+  float2* rho2 = cv.take<float2>((size_t)(n + 31) / 32 * 32);
+  float2* w2s = cv.take<float2>((size_t)d);
   int* idx = cv.take<int>((size_t)o->H * o->b);
   char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
@@ -445,7 +497,9 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   pb.K = n;
   pb.lda = ld;
   pb.v = rho;
+  pb.v2 = rho2;
   pb.x = wd;
+  pb.x2 = w2s;
   pb.yv = nullptr;
   pb.cG = 1.0 / (double)n;
   pb.cI = o->lam;
@@ -458,7 +512,9 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   // rho_0 = y - X^T w_0  (z_0 = X^T w_0, Alg. 1-2)
   CA_TRY(launch_recompute(ctx, pb, rho, yd, 1.0, -1.0));
   // a1 for all H blocks at once (counter-based, independent of the iterates)
+  prof_mark(ctx, PC_OTHER);
   k_sample<<<(unsigned)((o->H + 7) / 8), 256, 0, ctx->stream>>>(o->seed, o->h0, o->H, o->b, d, idx);
+  prof_mark(ctx, PC_OTHER);
   ctx->prof.kernel_launches += 1;
   CA_TRY_CUDA(cudaGetLastError());
   CA_TRY(run_dense(ctx, pb, o, idx, work, ctx->arena_bytes - (size_t)(work - (char*)ctx->arena)));
@@ -498,7 +554,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     if (v_host) need += align256((size_t)nnz * 4);
     const int sbm = (int)(std::min<long long>(o->s, o->H) * o->b);
     const size_t sbp = (size_t)sbm;
-    need += align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + 4096;
+    need += align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
     bool st;
@@ -512,6 +568,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* R = cv.take<double>(sbp * sbp);
     double* pvec = cv.take<double>(sbp);
     double* delta = cv.take<double>(sbp);
+    double* Ginv = cv.take<double>(sbp * CA_FAST_B);
     CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
     auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
       k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
@@ -531,13 +588,19 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       const int* ik = idx + (size_t)s * k * b;
       const long long npairs = (long long)sb * (sb + 1) / 2;
       const int gg = (int)std::max(1LL, std::min<long long>((npairs + 7) / 8, 8LL * ctx->num_sms));
-      prof_mark(ctx);
+      prof_mark(ctx, PC_GRAM);
       k_gram_csr<<<gg, 256, 0, ctx->stream>>>(rp, col, val, ik, n, sb, (int)sbp, R, ctx->d_err);
       k_proj_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb, wd,
                                                                      pvec, ctx->d_err);
-      prof_mark(ctx);
+      prof_mark(ctx, PC_GRAM);
       SolveArgs sa{ik, n, b, sk, sb, (int)sbp, 1.0 / ln, 1.0, 1.0, 1.0, ad, yd, delta};
-      k_solve<<<1, 256, (size_t)(sb + b * b + b) * 8, ctx->stream>>>(R, pvec, sa, ctx->d_err);
+      prof_mark(ctx, PC_SOLVE);
+      if (fast_solve(b, sb)) {
+        k_factor<<<sk, 32, (size_t)2 * b * b * 8, ctx->stream>>>(R, sa, Ginv, ctx->d_err);
+        ctx->prof.kernel_launches += 1;
+      }
+      launch_solve(ctx, R, pvec, Ginv, sa);
+      prof_mark(ctx, PC_SOLVE);
       k_scatter_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb,
                                                                         delta, -1.0 / ln, wd,
                                                                         ctx->d_err);
@@ -562,7 +625,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   const size_t el = xfmt == CA_DENSE_F64 ? 8 : 4;
   const bool x_host = !is_device_ptr(XT);
   const size_t xbytes = (size_t)(n - 1) * ld * el + (size_t)d * el;
-  need += dense_work_bytes(ctx, o, d, xfmt);
+  need += dense_work_bytes(ctx, o, d, xfmt) + align256((size_t)(d + 31) / 32 * 32 * 8) +
+          align256((size_t)n * 8);
   if (x_host) need += align256(xbytes) + 256;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
@@ -576,6 +640,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
   double* ad = stage(ctx, cv, alpha, (size_t)n, true, &st);
   double* wd = stage(ctx, cv, w, (size_t)d, false, &st);
+  float2* w2 = cv.take<float2>((size_t)(d + 31) / 32 * 32);
+  float2* a2s = cv.take<float2>((size_t)n);
   int* idx = cv.take<int>((size_t)o->H * o->b);
   char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
@@ -586,7 +652,9 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   pb.K = d;
   pb.lda = ld;
   pb.v = wd;
+  pb.v2 = w2;
   pb.x = ad;
+  pb.x2 = a2s;
   pb.yv = yd;
   pb.cG = 1.0 / ln;
   pb.cI = 1.0;
@@ -612,18 +680,17 @@ const char* ca_last_error(ca_ctx* ctx) { return ctx ? ctx->last_error : "no cont
 
 int ca_profile_enable(ca_ctx* ctx, int on) {
   if (!ctx) return CA_ERR_ARG;
+  ctx->prof = Profile();
   ctx->prof.on = on != 0;
-  ctx->prof.gram_ms = 0.0;
-  ctx->prof.gram_launches = 0;
-  ctx->prof.kernel_launches = 0;
   return CA_OK;
 }
 
-int ca_profile_read(ca_ctx* ctx, double* gram_ms_total, long long* gram_launches,
-                    long long* kernel_launches) {
+int ca_profile_read(ca_ctx* ctx, double* ms, long long* launches, long long* kernel_launches) {
   if (!ctx) return CA_ERR_ARG;
-  if (gram_ms_total) *gram_ms_total = ctx->prof.gram_ms;
-  if (gram_launches) *gram_launches = ctx->prof.gram_launches;
+  for (int c = 0; c < PC_N; ++c) {
+    if (ms) ms[c] = ctx->prof.ms[c];
+    if (launches) launches[c] = ctx->prof.launches[c];
+  }
   if (kernel_launches) *kernel_launches = ctx->prof.kernel_launches;
   return CA_OK;
 }
@@ -647,18 +714,22 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   CA_TRY_CUDA(cudaSetDevice(ctx->device));
   const GramPlan g = gram_plan(ctx, xfmt, prec, sb, K);
   const size_t el = g.tc ? 4 : 8;
+  const long long Kp = (K + 31) / 32 * 32;
   const size_t need = align256((size_t)g.P * g.sbp * g.sbp * el) + align256((size_t)g.P * g.sbp * 8) +
-                      align256((size_t)g.sbp * g.sbp * 8) + align256((size_t)g.sbp * 8) + 1024;
+                      align256((size_t)g.sbp * g.sbp * 8) + align256((size_t)g.sbp * 8) +
+                      align256((size_t)Kp * 8) + 1024;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
   void* part = g.tc ? (void*)cv.take<float>((size_t)g.P * g.sbp * g.sbp)
                     : (void*)cv.take<double>((size_t)g.P * g.sbp * g.sbp);
   double* ppart = cv.take<double>((size_t)g.P * g.sbp);
   double* R = cv.take<double>((size_t)g.sbp * g.sbp);
+  float2* v2 = cv.take<float2>((size_t)Kp);
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
-  CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, part, ppart));
+  k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, ctx->stream>>>(v, K, Kp, v2);
+  CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, v2, part, ppart));
   SolveArgs sa{idx, N, 1, 0, sb, g.sbp, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
-  launch_reduce_solve(ctx, g, part, ppart, R, p, sa);
+  launch_reduce_solve(ctx, g, part, ppart, R, p, nullptr, sa);
   k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(R, g.sbp, sb, G);
   CA_TRY_CUDA(cudaGetLastError());
   return finish(ctx);

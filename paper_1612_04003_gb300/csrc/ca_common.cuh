@@ -114,11 +114,34 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 // Packed lower-triangle index: e -> (i, j) with j <= i, e = i(i+1)/2 + j.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void tri_decode(long long e, int& i, int& j) {
-  long long r = (long long)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+  // single-precision estimate (FP64 is scarce on this part), integer fix-up
+  long long r = (long long)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
   while (r * (r + 1) / 2 > e) --r;
   while ((r + 1) * (r + 2) / 2 <= e) ++r;
   i = (int)r;
   j = (int)(e - r * (r + 1) / 2);
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (round-to-nearest FP32, no
+// reassociation).  Used for compensated FP32 sums where FP64 would be slow.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// hi + lo += x (compensated accumulation)
+__device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
+  float s, e;
+  two_sum(hi, x, s, e);
+  hi = s;
+  lo += e;
+}
+
+// x = hi + lo with hi = fp32(x), lo = fp32(x - hi)
+__device__ __forceinline__ float2 split_f64(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
 }
 
 // Solve constants of one outer step in the common form

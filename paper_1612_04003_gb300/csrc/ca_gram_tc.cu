@@ -35,7 +35,10 @@ struct TcCfg {
   static constexpr int kNS = (192 * 1024) / kStageTotal;        // 12 / 6 / 6 / 3 stages
   static constexpr int kTmemCols = (SBP == 256) ? 512 : 128;
   static constexpr int kRPT = SBP / 16;                         // rows per loader thread
-  static constexpr int kSmem = kNS * kStageTotal + 1024 + 512;
+  // projection-vector ring: 2*NS slots of 32 (hi, lo) pairs, so that a slot is
+  // rewritten only after every loader passed the barrier of a later stage
+  static constexpr int kVRing = 2 * kNS * 256;
+  static constexpr int kSmem = kNS * kStageTotal + kVRing + 1024 + 512;
 };
 
 __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
@@ -99,7 +102,7 @@ __device__ __forceinline__ float tf32_head(float x) {
 template <int SBP, bool THREE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
-          const int* __restrict__ idx, int sb, const double* __restrict__ v, long long natoms,
+          const int* __restrict__ idx, int sb, const float2* __restrict__ v2, long long natoms,
           float* __restrict__ part,
           double* __restrict__ ppart, unsigned* __restrict__ err) {
   using C = TcCfg<SBP, THREE>;
@@ -108,7 +111,8 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* stages = smem;  // NS x [big tile (| small tile)]
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * C::kStageTotal);
+  unsigned char* vring = smem + NS * C::kStageTotal;  // 2*NS x 256 B
+  uint64_t* full = reinterpret_cast<uint64_t*>(vring + C::kVRing);
   uint64_t* empty = full + NS;
   uint64_t* done = empty + NS;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
@@ -119,7 +123,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
   const int T = (int)(a_end - a_begin);
 
   // Rows >= sb and columns >= K stay zero for the whole kernel.
-  for (int e = tid; e < NS * C::kStageTotal / 16; e += kThreads)
+  for (int e = tid; e < (NS * C::kStageTotal + C::kVRing) / 16; e += kThreads)
     reinterpret_cast<uint4*>(stages)[e] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -159,6 +163,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       dsto[i] = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((l ^ (r & 7)) << 4));
     }
     const uint32_t stage0 = smem_u32(stages);
+    const uint32_t vring0 = smem_u32(vring);
     auto issue = [&](int t, int slot) {
       const long long k = (a_begin + t) * 32 + 4 * l;
       const long long rem = K - k;
@@ -167,13 +172,18 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
 #pragma unroll
       for (int i = 0; i < RPT; ++i)
         if (rowoff[i] >= 0) cp_async_16_zfill(dst + dsto[i], A + rowoff[i] + (bytes ? k : 0), bytes);
+      if (tid < 16)  // the stage's 32 (hi, lo) pairs of v (zero-padded to a multiple of 32)
+        cp_async_16_zfill(vring0 + (uint32_t)((t % (2 * NS)) * 256 + tid * 16),
+                          v2 + (a_begin + t) * 32 + 2 * tid, 16u);
     };
-    float pacc[RPT];
-    double pacc64[RPT];
+    // projection accumulators: FP32 partial sums over 8 stages, folded into
+    // a compensated (hi, lo) FP32 pair
+    float pacc[RPT], phi[RPT], plo[RPT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
       pacc[i] = 0.f;
-      pacc64[i] = 0.0;
+      phi[i] = 0.f;
+      plo[i] = 0.f;
     }
     bool ok = true;
     for (int t = 0; t < NS - 1; ++t) {
@@ -191,15 +201,17 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       cp_async_wait<NS - 1>();
       const int st = t % NS;
       unsigned char* big = stages + st * C::kStageTotal;
-      // projection on this thread's own chunks (exact FP32 inputs)
-      const long long kb = (a_begin + t) * 32 + 4 * l;
-      float vh[4], vl[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const double vv = (kb + e < K) ? v[kb + e] : 0.0;
-        vh[e] = (float)vv;
-        vl[e] = (float)(vv - (double)vh[e]);
+      if constexpr (!THREE) {  // the tile is ready for the MMA as loaded
+        fence_proxy_async_smem();
+        mbar_arrive(&full[st]);
       }
+      // every loader's copies of this stage (incl. the v slice) have landed
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // projection on this thread's own chunks (exact FP32 inputs)
+      const float4* vs = reinterpret_cast<const float4*>(vring + (t % (2 * NS)) * 256 + l * 32);
+      const float4 va = vs[0], vb = vs[1];
+      const float vh[4] = {va.x, va.z, vb.x, vb.z};
+      const float vl[4] = {va.y, va.w, vb.y, vb.w};
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         float4* p4 = reinterpret_cast<float4*>(big + dsto[i]);
@@ -220,18 +232,20 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       if ((t & 7) == 7) {
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
-          pacc64[i] += (double)pacc[i];
+          comp_add(phi[i], plo[i], pacc[i]);
           pacc[i] = 0.f;
         }
       }
-      fence_proxy_async_smem();
-      mbar_arrive(&full[st]);
+      if constexpr (THREE) {  // head / tail tiles written: hand the stage to the MMA
+        fence_proxy_async_smem();
+        mbar_arrive(&full[st]);
+      }
     }
     cp_async_wait<0>();
     // projection partials: reduce over the 8 lanes sharing a row group
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
-      double s = pacc64[i] + (double)pacc[i];
+      double s = (double)phi[i] + ((double)plo[i] + (double)pacc[i]);
       s += __shfl_xor_sync(0xffffffffu, s, 1);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
       s += __shfl_xor_sync(0xffffffffu, s, 4);
@@ -318,7 +332,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
 
 template <int SBP, bool THREE>
 int launch_one(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
-               const double* v,
+               const float2* v2,
                int P, float* part, double* ppart, unsigned* err, cudaStream_t stream) {
   using C = TcCfg<SBP, THREE>;
   static bool configured = false;
@@ -329,7 +343,7 @@ int launch_one(const float* A, long long lda, long long N, long long K, const in
     configured = true;
   }
   const long long natoms = (K + 31) / 32;
-  k_gram_tc<SBP, THREE><<<P, kThreads, C::kSmem, stream>>>(A, lda, N, K, idx, sb, v, natoms, part,
+  k_gram_tc<SBP, THREE><<<P, kThreads, C::kSmem, stream>>>(A, lda, N, K, idx, sb, v2, natoms, part,
                                                             ppart, err);
   return (int)cudaGetLastError();
 }
@@ -339,13 +353,13 @@ int launch_one(const float* A, long long lda, long long N, long long K, const in
 int gram_tc_max_sb() { return 256; }
 
 int launch_gram_tc(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
-                   const double* v, int P, int sbp, float* part, double* ppart, unsigned* err,
+                   const float2* v2, int P, int sbp, float* part, double* ppart, unsigned* err,
                    int three_pass, cudaStream_t stream) {
   if (sbp == 128)
-    return three_pass ? launch_one<128, true>(A, lda, N, K, idx, sb, v, P, part, ppart, err, stream)
-                      : launch_one<128, false>(A, lda, N, K, idx, sb, v, P, part, ppart, err, stream);
+    return three_pass ? launch_one<128, true>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, stream)
+                      : launch_one<128, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, stream);
   if (sbp == 256)
-    return three_pass ? launch_one<256, true>(A, lda, N, K, idx, sb, v, P, part, ppart, err, stream)
-                      : launch_one<256, false>(A, lda, N, K, idx, sb, v, P, part, ppart, err, stream);
+    return three_pass ? launch_one<256, true>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, stream)
+                      : launch_one<256, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, stream);
   return (int)cudaErrorInvalidValue;
 }

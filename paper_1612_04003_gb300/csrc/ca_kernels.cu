@@ -4,6 +4,8 @@
 // rows are sampled (primal: A = X, N = d, K = n; dual: A = X^T, N = n, K = d),
 // Y = the s'*b sampled rows of A, v the K-vector the Gram pass projects on
 // (primal: rho = y - z with z = X^T w; dual: w).
+#include <type_traits>
+
 #include "ca_kernels.cuh"
 
 // ---------------------------------------------------------------------------
@@ -215,48 +217,272 @@ __device__ void block_solve(const double* __restrict__ R, const double* __restri
   }
 }
 
-// Reduce the split-K partials to R (lower triangle, FP64) and p, then the
-// last CTA to finish runs the inner solves (no spin: a ticket counter).
-template <typename PT>
-__global__ void __launch_bounds__(256)
-k_reduce_solve(const PT* __restrict__ part, const double* __restrict__ ppart, int P, int sbp,
-               double* __restrict__ R, double* __restrict__ pvec, SolveArgs sa,
-               unsigned* __restrict__ ticket, unsigned* __restrict__ err) {
-  extern __shared__ double smem_d[];
-  __shared__ bool is_last;
-  const int sb = sa.sb;
-  const long long nlow = (long long)sb * (sb + 1) / 2;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long sq = (long long)sbp * sbp;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nlow + sb; e += stride) {
-    if (e < nlow) {
-      int i, j;
-      tri_decode(e, i, j);
-      const PT* src = part + (long long)i * sbp + j;
-      double s = 0.0;
-      for (int c = 0; c < P; ++c) s += (double)src[c * sq];
-      R[(long long)i * sa.ldr + j] = s;
-    } else {
-      const int i = (int)(e - nlow);
-      double s = 0.0;
-      for (int c = 0; c < P; ++c) s += ppart[(long long)c * sbp + i];
-      pvec[i] = s;
+// ---------------------------------------------------------------------------
+// a4, fast form (b <= 32, s*b <= 256).  The diagonal blocks
+// Gamma_j = cG R_jj + cI I are independent of the iterates, so they are
+// factored and inverted up front (one CTA per block, in parallel); the
+// dependent chain over j then needs no division or square root:
+//   rhs_j   = cP p_j - cI x0[I_j] - cY y[I_j]
+//             - sum_{t<j} (cG R_jt + cI [I_j == I_t]) Delta_t
+//   Delta_j = Gamma_j^{-1} rhs_j
+// where x0 is x at the start of the outer step; the index-equality term is the
+// lambda I_j^T I_t Delta_t (primal) / I_j^T I_t Delta alpha_t (dual) overlap
+// term of eq. "recur" and its dual analogue.  x is updated once per block at
+// the end (atomic adds: an index may recur across blocks).
+// ---------------------------------------------------------------------------
+
+// One warp: Cholesky of the SPD b x b block A (shared, row-major; destroyed),
+// then Gamma^{-1} = L^{-T} L^{-1} written to out (row-major b x b).  W is a
+// b x b shared scratch.  Lane p owns row / column p (b <= 32).
+__device__ void warp_spd_inverse(double* A, double* W, int b, double* __restrict__ out,
+                                 unsigned* err) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < b; ++k) {
+    if (lane == k) {
+      double dg = A[k * b + k];
+      if (!(dg > 0.0)) {
+        ca_flag(err, isfinite(dg) ? CA_DEV_ERR_NOT_SPD : CA_DEV_ERR_NONFINITE);
+        dg = 1.0;
+      }
+      A[k * b + k] = sqrt(dg);
+    }
+    __syncwarp();
+    const double piv = A[k * b + k];
+    if (lane > k && lane < b) A[lane * b + k] /= piv;
+    __syncwarp();
+    if (lane > k && lane < b) {
+      const double lk = A[lane * b + k];
+      for (int c = k + 1; c <= lane; ++c) A[lane * b + c] -= lk * A[c * b + k];
+    }
+    __syncwarp();
+  }
+  if (lane < b) {  // column `lane` of L^{-1} by forward substitution
+    const int c = lane;
+    for (int i = 0; i < b; ++i) {
+      double v = 0.0;
+      if (i >= c) {
+        v = (i == c) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) v -= A[i * b + k] * W[k * b + c];
+        v /= A[i * b + i];
+      }
+      W[i * b + c] = v;
     }
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  if (threadIdx.x == 0) *ticket = 0u;
-  block_solve(R, pvec, sa, err, smem_d);
+  __syncwarp();
+  if (lane < b) {  // row `lane` of L^{-T} L^{-1}
+    const int p = lane;
+    for (int q = 0; q < b; ++q) {
+      double v = 0.0;
+      for (int k = max(p, q); k < b; ++k) v += W[k * b + p] * W[k * b + q];
+      out[p * b + q] = v;
+    }
+  }
 }
 
-template __global__ void k_reduce_solve<double>(const double*, const double*, int, int, double*,
-                                                double*, SolveArgs, unsigned*, unsigned*);
-template __global__ void k_reduce_solve<float>(const float*, const double*, int, int, double*,
-                                               double*, SolveArgs, unsigned*, unsigned*);
+template <typename PT>
+__device__ __forceinline__ double sum_partials(const PT* __restrict__ src, int P, long long sq,
+                                               int warp) {
+  if constexpr (sizeof(PT) == 4) {
+    float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+    for (int c = warp; c < P; c += 8) comp_add(hi, lo, src[c * sq]);
+    return (double)hi + (double)lo;
+  } else {
+    double s = 0.0;
+#pragma unroll 4
+    for (int c = warp; c < P; c += 8) s += src[c * sq];
+    return s;
+  }
+}
+
+// Reduce the split-K partials.  CTAs 0..ndiag-1 each own diagonal block j:
+// they reduce it into R and (ndiag > 0) factor and invert Gamma_j into
+// Ginv[j].  The other CTAs reduce the remaining lower-triangle entries and
+// the projection p.  32 entries per pass (one per lane); the 8 warps split
+// the P partials.
+template <typename PT>
+__global__ void __launch_bounds__(256)
+k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, int sbp,
+         double* __restrict__ R, double* __restrict__ pvec, double* __restrict__ Ginv,
+         int ndiag, SolveArgs sa, unsigned* __restrict__ err) {
+  extern __shared__ double smem_d[];
+  __shared__ double red[8][32];
+  const int sb = sa.sb, b = sa.b, ldr = sa.ldr;
+  const long long sq = (long long)sbp * sbp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((int)blockIdx.x < ndiag) {
+    const int base = (int)blockIdx.x * b;
+    const int nent = b * (b + 1) / 2;
+    double* Gam = smem_d;      // b*b
+    double* W = Gam + b * b;   // b*b
+    for (int e0 = 0; e0 < nent; e0 += 32) {
+      const int e = e0 + lane;
+      int p = 0, q = 0;
+      double s = 0.0;
+      if (e < nent) {
+        tri_decode(e, p, q);
+        s = sum_partials(part + (long long)(base + p) * sbp + (base + q), P, sq, warp);
+      }
+      red[warp][lane] = s;
+      __syncthreads();
+      if (warp == 0 && e < nent) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += red[w][lane];
+        R[(long long)(base + p) * ldr + (base + q)] = t;
+        Gam[p * b + q] = sa.cG * t + (p == q ? sa.cI : 0.0);
+      }
+      __syncthreads();
+    }
+    if (warp == 0) warp_spd_inverse(Gam, W, b, Ginv + (long long)blockIdx.x * b * b, err);
+    return;
+  }
+  const long long nlow = (long long)sb * (sb + 1) / 2;
+  const long long stride = (long long)(gridDim.x - ndiag) * 32;
+  for (long long e0 = (long long)(blockIdx.x - ndiag) * 32; e0 < nlow + sb; e0 += stride) {
+    const long long e = e0 + lane;
+    int i = 0, j = 0;
+    int kind = 0;  // 0 none, 1 Gram entry, 2 projection entry
+    double s = 0.0;
+    if (e < nlow) {
+      tri_decode(e, i, j);
+      if (!(ndiag > 0 && i / b == j / b)) kind = 1;  // diagonal blocks belong to their CTA
+    } else if (e < nlow + sb) {
+      kind = 2;
+      i = (int)(e - nlow);
+    }
+    if (kind == 1) {
+      s = sum_partials(part + (long long)i * sbp + j, P, sq, warp);
+    } else if (kind == 2) {
+#pragma unroll 4
+      for (int c = warp; c < P; c += 8) s += ppart[(long long)c * sbp + i];
+    }
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && kind) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += red[w][lane];
+      if (kind == 1) R[(long long)i * ldr + j] = t;
+      else pvec[i] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template __global__ void k_reduce<double>(const double*, const double*, int, int, double*, double*,
+                                          double*, int, SolveArgs, unsigned*);
+template __global__ void k_reduce<float>(const float*, const double*, int, int, double*, double*,
+                                         double*, int, SolveArgs, unsigned*);
+
+// Factor and invert the diagonal blocks of an already formed R (sparse path).
+__global__ void __launch_bounds__(32)
+k_factor(const double* __restrict__ R, SolveArgs sa, double* __restrict__ Ginv,
+         unsigned* __restrict__ err) {
+  extern __shared__ double smem_d[];
+  const int b = sa.b, base = (int)blockIdx.x * b;
+  double* Gam = smem_d;
+  double* W = Gam + b * b;
+  for (int e = threadIdx.x; e < b * b; e += 32) {
+    const int p = e / b, q = e % b;
+    if (q <= p)
+      Gam[e] = sa.cG * R[(long long)(base + p) * sa.ldr + (base + q)] + (p == q ? sa.cI : 0.0);
+  }
+  __syncwarp();
+  warp_spd_inverse(Gam, W, b, Ginv + (long long)blockIdx.x * b * b, err);
+}
+
+// The dependent chain (one CTA of 256 threads).  Warp w handles rows
+// p = w + 8m (m < RW) of the current block; lane l the columns l + 32c.  The
+// next block row of R is loaded into registers before the current block's
+// Gamma^{-1} product, so its latency overlaps the synchronisations.
+template <int RW>
+__global__ void __launch_bounds__(256)
+k_chain(const double* __restrict__ R, const double* __restrict__ pvec,
+        const double* __restrict__ Ginv, SolveArgs a, unsigned* __restrict__ err) {
+  extern __shared__ double smem_d[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = a.b, sb = a.sb, ldr = a.ldr, s = a.s_cur;
+  double* Gs = smem_d;                  // sb*b: Gamma_j^{-1}, block j at j*b*b
+  double* rhs0 = Gs + (size_t)sb * b;   // sb
+  double* dlt = rhs0 + sb;              // sb
+  double* rb = dlt + sb;                // 32
+  int* sidx = reinterpret_cast<int*>(rb + 32);  // sb
+  for (int e = tid; e < sb * b; e += 256) Gs[e] = Ginv[e];
+  for (int r = tid; r < sb; r += 256) {
+    const int gi = a.idx[r];
+    double v = a.cP * pvec[r];
+    if (gi >= 0 && gi < a.N) {
+      v -= a.cI * a.x[gi];
+      if (a.yv) v -= a.cY * a.yv[gi];
+    } else {
+      ca_flag(err, CA_DEV_ERR_ARG);
+    }
+    sidx[r] = gi;
+    rhs0[r] = v;
+    dlt[r] = 0.0;
+  }
+  double pre[RW][8];
+  auto prefetch = [&](int j) {
+    const int jb = j * b;
+#pragma unroll
+    for (int m = 0; m < RW; ++m) {
+      const int p = warp + 8 * m;
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const int c = lane + 32 * cc;
+        pre[m][cc] = (p < b && c < jb) ? R[(long long)(jb + p) * ldr + c] : 0.0;
+      }
+    }
+  };
+  prefetch(0);
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    const int jb = j * b;
+#pragma unroll
+    for (int m = 0; m < RW; ++m) {
+      const int p = warp + 8 * m;
+      if (p < b) {  // warp-uniform
+        const int ip = sidx[jb + p];
+        double part = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          const int c = lane + 32 * cc;
+          if (c < jb) {
+            double g = a.cG * pre[m][cc];
+            if (sidx[c] == ip) g += a.cI;
+            part = fma(g, dlt[c], part);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) rb[p] = rhs0[jb + p] - part;
+      }
+    }
+    if (j + 1 < s) prefetch(j + 1);
+    __syncthreads();
+    if (tid < b) {
+      const double* gr = Gs + (size_t)j * b * b + tid * b;
+      double d = 0.0;
+      for (int q = 0; q < b; ++q) d = fma(gr[q], rb[q], d);
+      if (!isfinite(d)) ca_flag(err, CA_DEV_ERR_NONFINITE);
+      dlt[jb + tid] = d;
+      a.delta[jb + tid] = d;
+    }
+    __syncthreads();
+  }
+  for (int r = tid; r < sb; r += 256) {
+    const int gi = sidx[r];
+    if (gi >= 0 && gi < a.N) atomicAdd(a.x + gi, dlt[r]);
+  }
+}
+
+template __global__ void k_chain<1>(const double*, const double*, const double*, SolveArgs,
+                                    unsigned*);
+template __global__ void k_chain<2>(const double*, const double*, const double*, SolveArgs,
+                                    unsigned*);
+template __global__ void k_chain<4>(const double*, const double*, const double*, SolveArgs,
+                                    unsigned*);
 
 // The solves alone (sparse path: R and p are formed directly).
 __global__ void __launch_bounds__(256)
@@ -272,14 +498,20 @@ k_solve(const double* __restrict__ R, const double* __restrict__ pvec, SolveArgs
 // FP64 X: FP64 FMAs.  FP32 X: Delta split into two FP32 halves, FP32 products
 // and sums over the rows, one FP64 subtraction per element.
 // ---------------------------------------------------------------------------
+// CTA = 4 row groups x 64 threads; thread t of group g handles the 4
+// consecutive k at (64 blockIdx + t) * 4 and the rows r = g (mod 4); group 0
+// adds the groups' partial sums and writes v (and its FP32 split v2).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_update_dense(const T* __restrict__ A, long long lda, long long N, long long K,
                const int* __restrict__ idx, int sb, const double* __restrict__ delta, double cU,
-               double* __restrict__ v, unsigned* __restrict__ err) {
+               double* __restrict__ v, float2* __restrict__ v2, unsigned* __restrict__ err) {
+  using Acc = typename std::conditional<sizeof(T) == 8, double, float>::type;
   extern __shared__ unsigned char smem_u[];
+  __shared__ Acc red[3][64][4];
   int* sidx = reinterpret_cast<int*>(smem_u);
   double* sdl = reinterpret_cast<double*>(smem_u + ((sb * 4 + 255) & ~255));
+  float2* sdl2 = reinterpret_cast<float2*>(sdl);  // FP32 path: Delta as (hi, lo)
   for (int r = threadIdx.x; r < sb; r += blockDim.x) {
     int gi = idx[r];
     double dl = delta[r];
@@ -289,51 +521,63 @@ k_update_dense(const T* __restrict__ A, long long lda, long long N, long long K,
       dl = 0.0;
     }
     sidx[r] = gi;
-    sdl[r] = dl;
+    if constexpr (sizeof(T) == 8) sdl[r] = dl;
+    else sdl2[r] = split_f64(dl);
   }
   __syncthreads();
-  const long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  if (k >= K) return;
-  const int nk = (int)min(4ll, K - k);
-  if constexpr (sizeof(T) == 8) {
-    double acc[4] = {0, 0, 0, 0};
-    for (int r = 0; r < sb; ++r) {
-      const T* row = A + (long long)sidx[r] * lda + k;
-      const double dl = sdl[r];
+  const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const long long k = ((long long)blockIdx.x * 64 + t) * 4;
+  const int nk = k < K ? (int)min(4ll, K - k) : 0;
+  Acc acc[4] = {0, 0, 0, 0};
+  if (nk > 0) {
+    if constexpr (sizeof(T) == 8) {
+      for (int r = grp; r < sb; r += 4) {
+        const T* row = A + (long long)sidx[r] * lda + k;
+        const double dl = sdl[r];
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (e < nk) acc[e] = fma((double)row[e], dl, acc[e]);
-    }
-    for (int e = 0; e < nk; ++e) v[k + e] -= cU * acc[e];
-  } else {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    const bool vec = (nk == 4) && ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-#pragma unroll 8
-    for (int r = 0; r < sb; ++r) {
-      const float* row = reinterpret_cast<const float*>(A) + (long long)sidx[r] * lda + k;
-      const double dl = sdl[r];
-      const float dh = (float)dl, dlo = (float)(dl - (double)dh);
-      float x[4];
-      if (vec) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(row));
-        x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) x[e] = (e < nk) ? row[e] : 0.f;
+        for (int e = 0; e < 4; ++e)
+          if (e < nk) acc[e] = fma((double)row[e], dl, acc[e]);
       }
+    } else {
+      const bool vec = (nk == 4) && ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+#pragma unroll 8
+      for (int r = grp; r < sb; r += 4) {
+        const float* row = reinterpret_cast<const float*>(A) + (long long)sidx[r] * lda + k;
+        const float2 d2 = sdl2[r];
+        float x[4];
+        if (vec) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(row));
+          x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+        } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[e] = fmaf(x[e], dh, fmaf(x[e], dlo, acc[e]));
+          for (int e = 0; e < 4; ++e) x[e] = (e < nk) ? row[e] : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[e] = fmaf(x[e], d2.x, fmaf(x[e], d2.y, acc[e]));
+      }
     }
-    for (int e = 0; e < nk; ++e) v[k + e] -= cU * (double)acc[e];
+  }
+  if (grp > 0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) red[grp - 1][t][e] = acc[e];
+  }
+  __syncthreads();
+  if (grp == 0 && nk > 0) {
+    for (int e = 0; e < nk; ++e) {
+      const Acc tot = acc[e] + red[0][t][e] + red[1][t][e] + red[2][t][e];
+      const double nv = v[k + e] - cU * (double)tot;
+      v[k + e] = nv;
+      if (v2) v2[k + e] = split_f64(nv);
+    }
   }
 }
 
 template __global__ void k_update_dense<double>(const double*, long long, long long, long long,
                                                 const int*, int, const double*, double, double*,
-                                                unsigned*);
+                                                float2*, unsigned*);
 template __global__ void k_update_dense<float>(const float*, long long, long long, long long,
                                                const int*, int, const double*, double, double*,
-                                               unsigned*);
+                                               float2*, unsigned*);
 
 // ---------------------------------------------------------------------------
 // a6: full recompute  v[k] = c0 * y0[k] + c1 * sum_{r < N} A[r][k] x[r]
@@ -345,8 +589,8 @@ template __global__ void k_update_dense<float>(const float*, long long, long lon
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long K,
-                  const double* __restrict__ x, double c1, long long rows_per_split,
-                  double* __restrict__ v) {
+                  const double* __restrict__ x, const float2* __restrict__ x2, double c1,
+                  long long rows_per_split, double* __restrict__ v) {
   const long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (k >= K) return;
   const int nk = (int)min(4ll, K - k);
@@ -362,14 +606,16 @@ k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long
         if (e < nk) acc[e] = fma((double)row[e], xr, acc[e]);
     }
   } else {
+    // x split in FP32 halves (x2); FP32 partial sums over 32 rows folded into
+    // compensated FP32 pairs
     const bool vec = (nk == 4) && ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     for (long long rb = r0; rb < r1; rb += 32) {
       float part[4] = {0.f, 0.f, 0.f, 0.f};
       const long long re = min(r1, rb + 32);
 #pragma unroll 8
       for (long long r = rb; r < re; ++r) {
-        const double xr = x[r];
-        const float xh = (float)xr, xl = (float)(xr - (double)xh);
+        const float2 xs = __ldg(x2 + r);
         const float* row = reinterpret_cast<const float*>(A) + r * lda + k;
         float q[4];
         if (vec) {
@@ -380,19 +626,30 @@ k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long
           for (int e = 0; e < 4; ++e) q[e] = (e < nk) ? row[e] : 0.f;
         }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) part[e] = fmaf(q[e], xh, fmaf(q[e], xl, part[e]));
+        for (int e = 0; e < 4; ++e) part[e] = fmaf(q[e], xs.x, fmaf(q[e], xs.y, part[e]));
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) acc[e] += (double)part[e];
+      for (int e = 0; e < 4; ++e) comp_add(hi[e], lo[e], part[e]);
     }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] = (double)hi[e] + (double)lo[e];
   }
   for (int e = 0; e < nk; ++e) atomicAdd(v + k + e, c1 * acc[e]);
 }
 
 template __global__ void k_recompute_dense<double>(const double*, long long, long long, long long,
-                                                   const double*, double, long long, double*);
+                                                   const double*, const float2*, double, long long,
+                                                   double*);
 template __global__ void k_recompute_dense<float>(const float*, long long, long long, long long,
-                                                  const double*, double, long long, double*);
+                                                  const double*, const float2*, double, long long,
+                                                  double*);
+
+// v2[k] = (hi, lo) FP32 split of v[k]; zero for K <= k < Kpad
+__global__ void k_split(const double* __restrict__ v, long long K, long long Kpad,
+                        float2* __restrict__ v2) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < Kpad) v2[k] = k < K ? split_f64(v[k]) : make_float2(0.f, 0.f);
+}
 
 // v = c0 * y0 (or 0 when y0 is null)
 __global__ void k_axpby_init(const double* __restrict__ y0, double c0, long long K,
@@ -532,46 +789,55 @@ void launch_gram_simt(bool f64, dim3 grid, cudaStream_t st, const void* A, long 
                                              chunks_per_split, sbp, part, ppart, err);
 }
 
-void launch_reduce_solve_k(bool f32_partials, int grid, size_t smem, cudaStream_t st,
-                           const void* part, const double* ppart, int P, int sbp, double* R,
-                           double* pvec, const SolveArgs& sa, unsigned* ticket, unsigned* err) {
+void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, const void* part,
+                   const double* ppart, int P, int sbp, double* R, double* pvec, double* Ginv,
+                   int ndiag, const SolveArgs& sa, unsigned* err) {
   if (f32_partials)
-    k_reduce_solve<float><<<grid, 256, smem, st>>>(static_cast<const float*>(part), ppart, P, sbp,
-                                                    R, pvec, sa, ticket, err);
+    k_reduce<float><<<grid, 256, smem, st>>>(static_cast<const float*>(part), ppart, P, sbp, R, pvec,
+                                              Ginv, ndiag, sa, err);
   else
-    k_reduce_solve<double><<<grid, 256, smem, st>>>(static_cast<const double*>(part), ppart, P,
-                                                     sbp, R, pvec, sa, ticket, err);
+    k_reduce<double><<<grid, 256, smem, st>>>(static_cast<const double*>(part), ppart, P, sbp, R,
+                                               pvec, Ginv, ndiag, sa, err);
+}
+
+void launch_chain(int rows_per_warp, size_t smem, cudaStream_t st, const double* R,
+                  const double* pvec, const double* Ginv, const SolveArgs& sa, unsigned* err) {
+  if (rows_per_warp <= 1) k_chain<1><<<1, 256, smem, st>>>(R, pvec, Ginv, sa, err);
+  else if (rows_per_warp == 2) k_chain<2><<<1, 256, smem, st>>>(R, pvec, Ginv, sa, err);
+  else k_chain<4><<<1, 256, smem, st>>>(R, pvec, Ginv, sa, err);
 }
 
 void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
                          long long lda, long long N, long long K, const int* idx, int sb,
-                         const double* delta, double cU, double* v, unsigned* err) {
+                         const double* delta, double cU, double* v, float2* v2, unsigned* err) {
   if (f64)
     k_update_dense<double><<<grid, 256, smem, st>>>(static_cast<const double*>(A), lda, N, K, idx,
-                                                     sb, delta, cU, v, err);
+                                                     sb, delta, cU, v, v2, err);
   else
     k_update_dense<float><<<grid, 256, smem, st>>>(static_cast<const float*>(A), lda, N, K, idx,
-                                                    sb, delta, cU, v, err);
+                                                    sb, delta, cU, v, v2, err);
 }
 
 void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
-                            long long N, long long K, const double* x, double c1,
+                            long long N, long long K, const double* x, const float2* x2, double c1,
                             long long rows_per_split, double* v) {
   if (f64)
-    k_recompute_dense<double><<<grid, 256, 0, st>>>(static_cast<const double*>(A), lda, N, K, x, c1,
-                                                     rows_per_split, v);
+    k_recompute_dense<double><<<grid, 256, 0, st>>>(static_cast<const double*>(A), lda, N, K, x, x2,
+                                                     c1, rows_per_split, v);
   else
-    k_recompute_dense<float><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K, x, c1,
-                                                    rows_per_split, v);
+    k_recompute_dense<float><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K, x, x2,
+                                                    c1, rows_per_split, v);
 }
 
 int set_solve_smem_limit(int bytes) {
-  cudaError_t e1 = cudaFuncSetAttribute(k_reduce_solve<float>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaError_t e2 = cudaFuncSetAttribute(k_reduce_solve<double>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaError_t e3 = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e1 != cudaSuccess) return (int)e1;
-  if (e2 != cudaSuccess) return (int)e2;
-  return (int)e3;
+  cudaError_t e[6] = {
+      cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_reduce<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_reduce<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return (int)x;
+  return 0;
 }

@@ -11,20 +11,28 @@ void launch_gram_simt(bool f64, dim3 grid, cudaStream_t st, const void* A, long 
                       long long N, long long K, const int* idx, int sb, const double* v,
                       long long chunks_per_split, int sbp, double* part, double* ppart,
                       unsigned* err);
-void launch_reduce_solve_k(bool f32_partials, int grid, size_t smem, cudaStream_t st,
-                           const void* part, const double* ppart, int P, int sbp, double* R,
-                           double* pvec, const SolveArgs& sa, unsigned* ticket, unsigned* err);
+// a4: reduce the split-K partials (CTAs < ndiag also factor + invert the
+// diagonal blocks into Ginv), then the chain (fast form) or the general solve.
+void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, const void* part,
+                   const double* ppart, int P, int sbp, double* R, double* pvec, double* Ginv,
+                   int ndiag, const SolveArgs& sa, unsigned* err);
+void launch_chain(int rows_per_warp, size_t smem, cudaStream_t st, const double* R,
+                  const double* pvec, const double* Ginv, const SolveArgs& sa, unsigned* err);
+__global__ void k_factor(const double* R, SolveArgs sa, double* Ginv, unsigned* err);
+#define CA_FAST_B 32
+#define CA_FAST_SB 256
 void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
                          long long lda, long long N, long long K, const int* idx, int sb,
-                         const double* delta, double cU, double* v, unsigned* err);
+                         const double* delta, double cU, double* v, float2* v2, unsigned* err);
 void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
-                            long long N, long long K, const double* x, double c1,
+                            long long N, long long K, const double* x, const float2* x2, double c1,
                             long long rows_per_split, double* v);
 int set_solve_smem_limit(int bytes);
 
 __global__ void k_solve(const double* R, const double* pvec, SolveArgs sa, unsigned* err);
 
 __global__ void k_axpby_init(const double* y0, double c0, long long K, double* v);
+__global__ void k_split(const double* v, long long K, long long Kpad, float2* v2);
 
 __global__ void k_gram_csr(const long long* rowptr, const int* col, const float* val,
                            const int* idx, long long nrows, int sb, int ldr, double* R,
@@ -43,8 +51,9 @@ __global__ void k_symmetrize(const double* R, int ldr, int sb, double* G);
 // tcgen05 Gram (ca_gram_tc.cu): host-side launcher.  Returns a cudaError_t.
 // Computes FP32 partials part[c][i][j] (c < P, row stride sbp) of
 // sum_{k in split c} Y[i][k] Y[j][k] for the tiles covering j <= i, and FP64
-// partials ppart[c][i] of sum_k Y[i][k] v[k].  sbp is 128 (sb <= 128) or 256.
+// partials ppart[c][i] of sum_k Y[i][k] v[k], v given as FP32 pairs
+// (hi, lo) zero-padded to a multiple of 32 entries.  sbp is 128 (sb <= 128) or 256.
 int launch_gram_tc(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
-                   const double* v, int P, int sbp, float* part, double* ppart, unsigned* err,
+                   const float2* v2, int P, int sbp, float* part, double* ppart, unsigned* err,
                    int three_pass, cudaStream_t stream);
 int gram_tc_max_sb();
