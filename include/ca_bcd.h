@@ -153,6 +153,29 @@ int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long l
 int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N, long long K,
                     long long ld, const int* idx, int sb, const double* v, double* G, double* p);
 
+/* Steps a2+a3 exactly as ca_gram_project computes them, for callers that must
+ * not allocate device memory (the paper has no counterpart: this is an
+ * interface convenience).  Such callers include code running while a host
+ * framework owns every device allocation through its own pool, code on a
+ * latency-critical path where an allocation's implicit synchronisation is not
+ * acceptable, and code that may only enqueue work on a stream it was given.
+ * No context is needed and nothing is allocated: the scratch is one fixed
+ * device array inside the library (6.5 MiB, held on every GPU that loads the
+ * library until the process exits).
+ *   cuda_stream  the cudaStream_t to run on (NULL = legacy default stream),
+ *                on the current device.
+ *   Limits: sb <= 128 and K <= 262144 (beyond them: CA_ERR_UNSUPPORTED).
+ *   A, idx, v, G, p: as ca_gram_project, all device memory.
+ * The first call on a device looks up the array's device address (keep that
+ * first call outside any stream capture).  All calls share the array and it
+ * keeps the previous call's contents; calls that overlap on the GPU race on
+ * it, so order them (one stream, or events).  The call returns after the
+ * stream has finished its work.  Errors: CA_ERR_ARG, CA_ERR_UNSUPPORTED,
+ * CA_ERR_TIMEOUT, CA_ERR_CUDA. */
+int ca_gram_project_noalloc(void* cuda_stream, int xfmt, int prec, const void* A, long long N,
+                            long long K, long long ld, const int* idx, int sb, const double* v,
+                            double* G, double* p);
+
 /* Text of the last failing CUDA call seen by an entry point on this context
  * (empty if none); owned by the context, valid until the next call. */
 const char* ca_last_error(ca_ctx* ctx);

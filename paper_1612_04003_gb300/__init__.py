@@ -87,6 +87,8 @@ def load():
     lib.ca_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]
     lib.ca_profile_read.restype = i32
+    lib.ca_gram_project_noalloc.argtypes = [vp, i32, i32, vp, i64, i64, i64, vp, i32, vp, vp, vp]
+    lib.ca_gram_project_noalloc.restype = i32
     lib.ca_last_error.argtypes = [vp]
     lib.ca_last_error.restype = ctypes.c_char_p
     lib.ca_gram_project.argtypes = [vp, i32, i32, vp, i64, i64, i64, vp, i32, vp, vp, vp]
@@ -106,6 +108,19 @@ def header_functions() -> list[str]:
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
             names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(ca_\w+)\s*\(", text, re.M)
     return sorted(set(names))
+
+
+def gram_project_noalloc(A, idx, v, G, p, *, prec="tf32", ld=None, stream=None):
+    """ca_gram_project_noalloc: G = Y Y^T and p = Y v without any device
+    allocation (all arrays are device memory on the current device)."""
+    N, K = A.shape
+    pr = PREC[prec] if isinstance(prec, str) else int(prec)
+    st = load().ca_gram_project_noalloc(stream, _xfmt(A), pr, _ptr(A), N, K,
+                                        K if ld is None else ld, _ptr(idx), int(idx.shape[0]),
+                                        _ptr(v), _ptr(G), _ptr(p))
+    if st != CA_OK:
+        raise CaError(st, "ca_gram_project_noalloc")
+    return G, p
 
 
 def status_str(status: int) -> str:
