@@ -224,6 +224,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--s", type=int, default=None, help="unrolling depth (default %d)" % S)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -232,6 +233,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    s_run = args.s or S
 
     import numpy as np
     import torch
@@ -251,13 +253,13 @@ def main():
     ctx = ca.Context(local_rank, stream=stream.cuda_stream)
 
     # warm-up
-    time_solves(ctx, X, y, w, z, args.warmup, stream)
+    time_solves(ctx, X, y, w, z, args.warmup, stream, s=s_run)
     # timed region
     ctx.ca_profile_enable(True)
     clocks = ClockSampler(local_rank)
     clocks.start()
     barrier(world)
-    ms = time_solves(ctx, X, y, w, z, args.steps, stream)
+    ms = time_solves(ctx, X, y, w, z, args.steps, stream, s=s_run)
     barrier(world)
     clocks.stop()
     prof = ctx.ca_profile_read()
@@ -267,18 +269,24 @@ def main():
 
     # roofline of the dominant kernel (the tcgen05 Gram pass, one launch per outer step)
     peaks, peak_kind = _peaks()
-    sb = S * B
+    sb = s_run * B
     gram_ms = prof["gram_ms"] / max(1, prof["gram_launches"])
+    n_outer = -(-H // s_run)
+    fused = sb <= 128 and PREC in ("tf32", "3xtf32")  # a5 of step k rides in the a2+a3 launch of k+1
+    b_gram = sb * N_SAMPLES * 4 + N_SAMPLES * 8          # B_G: Y rows + the projection vector
+    b_upd = sb * N_SAMPLES * 4 + 2 * N_SAMPLES * 8       # B_U: Y rows + read/write of v
     breakdown = {c: {"ms_per_step": prof[f"{c}_ms"] / args.steps,
                      "share": prof[f"{c}_ms"] / max(ms, 1e-9)}
-                 for c in ("gram", "solve", "update", "other")}
-    alg_bytes = sb * N_SAMPLES * 4 + N_SAMPLES * 8          # Y rows + the projection vector
+                 for c in ("gram", "reduce", "chain", "update", "other")}
+    alg_bytes = (n_outer * b_gram + (n_outer - 1) * b_upd) / n_outer if fused else b_gram
     achieved = alg_bytes / (gram_ms * 1e-3) / 1e9
     trec = _traffic_record(os.path.join(ROOT, "paper_1612_04003_gb300", "csrc", "ca_gram_tc.cu"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"],
             "traffic": trec["traffic_bytes_per_launch"] if trec else None,
-            "kernel": f"k_gram_tc<256,{PREC}> (gather + Gram + projection)",
+            "kernel": (f"k_gram_tc<{128 if sb <= 128 else 256},{PREC}"
+                       f"{',fused update' if fused else ''}> (gather + Gram + projection"
+                       f"{' + deferred update of the previous outer step' if fused else ''})"),
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": gram_ms,
             "launches": prof["gram_launches"], "peak_source": f"hbm_gbs ({peak_kind})",
             "gram_share_of_step": prof["gram_ms"] / max(ms, 1e-9)}
@@ -291,12 +299,12 @@ def main():
     yh.copy_(y)
     wh = torch.zeros(D, dtype=torch.float64, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 10))
-    ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=S, H=H, lam=LAM, seed=42, prec=PREC)  # warm
+    ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=s_run, H=H, lam=LAM, seed=42, prec=PREC)  # warm
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         wh.zero_()
-        ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=S, H=H, lam=LAM, seed=42, prec=PREC)
+        ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=s_run, H=H, lam=LAM, seed=42, prec=PREC)
     t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     e2e = {"value": world * H / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8 + wh.numel() * 8),
@@ -325,7 +333,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "3xtf32 (fp32-faithful)", "data": "synthetic", "config": workload_config(),
+            "dtype": "3xtf32 (fp32-faithful)", "data": "synthetic",
+            "config": workload_config(s=s_run),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(prof["kernel_launches"]),
             "clocks": clocks.summary(), "sweep": sweep,

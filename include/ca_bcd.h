@@ -183,14 +183,16 @@ const char* ca_last_error(ca_ctx* ctx);
 /* Name of a status code (static string). */
 const char* ca_status_str(int status);
 
-/* Measurement hooks.  With profiling on, every following dense solve records
- * CUDA event pairs on the context's stream around each launch of four kernel
- * classes: [0] the Gram pass (a2+a3), [1] the reduce + inner solves (a4),
- * [2] the deferred update (a5), [3] everything else (sampling a1, the
- * recomputations a6).  ca_profile_read fills ms[4] (summed event time per
- * class), launches[4] (timed intervals per class) and *kernel_launches (all
- * kernels the solves launched) since the last ca_profile_enable; any pointer
- * may be NULL.  Errors: CA_ERR_ARG for a NULL context. */
+/* Measurement hooks.  With profiling on, every following solve records CUDA
+ * event pairs on the context's stream around each launch of five kernel
+ * classes: [0] the Gram pass (a2+a3), [1] the reduction of its partials (and
+ * the factorisation of the diagonal blocks, a4), [2] the deferred update
+ * (a5), [3] everything else (sampling a1, the recomputations a6), [4] the
+ * dependent chain of inner solves (a4).  ca_profile_read fills ms[5] (summed
+ * event time per class), launches[5] (timed intervals per class) and
+ * *kernel_launches (all kernels the solves launched) since the last
+ * ca_profile_enable; any pointer may be NULL.  Errors: CA_ERR_ARG for a NULL
+ * context. */
 int ca_profile_enable(ca_ctx* ctx, int on);
 int ca_profile_read(ca_ctx* ctx, double* ms, long long* launches, long long* kernel_launches);
 

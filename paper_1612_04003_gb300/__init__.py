@@ -254,11 +254,11 @@ class Context:
         if st != CA_OK:
             raise CaError(st, "ca_profile_enable")
 
-    PROFILE_CLASSES = ("gram", "solve", "update", "other")
+    PROFILE_CLASSES = ("gram", "reduce", "update", "other", "chain")
 
     def ca_profile_read(self):
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_longlong * 4)()
+        ms = (ctypes.c_double * 5)()
+        n = (ctypes.c_longlong * 5)()
         k = ctypes.c_longlong()
         st = self._lib.ca_profile_read(self.handle, ms, n, ctypes.byref(k))
         if st != CA_OK:

@@ -14,16 +14,16 @@ namespace {
 
 constexpr int kMaxB = 128;          // b x b block held in shared memory by the solve
 constexpr int kMaxSB = 1024;        // s*b right-hand sides held in shared memory
-constexpr int kSolveSmemMax = 200 * 1024;
+constexpr int kSolveSmemMax = 220 * 1024;
 
 // Kernel classes timed by the profiling hooks.
-enum { PC_GRAM = 0, PC_SOLVE = 1, PC_UPDATE = 2, PC_OTHER = 3, PC_N = 4 };
+enum { PC_GRAM = 0, PC_SOLVE = 1, PC_UPDATE = 2, PC_OTHER = 3, PC_CHAIN = 4, PC_N = 5 };
 
 struct Profile {
   bool on = false;
   std::vector<std::pair<int, cudaEvent_t>> ev;  // (class, start) / (class, stop) pairs
-  double ms[PC_N] = {0, 0, 0, 0};
-  long long launches[PC_N] = {0, 0, 0, 0};
+  double ms[PC_N] = {0, 0, 0, 0, 0};
+  long long launches[PC_N] = {0, 0, 0, 0, 0};
   long long kernel_launches = 0;
 };
 
@@ -212,7 +212,7 @@ GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
   g.tc = (xfmt == CA_DENSE_F32) && (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT);
   g.three = (prec == CA_GRAM_FP32_EXACT) ? 1 : 0;
   if (g.tc) {
-    g.sbp = sbm <= 128 ? 128 : 256;
+    g.sbp = sbm <= 32 ? 32 : (sbm <= 64 ? 64 : (sbm <= 128 ? 128 : 256));
     g.P = (int)std::min<long long>(ctx->num_sms, (K + 31) / 32);
   } else {
     g.sbp = (sbm + 63) / 64 * 64;
@@ -245,15 +245,17 @@ int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long lo
 
 bool fast_solve(int b, int sb) { return b <= CA_FAST_B && sb <= CA_FAST_SB; }
 
-size_t chain_smem(int b, int sb) { return (size_t)sb * b * 8 + (size_t)sb * 16 + 32 * 8 + (size_t)sb * 4 + 64; }
+size_t chain_smem(int b, int sb) {
+  const size_t ring = b <= 8 ? 4 * 256 * 8 * 8 : (b <= 16 ? 3 * 256 * 16 * 8 : 2 * 256 * 32 * 8);
+  return ring + (size_t)sb * b * 8 + 64 * 8 + (size_t)sb * 12 + 64;
+}
 
-// a4: the chain (fast form) or the general block forward substitution, from R, p (and Ginv).
-void launch_solve(ca_ctx* ctx, const double* R, const double* pvec, const double* Ginv,
-                  const SolveArgs& sa) {
+// a4: the chain (fast form, from Rs, p, Ginv) or the general block forward
+// substitution (from R, p).
+void launch_solve(ca_ctx* ctx, const double* R, const float2* Rs, const double* pvec,
+                  float2* Ginv, const SolveArgs& sa) {
   if (fast_solve(sa.b, sa.sb)) {
-    const int rw = (sa.b + 7) / 8;
-    launch_chain(rw <= 1 ? 1 : (rw <= 2 ? 2 : 4), chain_smem(sa.b, sa.sb), ctx->stream, R, pvec, Ginv,
-                 sa, ctx->d_err);
+    launch_chain(sa.b, chain_smem(sa.b, sa.sb), ctx->stream, R, Rs, pvec, Ginv, sa, ctx->d_err);
   } else {
     k_solve<<<1, 256, (size_t)(sa.sb + sa.b * sa.b + sa.b) * sizeof(double), ctx->stream>>>(
         R, pvec, sa, ctx->d_err);
@@ -263,17 +265,19 @@ void launch_solve(ca_ctx* ctx, const double* R, const double* pvec, const double
 // a4 entry: reduce the partials to R, p (+ the inverted diagonal blocks), then
 // (s_cur > 0) the inner solves.
 void launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const double* ppart,
-                         double* R, double* pvec, double* Ginv, const SolveArgs& sa) {
+                         double* R, float2* Rs, double* pvec, float2* Ginv, const SolveArgs& sa) {
   const bool fast = sa.s_cur > 0 && fast_solve(sa.b, sa.sb);
-  const int ndiag = fast ? sa.s_cur : 0;
   const long long entries = (long long)sa.sb * (sa.sb + 1) / 2 + sa.sb;
-  const int G = ndiag + (int)std::max(1LL, std::min<long long>((entries + 31) / 32, 4LL * ctx->num_sms));
-  const size_t rsm = fast ? (size_t)2 * sa.b * sa.b * sizeof(double) : 0;
-  launch_reduce(g.tc, G, rsm, ctx->stream, part, ppart, g.P, g.sbp, R, pvec, Ginv, ndiag, sa,
-                ctx->d_err);
+  const int G = (int)std::max(1LL, std::min<long long>((entries + 31) / 32, 8LL * ctx->num_sms));
+  prof_mark(ctx, PC_SOLVE);
+  launch_reduce(g.tc, G, 0, ctx->stream, part, ppart, g.P, g.sbp, R, fast ? Rs : nullptr, pvec,
+                nullptr, 0, sa, ctx->d_err);
+  prof_mark(ctx, PC_SOLVE);
   ctx->prof.kernel_launches += 1;
   if (sa.s_cur > 0) {
-    launch_solve(ctx, R, pvec, Ginv, sa);
+    prof_mark(ctx, PC_CHAIN);
+    launch_solve(ctx, R, Rs, pvec, Ginv, sa);
+    prof_mark(ctx, PC_CHAIN);
     ctx->prof.kernel_launches += 1;
   }
 }
@@ -293,35 +297,66 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   double* ppart = cv.take<double>((size_t)P * sbp);
   double* R = cv.take<double>((size_t)sbp * sbp);
   double* pvec = cv.take<double>((size_t)sbp);
-  double* delta = cv.take<double>((size_t)sbp);
-  double* Ginv = cv.take<double>((size_t)sbp * CA_FAST_B);
+  double* delta2[2] = {cv.take<double>((size_t)sbp), cv.take<double>((size_t)sbp)};
+  float2* Ginv = cv.take<float2>((size_t)sbp * CA_FAST_B);
+  float2* Rs = cv.take<float2>((size_t)sbp * sbp);
+  // The deferred update of outer step k (a5) runs inside the Gram launch of
+  // step k+1 when the tensor-core path has s*b <= 128; otherwise, after the
+  // last step, and before a due recomputation it runs on its own.
+  const bool fuse = g.tc && g.sbp <= 128;
+  auto due = [&](long long k) { return o->recompute_every > 0 && (k + 1) % o->recompute_every == 0; };
+  bool pending = false;  // an update (prev_*) not yet applied
+  const int* prev_idx = nullptr;
+  int prev_sb = 0;
+  const double* prev_delta = nullptr;
+  auto update_alone = [&]() -> int {
+    const size_t usm = align256((size_t)prev_sb * 4) + (size_t)prev_sb * 8;  // sidx | delta
+    const unsigned ug = (unsigned)((K + 255) / 256);
+    prof_mark(ctx, PC_UPDATE);
+    launch_update_dense(pb.xfmt == CA_DENSE_F64, ug, usm, ctx->stream, pb.A, pb.lda, pb.N, K,
+                        prev_idx, prev_sb, prev_delta, pb.cU, pb.v, pb.v2, ctx->d_err);
+    prof_mark(ctx, PC_UPDATE);
+    ctx->prof.kernel_launches += 1;
+    pending = false;
+    return cuda_status(cudaGetLastError());
+  };
 
   const long long n_outer = (H + s - 1) / s;
   for (long long k = 0; k < n_outer; ++k) {
     const int sk = (int)std::min<long long>(s, H - (long long)s * k);
     const int sb = sk * b;
     const int* idx = idx_all + (size_t)s * k * b;
-    // a2 + a3
+    double* delta = delta2[k & 1];
+    if (pending && (!fuse || due(k - 1))) {
+      CA_TRY(update_alone());                                   // a5 of step k-1
+      if (due(k - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));  // a6
+    }
+    // a2 + a3 (and a5 of step k-1 when fused)
+    GramUpdate gu{prev_idx, pending ? prev_sb : 0, prev_delta, pb.cU, pb.v2};
     prof_mark(ctx, PC_GRAM);
-    CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart));
+    if (pending) {
+      const int e = launch_gram_tc(static_cast<const float*>(pb.A), pb.lda, pb.N, K, idx, sb, pb.v2,
+                                   P, sbp, static_cast<float*>(part), ppart, ctx->d_err, g.three,
+                                   ctx->stream, &gu);
+      if (e != 0) return cuda_fail((cudaError_t)e, __LINE__);
+      pending = false;
+    } else {
+      CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart));
+    }
     prof_mark(ctx, PC_GRAM);
+    ctx->prof.kernel_launches += 1;
     // a4 (reduce of the split-K partials, then the s unrolled solves)
     SolveArgs sa{idx, pb.N, b, sk, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, delta};
-    prof_mark(ctx, PC_SOLVE);
-    launch_reduce_solve(ctx, g, part, ppart, R, pvec, Ginv, sa);
-    prof_mark(ctx, PC_SOLVE);
-    // a5
-    const size_t usm = align256((size_t)sb * 4) + (size_t)sb * 8;  // sidx | delta
-    const unsigned ug = (unsigned)((K + 255) / 256);
-    prof_mark(ctx, PC_UPDATE);
-    launch_update_dense(pb.xfmt == CA_DENSE_F64, ug, usm, ctx->stream, pb.A, pb.lda, pb.N, K, idx, sb,
-                        delta, pb.cU, pb.v, pb.v2, ctx->d_err);
-    prof_mark(ctx, PC_UPDATE);
-    ctx->prof.kernel_launches += 2;
+    launch_reduce_solve(ctx, g, part, ppart, R, Rs, pvec, Ginv, sa);
     CA_TRY_CUDA(cudaGetLastError());
-    // a6
-    if (o->recompute_every > 0 && (k + 1) % o->recompute_every == 0)
-      CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
+    pending = true;
+    prev_idx = idx;
+    prev_sb = sb;
+    prev_delta = delta;
+  }
+  if (pending) {
+    CA_TRY(update_alone());
+    if (due(n_outer - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
   }
   return CA_OK;
 }
@@ -341,8 +376,8 @@ size_t dense_work_bytes(ca_ctx* ctx, const ca_opts* o, long long K, int xfmt) {
     P = std::min(P, cap);
     el = 8;
   }
-  return align256(P * sbp * sbp * el) + align256(P * sbp * 8) + align256(sbp * sbp * 8) +
-         2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
+  return align256(P * sbp * sbp * el) + align256(P * sbp * 8) + 2 * align256(sbp * sbp * 8) +
+         3 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
 }
 
 // Stage a caller array on the device (copy in when `in`), return the device pointer.
@@ -554,7 +589,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     if (v_host) need += align256((size_t)nnz * 4);
     const int sbm = (int)(std::min<long long>(o->s, o->H) * o->b);
     const size_t sbp = (size_t)sbm;
-    need += align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
+    need += 2 * align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
     bool st;
@@ -568,7 +603,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* R = cv.take<double>(sbp * sbp);
     double* pvec = cv.take<double>(sbp);
     double* delta = cv.take<double>(sbp);
-    double* Ginv = cv.take<double>(sbp * CA_FAST_B);
+    float2* Ginv = cv.take<float2>(sbp * CA_FAST_B);
+    float2* Rs = cv.take<float2>(sbp * sbp);
     CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
     auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
       k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
@@ -596,10 +632,11 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       SolveArgs sa{ik, n, b, sk, sb, (int)sbp, 1.0 / ln, 1.0, 1.0, 1.0, ad, yd, delta};
       prof_mark(ctx, PC_SOLVE);
       if (fast_solve(b, sb)) {
-        k_factor<<<sk, 32, (size_t)2 * b * b * 8, ctx->stream>>>(R, sa, Ginv, ctx->d_err);
+        k_scale_split<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(
+            R, (int)sbp, sb, b, 1.0 / ln, Rs);
         ctx->prof.kernel_launches += 1;
       }
-      launch_solve(ctx, R, pvec, Ginv, sa);
+      launch_solve(ctx, R, Rs, pvec, Ginv, sa);
       prof_mark(ctx, PC_SOLVE);
       k_scatter_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb,
                                                                         delta, -1.0 / ln, wd,
@@ -729,7 +766,7 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, ctx->stream>>>(v, K, Kp, v2);
   CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, v2, part, ppart));
   SolveArgs sa{idx, N, 1, 0, sb, g.sbp, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
-  launch_reduce_solve(ctx, g, part, ppart, R, p, nullptr, sa);
+  launch_reduce_solve(ctx, g, part, ppart, R, nullptr, p, nullptr, sa);
   k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(R, g.sbp, sb, G);
   CA_TRY_CUDA(cudaGetLastError());
   return finish(ctx);

@@ -99,11 +99,27 @@ __device__ __forceinline__ void cp_async_16_zfill(uint32_t dst, const void* src,
                : "memory");
 }
 
+__device__ __forceinline__ void cp_async_8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// 1/d by Newton-Raphson, r <- r (2 - d r), from the FP32 reciprocal: each step
+// doubles the correct bits (about 23 -> 46 -> full FP64).  d must be a
+// normal FP32-representable magnitude; otherwise the FP64 division is used.
+__device__ __forceinline__ double rcp_newton(double d) {
+  const float f = (float)d;
+  double r = (double)__frcp_rn(f);
+  if (!(fabs(r) > 0.0) || !isfinite(r)) return 1.0 / d;
+  r = r * fma(-d, r, 2.0);
+  r = r * fma(-d, r, 2.0);
+  return r;
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -142,6 +158,37 @@ __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
 __device__ __forceinline__ float2 split_f64(double x) {
   const float h = (float)x;
   return make_float2(h, (float)(x - (double)h));
+}
+
+// Double-float arithmetic: a value is hi + lo (two FP32, |lo| <= ulp(hi)/2);
+// Dekker / Knuth error-free transformations give ~2^-44 relative accuracy
+// on the FP32 pipe, which on this part is ~64x faster than the FP64 pipe.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e += a.y + b.y;
+  const float h = s + e;
+  return make_float2(h, e - (h - s));
+}
+
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.x, -p) + fmaf(a.x, b.y, a.y * b.x);
+  const float h = p + e;
+  return make_float2(h, e - (h - p));
+}
+
+// (shi, slo) += a * b, with a and b double-float values
+__device__ __forceinline__ void df_fma_acc(float2 a, float2 b, float& shi, float& slo) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.x, -p);                 // exact low part of a.x*b.x
+  const float cross = fmaf(a.x, b.y, a.y * b.x);      // first-order terms
+  float s, t;
+  two_sum(shi, p, s, t);
+  shi = s;
+  slo += t + (e + cross);
 }
 
 // Solve constants of one outer step in the common form

@@ -234,49 +234,59 @@ __device__ void block_solve(const double* __restrict__ R, const double* __restri
 // One warp: Cholesky of the SPD b x b block A (shared, row-major; destroyed),
 // then Gamma^{-1} = L^{-T} L^{-1} written to out (row-major b x b).  W is a
 // b x b shared scratch.  Lane p owns row / column p (b <= 32).
-__device__ void warp_spd_inverse(double* A, double* W, int b, double* __restrict__ out,
-                                 unsigned* err) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k < b; ++k) {
-    if (lane == k) {
-      double dg = A[k * b + k];
-      if (!(dg > 0.0)) {
-        ca_flag(err, isfinite(dg) ? CA_DEV_ERR_NOT_SPD : CA_DEV_ERR_NONFINITE);
-        dg = 1.0;
+// Gamma_j^{-1} for one b x b block by the Gauss-Jordan sweep operator on a
+// symmetric positive definite matrix (Goodnight, 1979): sweeping pivot k maps
+// a_kk -> -1/a_kk, a_ik -> a_ik/a_kk, a_kj -> a_kj/a_kk and
+// a_ij -> a_ij - a_ik a_kj / a_kk; after all b pivots the matrix is -Gamma^{-1}.
+// A group of GW lanes (GW >= b, a power of two dividing 32) holds one row per
+// lane in registers; pivot rows are broadcast with shuffles; pivots are
+// inverted by Newton-Raphson.  Gamma = cG R_jj + cI I is read from R (FP64,
+// lower triangle, leading dimension ldr); the result goes to out (row-major
+// b x b FP32 pairs).  Returns false on a non-positive pivot.
+template <int BMAX, int GW>
+__device__ bool group_sweep_inverse(const double* __restrict__ R, int ldr, int base, int b, double cG,
+                                    double cI, float2* __restrict__ out) {
+  const int p = threadIdx.x & (GW - 1);
+  const unsigned mask = (GW == 32) ? 0xffffffffu : (((1u << GW) - 1u) << ((threadIdx.x & 31) & ~(GW - 1)));
+  double a[BMAX];
+#pragma unroll
+  for (int c = 0; c < BMAX; ++c) {
+    double v = 0.0;
+    if (p < b && c < b) {
+      const int i = p > c ? p : c, jj = p > c ? c : p;  // lower triangle of R
+      v = cG * R[(long long)(base + i) * ldr + (base + jj)] + (p == c ? cI : 0.0);
+    }
+    a[c] = v;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < BMAX; ++k) {
+    if (k < b) {
+      double ak[BMAX];
+#pragma unroll
+      for (int c = 0; c < BMAX; ++c) ak[c] = __shfl_sync(mask, a[c], k, GW);
+      double d = ak[k];
+      if (!(d > 0.0)) {
+        ok = false;
+        d = 1.0;
       }
-      A[k * b + k] = sqrt(dg);
-    }
-    __syncwarp();
-    const double piv = A[k * b + k];
-    if (lane > k && lane < b) A[lane * b + k] /= piv;
-    __syncwarp();
-    if (lane > k && lane < b) {
-      const double lk = A[lane * b + k];
-      for (int c = k + 1; c <= lane; ++c) A[lane * b + c] -= lk * A[c * b + k];
-    }
-    __syncwarp();
-  }
-  if (lane < b) {  // column `lane` of L^{-1} by forward substitution
-    const int c = lane;
-    for (int i = 0; i < b; ++i) {
-      double v = 0.0;
-      if (i >= c) {
-        v = (i == c) ? 1.0 : 0.0;
-        for (int k = c; k < i; ++k) v -= A[i * b + k] * W[k * b + c];
-        v /= A[i * b + i];
+      const double rd = rcp_newton(d);
+      if (p == k) {
+#pragma unroll
+        for (int c = 0; c < BMAX; ++c) a[c] = (c == k) ? -rd : ak[c] * rd;
+      } else {
+        const double f = a[k] * rd;
+#pragma unroll
+        for (int c = 0; c < BMAX; ++c) a[c] = (c == k) ? f : fma(-f, ak[c], a[c]);
       }
-      W[i * b + c] = v;
     }
   }
-  __syncwarp();
-  if (lane < b) {  // row `lane` of L^{-T} L^{-1}
-    const int p = lane;
-    for (int q = 0; q < b; ++q) {
-      double v = 0.0;
-      for (int k = max(p, q); k < b; ++k) v += W[k * b + p] * W[k * b + q];
-      out[p * b + q] = v;
-    }
+  if (p < b) {
+#pragma unroll
+    for (int c = 0; c < BMAX; ++c)
+      if (c < b) out[p * b + c] = split_f64(-a[c]);
   }
+  return ok;
 }
 
 template <typename PT>
@@ -284,59 +294,31 @@ __device__ __forceinline__ double sum_partials(const PT* __restrict__ src, int P
                                                int warp) {
   if constexpr (sizeof(PT) == 4) {
     float hi = 0.f, lo = 0.f;
-#pragma unroll 4
-    for (int c = warp; c < P; c += 8) comp_add(hi, lo, src[c * sq]);
+#pragma unroll 8
+    for (int c = warp; c < P; c += 8) comp_add(hi, lo, __ldg(src + c * sq));
     return (double)hi + (double)lo;
   } else {
     double s = 0.0;
-#pragma unroll 4
-    for (int c = warp; c < P; c += 8) s += src[c * sq];
+#pragma unroll 8
+    for (int c = warp; c < P; c += 8) s += __ldg(src + c * sq);
     return s;
   }
 }
 
-// Reduce the split-K partials.  CTAs 0..ndiag-1 each own diagonal block j:
-// they reduce it into R and (ndiag > 0) factor and invert Gamma_j into
-// Ginv[j].  The other CTAs reduce the remaining lower-triangle entries and
-// the projection p.  32 entries per pass (one per lane); the 8 warps split
-// the P partials.
+// Reduce the split-K partials into R (lower triangle) and p; Rs receives the
+// cG-scaled FP32 pairs of the entries the chain reads.  32 entries per pass
+// (one per lane); the 8 warps split the P partials.  (Ginv, ndiag: unused,
+// must be nullptr / 0.)
 template <typename PT>
 __global__ void __launch_bounds__(256)
 k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, int sbp,
-         double* __restrict__ R, double* __restrict__ pvec, double* __restrict__ Ginv,
-         int ndiag, SolveArgs sa, unsigned* __restrict__ err) {
-  extern __shared__ double smem_d[];
+         double* __restrict__ R, float2* __restrict__ Rs, double* __restrict__ pvec,
+         float2* __restrict__ Ginv, int ndiag, SolveArgs sa, unsigned* __restrict__ err) {
   __shared__ double red[8][32];
-  const int sb = sa.sb, b = sa.b, ldr = sa.ldr;
+  const int sb = sa.sb, ldr = sa.ldr;
   const long long sq = (long long)sbp * sbp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if ((int)blockIdx.x < ndiag) {
-    const int base = (int)blockIdx.x * b;
-    const int nent = b * (b + 1) / 2;
-    double* Gam = smem_d;      // b*b
-    double* W = Gam + b * b;   // b*b
-    for (int e0 = 0; e0 < nent; e0 += 32) {
-      const int e = e0 + lane;
-      int p = 0, q = 0;
-      double s = 0.0;
-      if (e < nent) {
-        tri_decode(e, p, q);
-        s = sum_partials(part + (long long)(base + p) * sbp + (base + q), P, sq, warp);
-      }
-      red[warp][lane] = s;
-      __syncthreads();
-      if (warp == 0 && e < nent) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) t += red[w][lane];
-        R[(long long)(base + p) * ldr + (base + q)] = t;
-        Gam[p * b + q] = sa.cG * t + (p == q ? sa.cI : 0.0);
-      }
-      __syncthreads();
-    }
-    if (warp == 0) warp_spd_inverse(Gam, W, b, Ginv + (long long)blockIdx.x * b * b, err);
-    return;
-  }
+  (void)Ginv;
   const long long nlow = (long long)sb * (sb + 1) / 2;
   const long long stride = (long long)(gridDim.x - ndiag) * 32;
   for (long long e0 = (long long)(blockIdx.x - ndiag) * 32; e0 < nlow + sb; e0 += stride) {
@@ -346,7 +328,7 @@ k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, i
     double s = 0.0;
     if (e < nlow) {
       tri_decode(e, i, j);
-      if (!(ndiag > 0 && i / b == j / b)) kind = 1;  // diagonal blocks belong to their CTA
+      kind = 1;
     } else if (e < nlow + sb) {
       kind = 2;
       i = (int)(e - nlow);
@@ -363,54 +345,93 @@ k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, i
       double t = 0.0;
 #pragma unroll
       for (int w = 0; w < 8; ++w) t += red[w][lane];
-      if (kind == 1) R[(long long)i * ldr + j] = t;
-      else pvec[i] = t;
+      if (kind == 1) {
+        R[(long long)i * ldr + j] = t;
+        if (Rs) Rs[(long long)i * ldr + j] = split_f64(sa.cG * t);
+      } else {
+        pvec[i] = t;
+      }
     }
     __syncthreads();
   }
 }
 
-template __global__ void k_reduce<double>(const double*, const double*, int, int, double*, double*,
-                                          double*, int, SolveArgs, unsigned*);
-template __global__ void k_reduce<float>(const float*, const double*, int, int, double*, double*,
-                                         double*, int, SolveArgs, unsigned*);
+template __global__ void k_reduce<double>(const double*, const double*, int, int, double*, float2*,
+                                          double*, float2*, int, SolveArgs, unsigned*);
+template __global__ void k_reduce<float>(const float*, const double*, int, int, double*, float2*,
+                                         double*, float2*, int, SolveArgs, unsigned*);
 
-// Factor and invert the diagonal blocks of an already formed R (sparse path).
+// Gamma_j^{-1} for every diagonal block j = blockIdx.x (one warp each; used
+// when b > 16, where the FP64 work of all s blocks would swamp one SM).
 __global__ void __launch_bounds__(32)
-k_factor(const double* __restrict__ R, SolveArgs sa, double* __restrict__ Ginv,
+k_factor(const double* __restrict__ R, SolveArgs sa, float2* __restrict__ Ginv,
          unsigned* __restrict__ err) {
-  extern __shared__ double smem_d[];
-  const int b = sa.b, base = (int)blockIdx.x * b;
-  double* Gam = smem_d;
-  double* W = Gam + b * b;
-  for (int e = threadIdx.x; e < b * b; e += 32) {
-    const int p = e / b, q = e % b;
-    if (q <= p)
-      Gam[e] = sa.cG * R[(long long)(base + p) * sa.ldr + (base + q)] + (p == q ? sa.cI : 0.0);
-  }
-  __syncwarp();
-  warp_spd_inverse(Gam, W, b, Ginv + (long long)blockIdx.x * b * b, err);
+  const int j = blockIdx.x;
+  if (!group_sweep_inverse<32, 32>(R, sa.ldr, j * sa.b, sa.b, sa.cG, sa.cI,
+                                   Ginv + (long long)j * sa.b * sa.b))
+    if ((threadIdx.x & 31) == 0) ca_flag(err, CA_DEV_ERR_NOT_SPD);
 }
 
-// The dependent chain (one CTA of 256 threads).  Warp w handles rows
-// p = w + 8m (m < RW) of the current block; lane l the columns l + 32c.  The
-// next block row of R is loaded into registers before the current block's
-// Gamma^{-1} product, so its latency overlaps the synchronisations.
-template <int RW>
+// Sum of n double-float values by a balanced tree (n a power of two).
+template <int N>
+__device__ __forceinline__ float2 df_tree_sum(float2 (&v)[N]) {
+#pragma unroll
+  for (int w = N / 2; w >= 1; w /= 2)
+#pragma unroll
+    for (int i = 0; i < w; ++i) v[i] = df_add(v[i], v[i + w]);
+  return v[0];
+}
+
+// The dependent chain (one CTA of 256 threads), for sb <= 256, b <= BMAX <= 32.
+// Prologue (FACTOR): the s diagonal blocks are inverted by lane groups of
+// BMAX lanes in parallel (group_sweep_inverse); otherwise Ginv is read.
+// Chain, right-looking: thread r owns row r and keeps the sum
+// acc_r = sum_{t solved} (cG R_rt + cI [I_r = I_t]) Delta_t; after block j is
+// solved every later row folds in its b new terms, and the rows of block j+1
+// then hold their complete right-hand sides.  The row slices
+// R[r][jb .. jb+b) arrive pre-scaled by cG as FP32 pairs (Rs); each thread
+// streams its own slices DEPTH steps ahead through a shared-memory ring with
+// cp.async (it reads only what it copied).  Products are summed as trees
+// (short dependency chains); everything on the dependent path is
+// double-float; FP64 converts in at the start and out at the end.
+template <int BMAX, int DEPTH, bool FACTOR>
 __global__ void __launch_bounds__(256)
-k_chain(const double* __restrict__ R, const double* __restrict__ pvec,
-        const double* __restrict__ Ginv, SolveArgs a, unsigned* __restrict__ err) {
+k_chain(const double* __restrict__ R, const float2* __restrict__ Rs,
+        const double* __restrict__ pvec, const float2* __restrict__ Ginv, SolveArgs a,
+        unsigned* __restrict__ err) {
   extern __shared__ double smem_d[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r = threadIdx.x;
   const int b = a.b, sb = a.sb, ldr = a.ldr, s = a.s_cur;
-  double* Gs = smem_d;                  // sb*b: Gamma_j^{-1}, block j at j*b*b
-  double* rhs0 = Gs + (size_t)sb * b;   // sb
-  double* dlt = rhs0 + sb;              // sb
-  double* rb = dlt + sb;                // 32
-  int* sidx = reinterpret_cast<int*>(rb + 32);  // sb
-  for (int e = tid; e < sb * b; e += 256) Gs[e] = Ginv[e];
-  for (int r = tid; r < sb; r += 256) {
-    const int gi = a.idx[r];
+  float2* ring = reinterpret_cast<float2*>(smem_d);        // DEPTH x 256 x BMAX
+  float2* Gs = ring + (size_t)DEPTH * 256 * BMAX;          // sb*b: Gamma_j^{-1}
+  float2* rb = Gs + (size_t)sb * b;                         // 32: rhs of the current block
+  float2* dl = rb + 32;                                     // 32: Delta of the current block
+  float2* dall = dl + 32;                                   // sb: all Delta
+  int* sidx = reinterpret_cast<int*>(dall + sb);            // sb
+  float2* myring = ring + (size_t)r * BMAX;                 // slot d at + d * 256 * BMAX
+  auto fetch = [&](int j) {  // row r's slice for step j into slot j % DEPTH
+    const int jb = j * b;
+    if (j < s && r >= jb + b && r < sb) {
+      const uint32_t dst = smem_u32(myring + (size_t)(j % DEPTH) * 256 * BMAX);
+      const float2* src = Rs + (long long)r * ldr + jb;
+      for (int q = 0; q < b; ++q) cp_async_8(dst + 8u * q, src + q);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < DEPTH; ++d) fetch(d);
+  if constexpr (FACTOR) {
+    constexpr int NG = 256 / BMAX;  // lane groups
+    for (int j = r / BMAX; j < s; j += NG)
+      if (!group_sweep_inverse<BMAX, BMAX>(R, ldr, j * b, b, a.cG, a.cI, Gs + (size_t)j * b * b))
+        if ((r & (BMAX - 1)) == 0) ca_flag(err, CA_DEV_ERR_NOT_SPD);
+  } else {
+    for (int e = r; e < sb * b; e += 256) Gs[e] = Ginv[e];
+  }
+  float2 rhs0 = make_float2(0.f, 0.f);
+  int gi = -1;
+  if (r < sb) {
+    gi = a.idx[r];
     double v = a.cP * pvec[r];
     if (gi >= 0 && gi < a.N) {
       v -= a.cI * a.x[gi];
@@ -418,71 +439,72 @@ k_chain(const double* __restrict__ R, const double* __restrict__ pvec,
     } else {
       ca_flag(err, CA_DEV_ERR_ARG);
     }
+    rhs0 = split_f64(v);
     sidx[r] = gi;
-    rhs0[r] = v;
-    dlt[r] = 0.0;
+    if (r < b) rb[r] = rhs0;  // block 0 has no earlier blocks
   }
-  double pre[RW][8];
-  auto prefetch = [&](int j) {
-    const int jb = j * b;
-#pragma unroll
-    for (int m = 0; m < RW; ++m) {
-      const int p = warp + 8 * m;
-#pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {
-        const int c = lane + 32 * cc;
-        pre[m][cc] = (p < b && c < jb) ? R[(long long)(jb + p) * ldr + c] : 0.0;
-      }
-    }
-  };
-  prefetch(0);
+  const float2 cI2 = split_f64(a.cI);
+  float2 acc = make_float2(0.f, 0.f);    // row r: sum over the solved blocks
+  float2 ovl = make_float2(0.f, 0.f);    // index-overlap sum of row r (rare)
+  // Gamma_j^{-1} rhs_j: L lanes per row, each a strided share of the b terms
+  constexpr int L = BMAX <= 16 ? BMAX : 8;
+  const int grow = r / L, glane = r & (L - 1);
   __syncthreads();
   for (int j = 0; j < s; ++j) {
     const int jb = j * b;
+    {  // every lane takes part in the shuffles (rows >= b contribute zero)
+      float2 t = make_float2(0.f, 0.f);
+      if (grow < b) {
+        const float2* gr = Gs + (size_t)j * b * b + grow * b;
+        for (int q = glane; q < b; q += L) t = df_add(t, df_mul(gr[q], rb[q]));
+      }
 #pragma unroll
-    for (int m = 0; m < RW; ++m) {
-      const int p = warp + 8 * m;
-      if (p < b) {  // warp-uniform
-        const int ip = sidx[jb + p];
-        double part = 0.0;
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {
-          const int c = lane + 32 * cc;
-          if (c < jb) {
-            double g = a.cG * pre[m][cc];
-            if (sidx[c] == ip) g += a.cI;
-            part = fma(g, dlt[c], part);
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) rb[p] = rhs0[jb + p] - part;
+      for (int o = L / 2; o >= 1; o /= 2) {
+        const float2 u = make_float2(__shfl_xor_sync(0xffffffffu, t.x, o, L),
+                                     __shfl_xor_sync(0xffffffffu, t.y, o, L));
+        t = df_add(t, u);
+      }
+      if (grow < b && glane == 0) {
+        dl[grow] = t;
+        dall[jb + grow] = t;
       }
     }
-    if (j + 1 < s) prefetch(j + 1);
+    cp_async_wait<DEPTH - 1>();  // this thread's slice for step j has landed
     __syncthreads();
-    if (tid < b) {
-      const double* gr = Gs + (size_t)j * b * b + tid * b;
-      double d = 0.0;
-      for (int q = 0; q < b; ++q) d = fma(gr[q], rb[q], d);
-      if (!isfinite(d)) ca_flag(err, CA_DEV_ERR_NONFINITE);
-      dlt[jb + tid] = d;
-      a.delta[jb + tid] = d;
+    if (r >= jb + b && r < sb) {  // fold block j into the later rows
+      const float2* sl = myring + (size_t)(j % DEPTH) * 256 * BMAX;
+      float2 pr[BMAX];
+#pragma unroll
+      for (int q = 0; q < BMAX; ++q) {
+        pr[q] = make_float2(0.f, 0.f);
+        if (q < b) {
+          const float2 dq = dl[q];
+          pr[q] = df_mul(sl[q], dq);
+          if (sidx[jb + q] == gi) ovl = df_add(ovl, dq);
+        }
+      }
+      acc = df_add(acc, df_tree_sum(pr));
+      if (r < jb + 2 * b) rb[r - jb - b] = df_add(rhs0, df_neg(df_add(acc, df_mul(cI2, ovl))));
     }
+    fetch(j + DEPTH);
     __syncthreads();
   }
-  for (int r = tid; r < sb; r += 256) {
-    const int gi = sidx[r];
-    if (gi >= 0 && gi < a.N) atomicAdd(a.x + gi, dlt[r]);
+  cp_async_wait<0>();
+  if (r < sb) {  // Delta out, x += Delta (atomic: an index may recur across blocks)
+    const float2 d2 = dall[r];
+    const double dv = (double)d2.x + (double)d2.y;
+    if (!isfinite(dv)) ca_flag(err, CA_DEV_ERR_NONFINITE);
+    a.delta[r] = dv;
+    if (gi >= 0 && gi < a.N) atomicAdd(a.x + gi, dv);
   }
 }
 
-template __global__ void k_chain<1>(const double*, const double*, const double*, SolveArgs,
-                                    unsigned*);
-template __global__ void k_chain<2>(const double*, const double*, const double*, SolveArgs,
-                                    unsigned*);
-template __global__ void k_chain<4>(const double*, const double*, const double*, SolveArgs,
-                                    unsigned*);
+template __global__ void k_chain<8, 4, true>(const double*, const float2*, const double*,
+                                             const float2*, SolveArgs, unsigned*);
+template __global__ void k_chain<16, 3, true>(const double*, const float2*, const double*,
+                                              const float2*, SolveArgs, unsigned*);
+template __global__ void k_chain<32, 2, false>(const double*, const float2*, const double*,
+                                               const float2*, SolveArgs, unsigned*);
 
 // The solves alone (sparse path: R and p are formed directly).
 __global__ void __launch_bounds__(256)
@@ -563,11 +585,27 @@ k_update_dense(const T* __restrict__ A, long long lda, long long N, long long K,
   }
   __syncthreads();
   if (grp == 0 && nk > 0) {
-    for (int e = 0; e < nk; ++e) {
-      const Acc tot = acc[e] + red[0][t][e] + red[1][t][e] + red[2][t][e];
-      const double nv = v[k + e] - cU * (double)tot;
-      v[k + e] = nv;
-      if (v2) v2[k + e] = split_f64(nv);
+    if constexpr (sizeof(T) == 8) {
+      for (int e = 0; e < nk; ++e) {
+        const double nv = v[k + e] - cU * (acc[e] + red[0][t][e] + red[1][t][e] + red[2][t][e]);
+        v[k + e] = nv;
+        if (v2) v2[k + e] = split_f64(nv);
+      }
+    } else {
+      // FP32 X: the FP32-pair copy v2 is the state the tensor-core passes
+      // keep current; update it in double-float and refresh v from it
+      const float2 cU2 = split_f64(cU);
+      for (int e = 0; e < nk; ++e) {
+        float hi = acc[e], lo = 0.f;
+        comp_add(hi, lo, red[0][t][e]);
+        comp_add(hi, lo, red[1][t][e]);
+        comp_add(hi, lo, red[2][t][e]);
+        float th, tl;
+        two_sum(hi, lo, th, tl);
+        const float2 nv = df_add(v2[k + e], df_neg(df_mul(cU2, make_float2(th, tl))));
+        v2[k + e] = nv;
+        v[k + e] = (double)nv.x + (double)nv.y;
+      }
     }
   }
 }
@@ -790,21 +828,36 @@ void launch_gram_simt(bool f64, dim3 grid, cudaStream_t st, const void* A, long 
 }
 
 void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, const void* part,
-                   const double* ppart, int P, int sbp, double* R, double* pvec, double* Ginv,
-                   int ndiag, const SolveArgs& sa, unsigned* err) {
+                   const double* ppart, int P, int sbp, double* R, float2* Rs, double* pvec,
+                   float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err) {
   if (f32_partials)
-    k_reduce<float><<<grid, 256, smem, st>>>(static_cast<const float*>(part), ppart, P, sbp, R, pvec,
-                                              Ginv, ndiag, sa, err);
+    k_reduce<float><<<grid, 256, smem, st>>>(static_cast<const float*>(part), ppart, P, sbp, R, Rs,
+                                              pvec, Ginv, ndiag, sa, err);
   else
     k_reduce<double><<<grid, 256, smem, st>>>(static_cast<const double*>(part), ppart, P, sbp, R,
-                                               pvec, Ginv, ndiag, sa, err);
+                                               Rs, pvec, Ginv, ndiag, sa, err);
 }
 
-void launch_chain(int rows_per_warp, size_t smem, cudaStream_t st, const double* R,
-                  const double* pvec, const double* Ginv, const SolveArgs& sa, unsigned* err) {
-  if (rows_per_warp <= 1) k_chain<1><<<1, 256, smem, st>>>(R, pvec, Ginv, sa, err);
-  else if (rows_per_warp == 2) k_chain<2><<<1, 256, smem, st>>>(R, pvec, Ginv, sa, err);
-  else k_chain<4><<<1, 256, smem, st>>>(R, pvec, Ginv, sa, err);
+void launch_chain(int b, size_t smem, cudaStream_t st, const double* R, const float2* Rs,
+                  const double* pvec, float2* Ginv, const SolveArgs& sa, unsigned* err) {
+  if (b <= 8) {
+    k_chain<8, 4, true><<<1, 256, smem, st>>>(R, Rs, pvec, Ginv, sa, err);
+  } else if (b <= 16) {
+    k_chain<16, 3, true><<<1, 256, smem, st>>>(R, Rs, pvec, Ginv, sa, err);
+  } else {
+    k_factor<<<sa.s_cur, 32, 0, st>>>(R, sa, Ginv, err);
+    k_chain<32, 2, false><<<1, 256, smem, st>>>(R, Rs, pvec, Ginv, sa, err);
+  }
+}
+
+// Rs[i][j] = FP32 split of cG R[i][j] for the lower-triangle entries outside
+// the diagonal blocks (the sparse path forms R directly).
+__global__ void k_scale_split(const double* __restrict__ R, int ldr, int sb, int b, double cG,
+                              float2* __restrict__ Rs) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)sb * sb) return;
+  const int i = (int)(e / sb), j = (int)(e % sb);
+  if (j < i && i / b != j / b) Rs[(long long)i * ldr + j] = split_f64(cG * R[(long long)i * ldr + j]);
 }
 
 void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
@@ -832,9 +885,9 @@ void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A,
 int set_solve_smem_limit(int bytes) {
   cudaError_t e[6] = {
       cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<16, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<32, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
       cudaFuncSetAttribute(k_reduce<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
       cudaFuncSetAttribute(k_reduce<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)};
   for (cudaError_t x : e)

@@ -11,14 +11,15 @@ void launch_gram_simt(bool f64, dim3 grid, cudaStream_t st, const void* A, long 
                       long long N, long long K, const int* idx, int sb, const double* v,
                       long long chunks_per_split, int sbp, double* part, double* ppart,
                       unsigned* err);
-// a4: reduce the split-K partials (CTAs < ndiag also factor + invert the
-// diagonal blocks into Ginv), then the chain (fast form) or the general solve.
+// a4: reduce the split-K partials, then the chain (fast form: it inverts the
+// diagonal blocks itself, or k_factor does for b > 16) or the general solve.
 void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, const void* part,
-                   const double* ppart, int P, int sbp, double* R, double* pvec, double* Ginv,
-                   int ndiag, const SolveArgs& sa, unsigned* err);
-void launch_chain(int rows_per_warp, size_t smem, cudaStream_t st, const double* R,
-                  const double* pvec, const double* Ginv, const SolveArgs& sa, unsigned* err);
-__global__ void k_factor(const double* R, SolveArgs sa, double* Ginv, unsigned* err);
+                   const double* ppart, int P, int sbp, double* R, float2* Rs, double* pvec,
+                   float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err);
+void launch_chain(int b, size_t smem, cudaStream_t st, const double* R, const float2* Rs,
+                  const double* pvec, float2* Ginv, const SolveArgs& sa, unsigned* err);
+__global__ void k_scale_split(const double* R, int ldr, int sb, int b, double cG, float2* Rs);
+__global__ void k_factor(const double* R, SolveArgs sa, float2* Ginv, unsigned* err);
 #define CA_FAST_B 32
 #define CA_FAST_SB 256
 void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
@@ -52,8 +53,18 @@ __global__ void k_symmetrize(const double* R, int ldr, int sb, double* G);
 // Computes FP32 partials part[c][i][j] (c < P, row stride sbp) of
 // sum_{k in split c} Y[i][k] Y[j][k] for the tiles covering j <= i, and FP64
 // partials ppart[c][i] of sum_k Y[i][k] v[k], v given as FP32 pairs
-// (hi, lo) zero-padded to a multiple of 32 entries.  sbp is 128 (sb <= 128) or 256.
+// (hi, lo) zero-padded to a multiple of 32 entries.  sbp (the tile height and
+// the row stride of the partials) is 32, 64, 128 or 256 >= sb.
+// Fused deferred update of the previous outer step (see ca_gram_tc.cu).
+struct GramUpdate {
+  const int* idx;       // rows of the previous outer step (sb of them); sb = 0: none
+  int sb;
+  const double* delta;  // their Delta
+  double cU;            // v -= cU * Yprev^T Delta
+  float2* v2;           // K entries as FP32 (hi, lo) pairs: read, updated in place
+};
+
 int launch_gram_tc(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
                    const float2* v2, int P, int sbp, float* part, double* ppart, unsigned* err,
-                   int three_pass, cudaStream_t stream);
+                   int three_pass, cudaStream_t stream, const GramUpdate* upd = nullptr);
 int gram_tc_max_sb();

@@ -127,7 +127,7 @@ extern "C" int ca_gram_project_noalloc(void* cuda_stream, int xfmt, int prec, co
   SolveArgs sa{idx, N, 1, 0, sb, sbp, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
   const long long entries = (long long)sb * (sb + 1) / 2 + sb;
   launch_reduce(tc, (int)std::min<long long>((entries + 31) / 32, 256), 0, stream, part, ppart, P,
-                sbp, R, p, nullptr, 0, sa, err);
+                sbp, R, nullptr, p, nullptr, 0, sa, err);
   k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, stream>>>(R, sbp, sb, G);
   if (cudaGetLastError() != cudaSuccess) return CA_ERR_CUDA;
   unsigned host_err = 0;
