@@ -2,10 +2,14 @@
 
 Workload (the dense primal FP32 configuration): X 4096 x 262144 FP32 with
 geometrically scaled rows (condition 1e3), y = X^T w_true + 1% noise,
-lambda = 1e-4, b = 8, s = 32, H = 4096 block updates, FP32-faithful Gram on
-the tensor cores (3xTF32 split products, FP32 accumulation), FP64 solves.  One step = one full solve (sampling, H/s outer steps of
+lambda = 1e-4, b = 8, s = 16, H = 4096 block updates, FP32-faithful Gram on
+the tensor cores (3xTF32 split products, FP32 accumulation), FP64-accurate
+solves.  One step = one full solve (sampling, H/s outer steps of
 gather+Gram+projection, inner solves, deferred update, and the final
 z = X^T w_H pass) with X resident in HBM.  X (4 GiB) is larger than L2.
+The value comes from K timed solves without per-kernel events; the roofline
+and the per-kernel breakdown from a second timed pass of K solves with CUDA
+events around every launch (they cost a few percent of throughput).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -30,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CA-BCD block-updates/s"
 UNIT = "block-updates/s"
-D, N_SAMPLES, COND, LAM, B, S, H = 4096, 262144, 1e3, 1e-4, 8, 32, 4096
+D, N_SAMPLES, COND, LAM, B, S, H = 4096, 262144, 1e3, 1e-4, 8, 16, 4096
 PREC = "3xtf32"
 
 
@@ -166,17 +170,17 @@ def time_solves(ctx, X, y, w, z, steps, stream, b=B, s=S, h=H, prec=PREC):
 
 def cpu_baseline(X_host_f32, y_host, budget_s: float = 30.0):
     """The FP64 oracle as it stands (single thread) on a bounded sample of the
-    workload: the first outer step (s = 32 block updates) of the same solve."""
+    workload: the first 4 outer steps (4 s block updates) of the same solve."""
     import numpy as np
     import oracle
     X64 = X_host_f32.astype(np.float64)
-    h_sample = S
+    h_sample = 4 * S
     t0 = time.perf_counter()
     oracle.ca_bcd(X64, y_host, LAM, b=B, s=S, H=h_sample, seed=42)
     dt = time.perf_counter() - t0
     return {"value": h_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first outer step ({h_sample} block updates, b={B}, s={S}) of the same "
-                      f"{D}x{N_SAMPLES} solve, FP64 C oracle, single thread; {dt:.2f} s"}
+            "sample": f"first 4 outer steps ({h_sample} block updates, b={B}, s={S}) of the "
+                      f"same {D}x{N_SAMPLES} solve, FP64 C oracle, single thread; {dt:.2f} s"}
 
 
 def run_reference(args, rank: int, world: int):
@@ -225,6 +229,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--s", type=int, default=None, help="unrolling depth (default %d)" % S)
+    ap.add_argument("--n", type=int, default=None,
+                    help="samples (columns of X); smaller than the default only for profiler captures")
+    ap.add_argument("--h", type=int, default=None, help="block updates per solve (default %d)" % H)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -234,6 +241,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     s_run = args.s or S
+    n_run = args.n or N_SAMPLES
+    h_run = args.h or H
 
     import numpy as np
     import torch
@@ -247,36 +256,43 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    X, y, _ = synth.dense_primal_torch(D, N_SAMPLES, cond=COND, seed=1, device="cuda")
+    X, y, _ = synth.dense_primal_torch(D, n_run, cond=COND, seed=1, device="cuda")
     w = torch.zeros(D, dtype=torch.float64, device="cuda")
-    z = torch.zeros(N_SAMPLES, dtype=torch.float64, device="cuda")
+    z = torch.zeros(n_run, dtype=torch.float64, device="cuda")
     ctx = ca.Context(local_rank, stream=stream.cuda_stream)
 
     # warm-up
-    time_solves(ctx, X, y, w, z, args.warmup, stream, s=s_run)
-    # timed region
-    ctx.ca_profile_enable(True)
+    time_solves(ctx, X, y, w, z, args.warmup, stream, s=s_run, h=h_run)
+    # timed region (value): K solves, no per-kernel events
+    ctx.ca_profile_enable(False)  # resets the launch counter
     clocks = ClockSampler(local_rank)
     clocks.start()
     barrier(world)
-    ms = time_solves(ctx, X, y, w, z, args.steps, stream, s=s_run)
+    ms = time_solves(ctx, X, y, w, z, args.steps, stream, s=s_run, h=h_run)
+    barrier(world)
+    launches = ctx.ca_profile_read()["kernel_launches"]
+    # second timed pass (roofline, breakdown): the same K solves with CUDA
+    # events around every launch, on the library's stream
+    ctx.ca_profile_enable(True)
+    barrier(world)
+    ms_prof = time_solves(ctx, X, y, w, z, args.steps, stream, s=s_run, h=h_run)
     barrier(world)
     clocks.stop()
     prof = ctx.ca_profile_read()
     ctx.ca_profile_enable(False)
     ms_step = max_over_ranks(ms / args.steps, world)
-    value = world * H / (ms_step * 1e-3)
+    value = world * h_run / (ms_step * 1e-3)
 
     # roofline of the dominant kernel (the tcgen05 Gram pass, one launch per outer step)
     peaks, peak_kind = _peaks()
     sb = s_run * B
     gram_ms = prof["gram_ms"] / max(1, prof["gram_launches"])
-    n_outer = -(-H // s_run)
+    n_outer = -(-h_run // s_run)
     fused = sb <= 128 and PREC in ("tf32", "3xtf32")  # a5 of step k rides in the a2+a3 launch of k+1
-    b_gram = sb * N_SAMPLES * 4 + N_SAMPLES * 8          # B_G: Y rows + the projection vector
-    b_upd = sb * N_SAMPLES * 4 + 2 * N_SAMPLES * 8       # B_U: Y rows + read/write of v
+    b_gram = sb * n_run * 4 + n_run * 8          # B_G: Y rows + the projection vector
+    b_upd = sb * n_run * 4 + 2 * n_run * 8       # B_U: Y rows + read/write of v
     breakdown = {c: {"ms_per_step": prof[f"{c}_ms"] / args.steps,
-                     "share": prof[f"{c}_ms"] / max(ms, 1e-9)}
+                     "share": prof[f"{c}_ms"] / max(ms_prof, 1e-9)}
                  for c in ("gram", "reduce", "chain", "update", "other")}
     alg_bytes = (n_outer * b_gram + (n_outer - 1) * b_upd) / n_outer if fused else b_gram
     achieved = alg_bytes / (gram_ms * 1e-3) / 1e9
@@ -289,24 +305,27 @@ def main():
                        f"{' + deferred update of the previous outer step' if fused else ''})"),
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": gram_ms,
             "launches": prof["gram_launches"], "peak_source": f"hbm_gbs ({peak_kind})",
-            "gram_share_of_step": prof["gram_ms"] / max(ms, 1e-9)}
+            "gram_share_of_step": prof["gram_ms"] / max(ms_prof, 1e-9),
+            "measured": "CUDA events around each launch on the library stream, over a second "
+                        "timed pass of the same K solves (ms_per_step of that pass: %.3f)"
+                        % (ms_prof / args.steps)}
     roof["breakdown"] = breakdown
 
     # end to end through the C ABI with host buffers (pinned), copies inside
-    Xh = torch.empty((D, N_SAMPLES), dtype=torch.float32, pin_memory=True)
+    Xh = torch.empty((D, n_run), dtype=torch.float32, pin_memory=True)
     Xh.copy_(X)
-    yh = torch.empty(N_SAMPLES, dtype=torch.float64, pin_memory=True)
+    yh = torch.empty(n_run, dtype=torch.float64, pin_memory=True)
     yh.copy_(y)
     wh = torch.zeros(D, dtype=torch.float64, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 10))
-    ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=s_run, H=H, lam=LAM, seed=42, prec=PREC)  # warm
+    ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=s_run, H=h_run, lam=LAM, seed=42, prec=PREC)  # warm
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         wh.zero_()
-        ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=s_run, H=H, lam=LAM, seed=42, prec=PREC)
+        ctx.ca_bcd_solve(Xh, yh, wh, None, b=B, s=s_run, H=h_run, lam=LAM, seed=42, prec=PREC)
     t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
-    e2e = {"value": world * H / t_e2e, "unit": UNIT,
+    e2e = {"value": world * h_run / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 8 + wh.numel() * 8),
            "d2h_bytes_per_step": int(wh.numel() * 8), "ms_per_step": t_e2e * 1e3,
            "how": "ca_bcd_solve on pinned host X, y, w: the library copies them to the device "
@@ -319,10 +338,10 @@ def main():
         for prec_ in ("3xtf32", "tf32"):
             for (b_, s_) in [(8, 1), (8, 4), (8, 8), (8, 16), (8, 32), (32, 1), (32, 4), (32, 8)]:
                 nst = 2 if s_ == 1 else 4
-                time_solves(ctx, X, y, w, z, 1, stream, b=b_, s=s_, prec=prec_)
-                t = time_solves(ctx, X, y, w, z, nst, stream, b=b_, s=s_, prec=prec_) / nst
+                time_solves(ctx, X, y, w, z, 1, stream, b=b_, s=s_, h=h_run, prec=prec_)
+                t = time_solves(ctx, X, y, w, z, nst, stream, b=b_, s=s_, h=h_run, prec=prec_) / nst
                 sweep.append({"gram": prec_, "b": b_, "s": s_, "ms_per_step": t,
-                              "block_updates_per_s": H / (t * 1e-3)})
+                              "block_updates_per_s": h_run / (t * 1e-3)})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -334,9 +353,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "3xtf32 (fp32-faithful)", "data": "synthetic",
-            "config": workload_config(s=s_run),
+            "config": workload_config(n=n_run, s=s_run, h=h_run),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(prof["kernel_launches"]),
+            "gpu_launches": int(launches),
             "clocks": clocks.summary(), "sweep": sweep,
             "parallelism": "replicas" if world > 1 else "single GPU",
         }

@@ -67,7 +67,9 @@ typedef enum {
 typedef enum {
   CA_DENSE_F64 = 0, /* dense, FP64                                              */
   CA_DENSE_F32 = 1, /* dense, FP32                                              */
-  CA_CSR_F32 = 2    /* dual only: CSR of X^T (row i = sample i), FP32 values    */
+  CA_CSR_F32 = 2,   /* dual only: CSR of X^T (row i = sample i), FP32 values    */
+  CA_DENSE_F32_PANELS = 3 /* dense FP32 in 32-column panels (ca_pack_panels);
+                           * tcgen05 Gram modes only                          */
 } ca_xfmt;
 
 /* Arithmetic of the Gram matrix (step a3).  The projection, the solves and
@@ -111,10 +113,14 @@ typedef struct ca_ctx ca_ctx;
 int ca_bcd_init(ca_ctx** ctx, int device, void* cuda_stream, size_t scratch_bytes_max);
 
 /* Primal CA-BCD (Algorithm 2; Algorithm 1 when s = 1).
- *   xfmt  CA_DENSE_F64 or CA_DENSE_F32.
+ *   xfmt  CA_DENSE_F64, CA_DENSE_F32 or CA_DENSE_F32_PANELS.
  *   X     d x n row-major (row f = feature f), leading dimension ld >= n
  *         elements.  For the tcgen05 Gram modes, X and ld*4 bytes must be
- *         16-byte aligned.
+ *         16-byte aligned; the solve then first repacks X into 32-column
+ *         panels in its scratch (one pass over X; ca_pack_panels layout) and
+ *         reads only the panels.  CA_DENSE_F32_PANELS: X is already in that
+ *         layout (ceil(n/32) * d * 32 floats; ld is ignored); TF32 / 3xTF32
+ *         only.
  *   y     n labels (FP64).
  *   w     d (FP64): w0 on entry, w_H on return.
  *   z     NULL, or n (FP64): receives X^T w_H computed by a final full pass.
@@ -128,6 +134,9 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
 /* Dual CA-BDCD (Algorithm 4; Algorithm 3 when s = 1).
  *   xfmt  CA_DENSE_F64 / CA_DENSE_F32: XT is X^T, n x d row-major (row i =
  *         sample i = column x_i of X), leading dimension ld >= d.
+ *         CA_DENSE_F32_PANELS: X^T in 32-column panels (ceil(d/32) * n * 32
+ *         floats).  FP32 with a tcgen05 Gram mode is repacked as for the
+ *         primal.
  *         CA_CSR_F32: XT points to a ca_csr (ld is ignored).
  *   y     n labels (FP64).
  *   alpha n (FP64): alpha0 on entry, alpha_H on return.
@@ -175,6 +184,17 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
 int ca_gram_project_noalloc(void* cuda_stream, int xfmt, int prec, const void* A, long long N,
                             long long K, long long ld, const int* idx, int sb, const double* v,
                             double* G, double* p);
+
+/* Storage conversion for the tcgen05 Gram modes (not a step of the paper's
+ * method: a layout of X that the gather reads at a higher fraction of HBM
+ * bandwidth).  Writes the N x K row-major FP32 matrix A (leading dimension
+ * ld, A and ld*4 bytes 16-byte aligned) as ceil(K/32) panels of N rows x 32
+ * columns: out[(a*N + r)*32 + c] = A[r][32a + c], zero where 32a + c >= K.
+ * out holds ceil(K/32)*N*32 floats.  A and out are device memory owned by the
+ * caller; the work runs on the context's stream and the call returns when it
+ * is enqueued (pass the result to the solves as CA_DENSE_F32_PANELS).
+ * Errors: CA_ERR_ARG, CA_ERR_CUDA. */
+int ca_pack_panels(ca_ctx* ctx, const float* A, long long N, long long K, long long ld, float* out);
 
 /* Text of the last failing CUDA call seen by an entry point on this context
  * (empty if none); owned by the context, valid until the next call. */

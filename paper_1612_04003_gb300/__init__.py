@@ -28,6 +28,7 @@ CA_ERR_UNSUPPORTED = -7
 CA_DENSE_F64 = 0
 CA_DENSE_F32 = 1
 CA_CSR_F32 = 2
+CA_DENSE_F32_PANELS = 3
 
 CA_GRAM_F64 = 0
 CA_GRAM_FP32_EXACT = 1
@@ -93,6 +94,8 @@ def load():
     lib.ca_last_error.restype = ctypes.c_char_p
     lib.ca_gram_project.argtypes = [vp, i32, i32, vp, i64, i64, i64, vp, i32, vp, vp, vp]
     lib.ca_gram_project.restype = i32
+    lib.ca_pack_panels.argtypes = [vp, vp, i64, i64, i64, vp]
+    lib.ca_pack_panels.restype = i32
     lib.ca_selftest_wait_timeout.argtypes = [vp, i64]
     lib.ca_selftest_wait_timeout.restype = i32
     _lib = lib
@@ -189,31 +192,43 @@ class Context:
                        int(h0))
 
     def ca_bcd_solve(self, X, y, w, z=None, *, b, s=1, H, lam, seed=42, prec="tf32",
-                     recompute_every=0, h0=0, n=None, ld=None):
+                     recompute_every=0, h0=0, n=None, ld=None, panels=None):
         """Primal CA-BCD: w (in: w0, out: w_H) and optionally z = X^T w_H.
-        X is d x ld (ld = X.shape[1]); n (default ld) columns are used."""
-        d, cols = X.shape
-        n = cols if n is None else int(n)
-        ld = cols if ld is None else int(ld)
+        X is d x ld (ld = X.shape[1]); n (default ld) columns are used.
+        panels=(d, n): X holds the 32-column panels of a d x n matrix
+        (ca_pack_panels)."""
         for a in (y, w) + ((z,) if z is not None else ()):
             if not _dtype_is_f64(a):
                 raise TypeError("y, w, z must be float64")
         o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0)
-        st = self._lib.ca_bcd_solve(self.handle, _xfmt(X), _ptr(X), d, n, ld,
+        if panels is not None:
+            d, n = (int(v) for v in panels)
+            xf, ld = CA_DENSE_F32_PANELS, 0
+        else:
+            d, cols = X.shape
+            n = cols if n is None else int(n)
+            ld = cols if ld is None else int(ld)
+            xf = _xfmt(X)
+        st = self._lib.ca_bcd_solve(self.handle, xf, _ptr(X), d, n, ld,
                                     _ptr(y), ctypes.byref(o), _ptr(w), _ptr(z))
         if st != CA_OK:
             raise CaError(st, "ca_bcd_solve", self.last_error())
         return w, z
 
     def ca_bdcd_solve(self, XT, y, alpha, w, *, b, s=1, H, lam, seed=42, prec="tf32",
-                      recompute_every=0, h0=0, d=None, ld=None):
-        """Dual CA-BDCD.  XT is X^T (n x d, dense) or a (rowptr, col, val) CSR
-        triple of X^T (then d must be given)."""
+                      recompute_every=0, h0=0, d=None, ld=None, panels=None):
+        """Dual CA-BDCD.  XT is X^T (n x d, dense), a (rowptr, col, val) CSR
+        triple of X^T (then d must be given), or with panels=(n, d) the
+        32-column panels of X^T (ca_pack_panels)."""
         for a in (y, alpha, w):
             if not _dtype_is_f64(a):
                 raise TypeError("y, alpha, w must be float64")
         o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0)
-        if isinstance(XT, (tuple, list)):
+        if panels is not None:
+            n, dd = (int(v) for v in panels)
+            st = self._lib.ca_bdcd_solve(self.handle, CA_DENSE_F32_PANELS, _ptr(XT), dd, n, 0,
+                                         _ptr(y), ctypes.byref(o), _ptr(alpha), _ptr(w))
+        elif isinstance(XT, (tuple, list)):
             rowptr, col, val = XT
             csr = ca_csr(_ptr(rowptr), _ptr(col), _ptr(val))
             n = int(rowptr.shape[0]) - 1
@@ -245,6 +260,17 @@ class Context:
         if st != CA_OK:
             raise CaError(st, "ca_gram_project", self.last_error())
         return G, p
+
+    def ca_pack_panels(self, A, out, *, K=None):
+        """Write the first K (default all) columns of the FP32 device matrix A
+        (N x ld) as 32-column panels into out (ceil(K/32)*N*32 floats,
+        device), on the context's stream."""
+        N, ld = A.shape
+        K = ld if K is None else int(K)
+        st = self._lib.ca_pack_panels(self.handle, _ptr(A), N, K, ld, _ptr(out))
+        if st != CA_OK:
+            raise CaError(st, "ca_pack_panels", self.last_error())
+        return out
 
     def ca_selftest_wait_timeout(self, limit_ns: int) -> int:
         return int(self._lib.ca_selftest_wait_timeout(self.handle, int(limit_ns)))

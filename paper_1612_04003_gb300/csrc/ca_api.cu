@@ -21,7 +21,8 @@ enum { PC_GRAM = 0, PC_SOLVE = 1, PC_UPDATE = 2, PC_OTHER = 3, PC_CHAIN = 4, PC_
 
 struct Profile {
   bool on = false;
-  std::vector<std::pair<int, cudaEvent_t>> ev;  // (class, start) / (class, stop) pairs
+  std::vector<cudaEvent_t> pool;  // events, created once and reused
+  std::vector<int> cls;           // class of pool[i] for the marks of this call: start / stop pairs
   double ms[PC_N] = {0, 0, 0, 0, 0};
   long long launches[PC_N] = {0, 0, 0, 0, 0};
   long long kernel_launches = 0;
@@ -123,25 +124,29 @@ int finish(ca_ctx* ctx) {
                               ctx->stream));
   CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
   if (ctx->prof.on) {
-    for (size_t i = 0; i + 1 < ctx->prof.ev.size(); i += 2) {
+    Profile& pr = ctx->prof;
+    for (size_t i = 0; i + 1 < pr.cls.size(); i += 2) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ctx->prof.ev[i].second, ctx->prof.ev[i + 1].second);
-      ctx->prof.ms[ctx->prof.ev[i].first] += ms;
-      ctx->prof.launches[ctx->prof.ev[i].first] += 1;
+      cudaEventElapsedTime(&ms, pr.pool[i], pr.pool[i + 1]);
+      pr.ms[pr.cls[i]] += ms;
+      pr.launches[pr.cls[i]] += 1;
     }
-    for (auto& e : ctx->prof.ev) cudaEventDestroy(e.second);
-    ctx->prof.ev.clear();
+    pr.cls.clear();
   }
   return status_from_err(*ctx->h_err);
 }
 
 // Record an event of class cls on the context's stream (profiling only).
 void prof_mark(ca_ctx* ctx, int cls) {
-  if (!ctx->prof.on) return;
-  cudaEvent_t e;
-  if (cudaEventCreate(&e) != cudaSuccess) return;
-  cudaEventRecord(e, ctx->stream);
-  ctx->prof.ev.emplace_back(cls, e);
+  Profile& pr = ctx->prof;
+  if (!pr.on) return;
+  if (pr.cls.size() == pr.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    pr.pool.push_back(e);
+  }
+  cudaEventRecord(pr.pool[pr.cls.size()], ctx->stream);
+  pr.cls.push_back(cls);
 }
 
 int check_opts(const ca_opts* o, long long N) {
@@ -160,7 +165,8 @@ int check_opts(const ca_opts* o, long long N) {
 // The dense outer-step loop shared by both methods.
 struct DenseProblem {
   int xfmt;                 // CA_DENSE_F64 / CA_DENSE_F32
-  const void* A;            // N x K row-major, leading dim lda (device)
+  const void* A;            // N x K row-major, leading dim lda (device), or panels
+  bool panel = false;       // FP32 A stored as 32-column panels [K/32][N][32]
   long long N, K, lda;
   double* v;                // K: projection vector (rho or w), device
   float2* v2;               // its (hi, lo) FP32 split, zero-padded to a multiple of 32
@@ -189,7 +195,7 @@ int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const do
     ctx->prof.kernel_launches += 1;
   }
   launch_recompute_dense(pb.xfmt == CA_DENSE_F64, grid, ctx->stream, pb.A, pb.lda, N, K, pb.x, pb.x2,
-                         c1, rps, vout);
+                         c1, rps, vout, pb.panel);
   ctx->prof.kernel_launches += 2;
   if (vout == pb.v && pb.v2) {
     const long long Kp = (K + 31) / 32 * 32;
@@ -232,10 +238,11 @@ GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
 // a2+a3: split-K partials of Y Y^T and Y v for the sampled rows idx[0..sb).
 int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long long lda, long long N,
                 long long K, const int* idx, int sb, const double* v, const float2* v2, void* part,
-                double* ppart) {
+                double* ppart, bool panel = false) {
   if (g.tc) {
     const int e = launch_gram_tc(static_cast<const float*>(A), lda, N, K, idx, sb, v2, g.P, g.sbp,
-                                 static_cast<float*>(part), ppart, ctx->d_err, g.three, ctx->stream);
+                                 static_cast<float*>(part), ppart, ctx->d_err, g.three, ctx->stream,
+                                 nullptr, panel);
     return e == 0 ? CA_OK : CA_ERR_CUDA;
   }
   launch_gram_simt(xfmt == CA_DENSE_F64, dim3(g.P, g.ntiles), ctx->stream, A, lda, N, K, idx, sb, v,
@@ -246,40 +253,60 @@ int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long lo
 bool fast_solve(int b, int sb) { return b <= CA_FAST_B && sb <= CA_FAST_SB; }
 
 size_t chain_smem(int b, int sb) {
-  const size_t ring = b <= 8 ? 4 * 256 * 8 * 8 : (b <= 16 ? 3 * 256 * 16 * 8 : 2 * 256 * 32 * 8);
+  const size_t ring = b <= 8 ? 6 * 256 * 8 * 8 : (b <= 16 ? 3 * 256 * 16 * 8 : 2 * 256 * 32 * 8);
   return ring + (size_t)sb * b * 8 + 64 * 8 + (size_t)sb * 12 + 64;
 }
 
-// a4: the chain (fast form, from Rs, p, Ginv) or the general block forward
-// substitution (from R, p).
+// a4: the chain (fast form, from Rs, p and the inverted diagonal blocks
+// Ginv) or the general block forward substitution (from R, p).
 void launch_solve(ca_ctx* ctx, const double* R, const float2* Rs, const double* pvec,
-                  float2* Ginv, const SolveArgs& sa) {
+                  const float2* Ginv, const SolveArgs& sa) {
   if (fast_solve(sa.b, sa.sb)) {
-    launch_chain(sa.b, chain_smem(sa.b, sa.sb), ctx->stream, R, Rs, pvec, Ginv, sa, ctx->d_err);
+    launch_chain(sa.b, chain_smem(sa.b, sa.sb), ctx->stream, Rs, pvec, Ginv, sa, ctx->d_err);
   } else {
     k_solve<<<1, 256, (size_t)(sa.sb + sa.b * sa.b + sa.b) * sizeof(double), ctx->stream>>>(
         R, pvec, sa, ctx->d_err);
   }
 }
 
-// a4 entry: reduce the partials to R, p (+ the inverted diagonal blocks), then
-// (s_cur > 0) the inner solves.
-void launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const double* ppart,
-                         double* R, float2* Rs, double* pvec, float2* Ginv, const SolveArgs& sa) {
+// a4 entry: reduce the partials to R, p and invert the diagonal blocks (in
+// the reduce launch for b <= 16, by k_factor otherwise), then (s_cur > 0) the
+// inner solves.
+int launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const double* ppart,
+                        double* R, float2* Rs, double* pvec, float2* Ginv, const SolveArgs& sa) {
   const bool fast = sa.s_cur > 0 && fast_solve(sa.b, sa.sb);
   const long long entries = (long long)sa.sb * (sa.sb + 1) / 2 + sa.sb;
-  const int G = (int)std::max(1LL, std::min<long long>((entries + 31) / 32, 8LL * ctx->num_sms));
+  const long long passes = (entries + 31) / 32;
+  const int G = (int)std::max(1LL, std::min<long long>(passes, 8LL * ctx->num_sms));
+  const int ndiag = (fast && sa.b <= 16) ? sa.s_cur : 0;
+  if (g.tc && ndiag) {
+    // one launch: reduce (+ diagonal inverses), then the chain on the last
+    // CTA; one CTA per SM (the chain's shared memory), so at most num_sms
+    const int grid = (int)std::min<long long>(passes + ndiag, ctx->num_sms);
+    prof_mark(ctx, PC_SOLVE);
+    const int e = launch_reduce_chain(grid, chain_smem(sa.b, sa.sb), ctx->stream,
+                                      static_cast<const float*>(part), ppart, g.P, g.sbp, R, Rs,
+                                      pvec, Ginv, ndiag, sa, ctx->d_err, ctx->d_ticket);
+    prof_mark(ctx, PC_SOLVE);
+    ctx->prof.kernel_launches += 1;
+    return e != 0 ? cuda_fail((cudaError_t)e, __LINE__) : CA_OK;
+  }
   prof_mark(ctx, PC_SOLVE);
-  launch_reduce(g.tc, G, 0, ctx->stream, part, ppart, g.P, g.sbp, R, fast ? Rs : nullptr, pvec,
-                nullptr, 0, sa, ctx->d_err);
-  prof_mark(ctx, PC_SOLVE);
+  launch_reduce(g.tc, G + ndiag, 0, ctx->stream, part, ppart, g.P, g.sbp, R, fast ? Rs : nullptr,
+                pvec, ndiag ? Ginv : nullptr, ndiag, sa, ctx->d_err);
   ctx->prof.kernel_launches += 1;
+  if (fast && !ndiag) {
+    launch_factor(ctx->stream, R, sa, Ginv, ctx->d_err);
+    ctx->prof.kernel_launches += 1;
+  }
+  prof_mark(ctx, PC_SOLVE);
   if (sa.s_cur > 0) {
     prof_mark(ctx, PC_CHAIN);
     launch_solve(ctx, R, Rs, pvec, Ginv, sa);
     prof_mark(ctx, PC_CHAIN);
     ctx->prof.kernel_launches += 1;
   }
+  return cuda_status(cudaGetLastError());
 }
 
 int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_all, char* work,
@@ -303,7 +330,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   // The deferred update of outer step k (a5) runs inside the Gram launch of
   // step k+1 when the tensor-core path has s*b <= 128; otherwise, after the
   // last step, and before a due recomputation it runs on its own.
-  const bool fuse = g.tc && g.sbp <= 128;
+  const bool fuse = g.tc && g.sbp <= 128 && pb.panel;
   auto due = [&](long long k) { return o->recompute_every > 0 && (k + 1) % o->recompute_every == 0; };
   bool pending = false;  // an update (prev_*) not yet applied
   const int* prev_idx = nullptr;
@@ -314,7 +341,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     const unsigned ug = (unsigned)((K + 255) / 256);
     prof_mark(ctx, PC_UPDATE);
     launch_update_dense(pb.xfmt == CA_DENSE_F64, ug, usm, ctx->stream, pb.A, pb.lda, pb.N, K,
-                        prev_idx, prev_sb, prev_delta, pb.cU, pb.v, pb.v2, ctx->d_err);
+                        prev_idx, prev_sb, prev_delta, pb.cU, pb.v, pb.v2, ctx->d_err, pb.panel);
     prof_mark(ctx, PC_UPDATE);
     ctx->prof.kernel_launches += 1;
     pending = false;
@@ -337,17 +364,18 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     if (pending) {
       const int e = launch_gram_tc(static_cast<const float*>(pb.A), pb.lda, pb.N, K, idx, sb, pb.v2,
                                    P, sbp, static_cast<float*>(part), ppart, ctx->d_err, g.three,
-                                   ctx->stream, &gu);
+                                   ctx->stream, &gu, true);
       if (e != 0) return cuda_fail((cudaError_t)e, __LINE__);
       pending = false;
     } else {
-      CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart));
+      CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart,
+                         pb.panel));
     }
     prof_mark(ctx, PC_GRAM);
     ctx->prof.kernel_launches += 1;
     // a4 (reduce of the split-K partials, then the s unrolled solves)
     SolveArgs sa{idx, pb.N, b, sk, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, delta};
-    launch_reduce_solve(ctx, g, part, ppart, R, Rs, pvec, Ginv, sa);
+    CA_TRY(launch_reduce_solve(ctx, g, part, ppart, R, Rs, pvec, Ginv, sa));
     CA_TRY_CUDA(cudaGetLastError());
     pending = true;
     prev_idx = idx;
@@ -378,6 +406,17 @@ size_t dense_work_bytes(ca_ctx* ctx, const ca_opts* o, long long K, int xfmt) {
   }
   return align256(P * sbp * sbp * el) + align256(P * sbp * 8) + 2 * align256(sbp * sbp * 8) +
          3 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
+}
+
+size_t panel_bytes(long long N, long long K) { return (size_t)((K + 31) / 32) * (size_t)N * 128; }
+
+void launch_pack(ca_ctx* ctx, const float* A, long long N, long long K, long long lda, float* out) {
+  const long long units = N * ((K + 31) / 32);
+  const long long blocks = std::min<long long>((units * 8 + 255) / 256, 16LL * ctx->num_sms);
+  prof_mark(ctx, PC_OTHER);
+  k_pack_panels<<<(unsigned)std::max(1LL, blocks), 256, 0, ctx->stream>>>(A, N, K, lda, out);
+  prof_mark(ctx, PC_OTHER);
+  ctx->prof.kernel_launches += 1;
 }
 
 // Stage a caller array on the device (copy in when `in`), return the device pointer.
@@ -452,7 +491,7 @@ void ca_bcd_destroy(ca_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (auto& e : ctx->prof.ev) cudaEventDestroy(e.second);
+  for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -483,25 +522,30 @@ int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long l
 int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n, long long ld,
                  const double* y, const ca_opts* o, double* w, double* z) {
   t_cur_ctx = ctx;
-  if (!ctx || !X || !y || !w || d < 1 || n < 1 || ld < n) return CA_ERR_ARG;
-  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32) return CA_ERR_ARG;
+  const bool pre = xfmt == CA_DENSE_F32_PANELS;
+  if (!ctx || !X || !y || !w || d < 1 || n < 1 || (!pre && ld < n)) return CA_ERR_ARG;
+  ctx->prof.cls.clear();  // marks of an earlier call that failed before finishing
+  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32 && !pre) return CA_ERR_ARG;
   CA_TRY(check_opts(o, d));
-  const bool tc = (xfmt == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
+  const int xf = pre ? (int)CA_DENSE_F32 : xfmt;  // element type of X
+  const bool tc = (xf == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
   if (o->prec == CA_GRAM_BF16X3 || o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
+  if (pre && !tc) return CA_ERR_ARG;
   if (tc) {
-    if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return CA_ERR_ARG;
+    if ((!pre && (ld & 3) != 0) || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return CA_ERR_ARG;
     if (std::min<long long>(o->s, o->H) * o->b > gram_tc_max_sb()) return CA_ERR_UNSUPPORTED;
   }
   CA_TRY_CUDA(cudaSetDevice(ctx->device));
-  const size_t el = xfmt == CA_DENSE_F64 ? 8 : 4;
+  const size_t el = xf == CA_DENSE_F64 ? 8 : 4;
   const bool x_host = !is_device_ptr(X), y_host = !is_device_ptr(y), w_host = !is_device_ptr(w);
   const bool z_host = z && !is_device_ptr(z);
-  const size_t xbytes = (size_t)(d - 1) * ld * el + (size_t)n * el;
-  size_t need = dense_work_bytes(ctx, o, n, xfmt) + align256((size_t)n * 8) /* rho */ +
+  const size_t xbytes = pre ? panel_bytes(d, n) : (size_t)(d - 1) * ld * el + (size_t)n * el;
+  size_t need = dense_work_bytes(ctx, o, n, xf) + align256((size_t)n * 8) /* rho */ +
                 align256((size_t)(n + 31) / 32 * 32 * 8) /* rho split */ +
                 align256((size_t)d * 8) /* w split */ +
                 align256((size_t)o->H * o->b * 4) /* idx */;
   if (x_host) need += align256(xbytes) + 256;
+  if (tc && !pre) need += align256(panel_bytes(d, n)) + 256;
   if (y_host) need += align256((size_t)n * 8);
   if (w_host) need += align256((size_t)d * 8);
   if (z_host) need += align256((size_t)n * 8);
@@ -515,6 +559,13 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
     CA_TRY_CUDA(cudaMemcpyAsync(p, X, xbytes, cudaMemcpyHostToDevice, ctx->stream));
     Xd = p;
   }
+  bool panel = pre;
+  if (tc && !pre) {  // the gather reads 32-column panels (ca_pack_panels layout)
+    float* pk = cv.take<float>(panel_bytes(d, n) / 4);
+    launch_pack(ctx, static_cast<const float*>(Xd), d, n, ld, pk);
+    Xd = pk;
+    panel = true;
+  }
   const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
   double* wd = stage(ctx, cv, w, (size_t)d, true, &st);
   double* zd = z ? stage(ctx, cv, z, (size_t)n, false, &st) : nullptr;
@@ -526,8 +577,9 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
 
   DenseProblem pb;
-  pb.xfmt = xfmt;
+  pb.xfmt = xf;
   pb.A = Xd;
+  pb.panel = panel;
   pb.N = d;
   pb.K = n;
   pb.lda = ld;
@@ -565,7 +617,10 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
                   const double* y, const ca_opts* o, double* alpha, double* w) {
   t_cur_ctx = ctx;
   if (!ctx || !XT || !y || !alpha || !w || d < 1 || n < 1) return CA_ERR_ARG;
-  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32 && xfmt != CA_CSR_F32) return CA_ERR_ARG;
+  ctx->prof.cls.clear();  // marks of an earlier call that failed before finishing
+  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32 && xfmt != CA_CSR_F32 &&
+      xfmt != CA_DENSE_F32_PANELS)
+    return CA_ERR_ARG;
   CA_TRY(check_opts(o, n));
   CA_TRY_CUDA(cudaSetDevice(ctx->device));
   const double ln = o->lam * (double)n;
@@ -588,7 +643,9 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     if (c_host) need += align256((size_t)nnz * 4);
     if (v_host) need += align256((size_t)nnz * 4);
     const int sbm = (int)(std::min<long long>(o->s, o->H) * o->b);
-    const size_t sbp = (size_t)sbm;
+    // leading dimension of R / Rs: a multiple of 32 (the chain copies 16-byte
+    // row pairs of the transposed Rs)
+    const size_t sbp = (size_t)(sbm + 31) / 32 * 32;
     need += 2 * align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
@@ -634,7 +691,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       if (fast_solve(b, sb)) {
         k_scale_split<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(
             R, (int)sbp, sb, b, 1.0 / ln, Rs);
-        ctx->prof.kernel_launches += 1;
+        launch_factor(ctx->stream, R, sa, Ginv, ctx->d_err);
+        ctx->prof.kernel_launches += 2;
       }
       launch_solve(ctx, R, Rs, pvec, Ginv, sa);
       prof_mark(ctx, PC_SOLVE);
@@ -651,20 +709,24 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     return finish(ctx);
   }
 
-  // dense dual: XT is n x d row-major (row i = sample i)
-  if (ld < d) return CA_ERR_ARG;
-  const bool tc = (xfmt == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
+  // dense dual: XT is n x d row-major (row i = sample i), or its panels
+  const bool pre = xfmt == CA_DENSE_F32_PANELS;
+  if (!pre && ld < d) return CA_ERR_ARG;
+  const int xf = pre ? (int)CA_DENSE_F32 : xfmt;
+  const bool tc = (xf == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
   if (o->prec == CA_GRAM_BF16X3 || o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
+  if (pre && !tc) return CA_ERR_ARG;
   if (tc) {
-    if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(XT) & 15) != 0) return CA_ERR_ARG;
+    if ((!pre && (ld & 3) != 0) || (reinterpret_cast<uintptr_t>(XT) & 15) != 0) return CA_ERR_ARG;
     if (std::min<long long>(o->s, o->H) * o->b > gram_tc_max_sb()) return CA_ERR_UNSUPPORTED;
   }
-  const size_t el = xfmt == CA_DENSE_F64 ? 8 : 4;
+  const size_t el = xf == CA_DENSE_F64 ? 8 : 4;
   const bool x_host = !is_device_ptr(XT);
-  const size_t xbytes = (size_t)(n - 1) * ld * el + (size_t)d * el;
-  need += dense_work_bytes(ctx, o, d, xfmt) + align256((size_t)(d + 31) / 32 * 32 * 8) +
+  const size_t xbytes = pre ? panel_bytes(n, d) : (size_t)(n - 1) * ld * el + (size_t)d * el;
+  need += dense_work_bytes(ctx, o, d, xf) + align256((size_t)(d + 31) / 32 * 32 * 8) +
           align256((size_t)n * 8);
   if (x_host) need += align256(xbytes) + 256;
+  if (tc && !pre) need += align256(panel_bytes(n, d)) + 256;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
   bool st;
@@ -673,6 +735,13 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     void* p = cv.take<char>(xbytes);
     CA_TRY_CUDA(cudaMemcpyAsync(p, XT, xbytes, cudaMemcpyHostToDevice, ctx->stream));
     Xd = p;
+  }
+  bool panel = pre;
+  if (tc && !pre) {  // the gather reads 32-column panels (ca_pack_panels layout)
+    float* pk = cv.take<float>(panel_bytes(n, d) / 4);
+    launch_pack(ctx, static_cast<const float*>(Xd), n, d, ld, pk);
+    Xd = pk;
+    panel = true;
   }
   const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
   double* ad = stage(ctx, cv, alpha, (size_t)n, true, &st);
@@ -683,8 +752,9 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
   DenseProblem pb;
-  pb.xfmt = xfmt;
+  pb.xfmt = xf;
   pb.A = Xd;
+  pb.panel = panel;
   pb.N = n;
   pb.K = d;
   pb.lda = ld;
@@ -713,11 +783,25 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
 
 // Profiling of the Gram launches (CUDA events on the context's stream around
 // every a2+a3 launch of the following solves).
+int ca_pack_panels(ca_ctx* ctx, const float* A, long long N, long long K, long long ld, float* out) {
+  t_cur_ctx = ctx;
+  if (!ctx || !A || !out || N < 1 || K < 1 || ld < K || (ld & 3) != 0 ||
+      (reinterpret_cast<uintptr_t>(A) & 15) != 0 || (reinterpret_cast<uintptr_t>(out) & 15) != 0)
+    return CA_ERR_ARG;
+  if (!is_device_ptr(A) || !is_device_ptr(out)) return CA_ERR_ARG;
+  CA_TRY_CUDA(cudaSetDevice(ctx->device));
+  launch_pack(ctx, A, N, K, ld, out);
+  return cuda_status(cudaGetLastError());
+}
+
 const char* ca_last_error(ca_ctx* ctx) { return ctx ? ctx->last_error : "no context"; }
 
 int ca_profile_enable(ca_ctx* ctx, int on) {
   if (!ctx) return CA_ERR_ARG;
+  std::vector<cudaEvent_t> pool;
+  pool.swap(ctx->prof.pool);  // keep the events across resets
   ctx->prof = Profile();
+  ctx->prof.pool.swap(pool);
   ctx->prof.on = on != 0;
   return CA_OK;
 }
@@ -766,7 +850,7 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, ctx->stream>>>(v, K, Kp, v2);
   CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, v2, part, ppart));
   SolveArgs sa{idx, N, 1, 0, sb, g.sbp, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
-  launch_reduce_solve(ctx, g, part, ppart, R, nullptr, p, nullptr, sa);
+  CA_TRY(launch_reduce_solve(ctx, g, part, ppart, R, nullptr, p, nullptr, sa));
   k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(R, g.sbp, sb, G);
   CA_TRY_CUDA(cudaGetLastError());
   return finish(ctx);

@@ -122,6 +122,15 @@ __device__ __forceinline__ double rcp_newton(double d) {
   return r;
 }
 
+// Programmatic dependent launch: wait until the preceding grid in the stream
+// has completed (its memory visible); no-op without a programmatic dependency.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Let the next grid in the stream (if launched as a programmatic dependent)
+// start scheduling its CTAs.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

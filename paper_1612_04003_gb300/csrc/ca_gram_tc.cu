@@ -9,17 +9,24 @@
 //  * grid = P CTAs, one per SM; CTA c owns a contiguous range of 32-column
 //    K-atoms and produces split-K partials (the single-GPU counterpart of the
 //    paper's all-reduce of the Gram matrix, Sec. 4);
-//  * warps 0-3 gather the sampled rows with 16-byte cp.async straight into
+//  * A is row-major, or (in the solves) stored as 32-column panels
+//    [K/32][N][32]: a stage's sampled rows then lie in one N x 128-byte block
+//    instead of N rows a full row length apart, which lets the gather run
+//    at a higher fraction of HBM bandwidth (fewer pages and DRAM rows per stage);
+//  * warps 0-7 gather the sampled rows with 16-byte cp.async straight into
 //    the 128-byte-swizzled K-major layout that tcgen05.mma reads (8-row atoms
 //    of 1024 bytes, 16-byte chunk c of row r stored at chunk c ^ (r % 8)),
 //    NS stages deep; the same warps form the projection from the staged tile
-//    on CUDA cores (v split into two FP32 halves, FP32 products, FP64 sums);
-//  * warp 4 allocates tensor memory and one thread issues the MMAs
+//    on CUDA cores (v split into two FP32 halves, FP32 products, compensated
+//    FP32 sums);
+//  * warp 8 allocates tensor memory and one thread issues the MMAs
 //    (M = 128; N = the padded s*b) accumulating Y Y^T in TMEM;
-//  * after the K loop warps 0-3 read TMEM (tcgen05.ld) and store the FP32
+//  * after the K loop warps 0-7 read TMEM (tcgen05.ld) and store the FP32
 //    partial tile(s) that cover the lower triangle.
 // With three_pass the FP32 inputs are split into a TF32 head and a TF32 tail
-// (x = hi + lo) and hi*hi + hi*lo + lo*hi are accumulated (3xTF32).
+// (x = hi + lo) and hi*hi + hi*lo + lo*hi are accumulated (3xTF32); the
+// loaders write hi and lo into a separate 2-slot operand ring, so the load
+// ring never waits on the tensor cores.
 // With a fused update (s*b <= 128) each stage also brings in the previous
 // outer step's rows: the loader warps apply that step's deferred update
 // (v -= cU Yprev^T Delta, in double-float on the FP32-pair copy of v) to the
@@ -38,32 +45,42 @@ constexpr int kThreads = kLoaderThreads + 32;
 
 template <int SBP, bool THREE, bool UPD = false>
 struct TcCfg {
-  static constexpr int kStageBytes = SBP * 128;                 // SBP rows x 32 fp32
-  // [head tile | tail tile (3xTF32) | previous step's rows (fused update)]
-  static constexpr int kStageTotal = kStageBytes * (1 + (THREE ? 1 : 0) + (UPD ? 1 : 0));
-  static constexpr int kPrevOff = kStageBytes * (THREE ? 2 : 1);
-  // ring depth: as many stages as fit (capped), so that short tiles (s*b <= 64)
-  // still keep enough bytes in flight
-  static constexpr int kNS = (176 * 1024) / kStageTotal < 32 ? (176 * 1024) / kStageTotal : 32;
+  static constexpr int kTileBytes = SBP * 128;                  // SBP rows x 32 fp32
+  // cp.async slot: [current rows | previous step's rows (fused update)]
+  static constexpr int kRawBytes = kTileBytes * (UPD ? 2 : 1);
+  static constexpr int kPrevOff = kTileBytes;
+  // 3xTF32: the loaders write the (head, tail) tiles into a separate ring of
+  // kMS slots that the MMA reads, so a load slot is free again as soon as its
+  // own thread has consumed it (no wait on the MMA before a refill).  Plain
+  // TF32: the MMA reads the load slot itself.
+  static constexpr int kMmaSlotBytes = THREE ? 2 * kTileBytes : 0;
+  static constexpr int kBudget = 200 * 1024;                    // both rings
+  static constexpr int kMS =
+      THREE ? ((kBudget - 2 * kMmaSlotBytes) / kRawBytes >= 4 ? 2 : 1) : 0;
+  static constexpr int kNSfit = (kBudget - kMS * kMmaSlotBytes) / kRawBytes;
+  static constexpr int kNS = kNSfit < 16 ? kNSfit : 16;         // load-ring depth
+  static constexpr int kMmaRing = kMS * kMmaSlotBytes;
   // SBP <= 128 with the 3-product split keeps two accumulators: D = hi hi^T
   // and T = hi lo^T (lo hi^T = T^T is added in the epilogue)
   static constexpr bool kSym = (SBP <= 128) && THREE;
   static constexpr int kTmemCols = (SBP == 256) ? 512 : (kSym ? 256 : 128);
-  // the M = 128 MMA reads 128 rows of the head tile; with SBP < 128 the rows
-  // past the tile are whatever follows in shared memory (their accumulator
-  // rows are never stored), so keep that much slack past the ring
-  static constexpr int kSlack = (SBP < 128 && kStageTotal < 16384) ? 16384 - kStageTotal : 0;
+  // the M = 128 MMA reads 128 rows of its A tile; with SBP < 128 the rows past
+  // the tile are whatever follows in shared memory (their accumulator rows
+  // are never stored).  The MMA ring is followed by the load ring; the last
+  // load slot (plain TF32) needs that much slack behind it.
+  static constexpr int kSlack = (!THREE && kRawBytes < 16384) ? 16384 - kRawBytes : 0;
   static constexpr int kRPT = SBP / 32;                         // rows per loader thread
   // projection-vector ring: 2*NS slots of 32 (hi, lo) pairs, so that a slot is
   // rewritten only after every loader passed the barrier of a later stage
   static constexpr int kVRing = 2 * kNS * 256;
-  // fused update: per-stage cross-group sums (16 x 32 FP32) and v_new split
-  // per-warp column sums and the stage's updated v (fused update)
-  static constexpr int kUpdBytes = UPD ? (kLoaderWarps * 32 * 4 + 32 * 8) : 0;
-  // refill a stage after processing the current one (the empty-slot wait then
-  // targets an MMA issued one iteration earlier); needs >= 4 stages
-  static constexpr bool kLateRefill = kNS >= 4;
-  static constexpr int kSmem = kNS * kStageTotal + kVRing + kUpdBytes + kSlack + 1024 + 512;
+  // fused update: per-warp column sums, double-buffered by stage parity
+  static constexpr int kUpdBytes = UPD ? 2 * kLoaderWarps * 32 * 4 : 0;
+  static constexpr int kZeroBytes = kMmaRing + kNS * kRawBytes + kVRing + kUpdBytes + kSlack;
+  static constexpr int kSmem = kZeroBytes + 1024 + 512;
+  static_assert(THREE || kNS >= 4, "plain TF32 refills one stage late: needs >= 4 slots");
+  static_assert(kNS >= 2, "load ring too shallow");
+  static_assert(!kSym || kMmaRing + kNS * kRawBytes >= 128 * 129 * 4, "no room for the T tile");
+  static_assert(kSmem <= 232448, "shared memory");
 };
 
 __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
@@ -125,22 +142,22 @@ __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-template <int SBP, bool THREE, bool UPD>
+template <int SBP, bool THREE, bool UPD, bool PANEL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
           const int* __restrict__ idx, int sb, const float2* __restrict__ v2, long long natoms,
           float* __restrict__ part, double* __restrict__ ppart, unsigned* __restrict__ err,
           GramUpdate u) {
   using C = TcCfg<SBP, THREE, UPD>;
-  constexpr int NS = C::kNS, RPT = C::kRPT;
+  constexpr int NS = C::kNS, MS = C::kMS, RPT = C::kRPT;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* stages = smem;  // NS x [big tile (| small tile)]
-  unsigned char* vring = smem + NS * C::kStageTotal;  // 2*NS x 256 B
-  float* ured = reinterpret_cast<float*>(vring + C::kVRing);  // [kLoaderWarps][32] (fused update)
-  float2* vn2s = reinterpret_cast<float2*>(ured + kLoaderWarps * 32);  // [32]
-  uint64_t* full = reinterpret_cast<uint64_t*>(vring + C::kVRing + C::kUpdBytes + C::kSlack);
+  unsigned char* mring = smem;                    // MS x [head tile | tail tile] (3xTF32)
+  unsigned char* raw = smem + C::kMmaRing;        // NS x [current rows | previous rows]
+  unsigned char* vring = raw + NS * C::kRawBytes;  // 2*NS x 256 B
+  float* ured = reinterpret_cast<float*>(vring + C::kVRing);  // [2][kLoaderWarps][32]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kZeroBytes);
   uint64_t* empty = full + NS;
   uint64_t* done = empty + NS;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
@@ -150,12 +167,12 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
   const long long a_begin = natoms * c / P, a_end = natoms * (c + 1) / P;
   const int T = (int)(a_end - a_begin);
 
-  // Rows >= sb and columns >= K stay zero for the whole kernel.
-  for (int e = tid; e < (NS * C::kStageTotal + C::kVRing + C::kUpdBytes + C::kSlack) / 16;
-       e += kThreads)
-    reinterpret_cast<uint4*>(stages)[e] = make_uint4(0u, 0u, 0u, 0u);
+  // Shared memory is not cleared: rows >= sb of a tile (never loaded) only
+  // reach accumulator rows / columns >= sb and projection entries >= sb,
+  // which are never stored or never read; the K tail past the last column is
+  // zero-filled by the copies (row-major) or zero in the panels.
   if (tid == 0) {
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < NS; ++s) {  // (3xTF32 uses the first MS pairs)
       mbar_init(&full[s], kLoaderThreads);
       mbar_init(&empty[s], 1);
     }
@@ -179,6 +196,9 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
 
   if (warp < kLoaderWarps) {
     // ---------------- loaders / projection / epilogue ----------------
+    // Thread (g, l) copies, reads and converts 16-byte chunk l of rows
+    // g + 32 i: a load slot holds only data its own thread consumes, so the
+    // thread may refill it right after use.
     const int g = tid >> 3, l = tid & 7;
     long long rowoff[RPT];
     uint32_t dsto[RPT];
@@ -188,11 +208,11 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       const long long gi = (r < sb) ? (long long)idx[r] : -1;
       const bool in_range = gi >= 0 && gi < N;
       if (r < sb && !in_range) ca_flag(err, CA_DEV_ERR_ARG);  // skipped, never read
-      rowoff[i] = in_range ? gi * lda : -1;
+      rowoff[i] = in_range ? gi * (PANEL ? 32 : lda) : -1;
       dsto[i] = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((l ^ (r & 7)) << 4));
     }
-    // fused update: this thread's rows of the previous outer step and their
-    // Delta as FP32 (hi, lo)
+    // fused update: this thread's rows of the previous outer step (their
+    // Delta is read once the preceding grid has finished, below)
     const float2 u_cU2 = split_f64(u.cU);
     long long prevoff[UPD ? RPT : 1];
     float dph[UPD ? RPT : 1], dpl[UPD ? RPT : 1];
@@ -203,27 +223,32 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         const long long gi = (r < u.sb) ? (long long)u.idx[r] : -1;
         const bool in_range = gi >= 0 && gi < N;
         if (r < u.sb && !in_range) ca_flag(err, CA_DEV_ERR_ARG);
-        prevoff[i] = in_range ? gi * lda : -1;
-        const float2 d2 = split_f64(in_range ? u.delta[r] : 0.0);
-        dph[i] = d2.x;
-        dpl[i] = d2.y;
+        prevoff[i] = in_range ? gi * (PANEL ? 32 : lda) : -1;
       }
     }
-    const uint32_t stage0 = smem_u32(stages);
+    const uint32_t raw0 = smem_u32(raw);
     const uint32_t vring0 = smem_u32(vring);
     auto issue = [&](int t, int slot) {
+      // row-major: row gi, columns k .. k+3 at A + gi lda + k (the K tail is
+      // zero-filled); panels: 32-column panel a of N rows x 128 B at
+      // A + a N 32, zero-padded past K
       const long long k = (a_begin + t) * 32 + 4 * l;
-      const long long rem = K - k;
-      const uint32_t bytes = rem >= 4 ? 16u : (rem > 0 ? (uint32_t)rem * 4u : 0u);
-      const uint32_t dst = stage0 + (uint32_t)(slot * C::kStageTotal);
+      uint32_t bytes = 16u;
+      long long col = PANEL ? (a_begin + t) * N * 32 + 4 * l : k;
+      if constexpr (!PANEL) {
+        const long long rem = K - k;
+        bytes = rem >= 4 ? 16u : (rem > 0 ? (uint32_t)rem * 4u : 0u);
+        if (!bytes) col = 0;
+      }
+      const uint32_t dst = raw0 + (uint32_t)(slot * C::kRawBytes);
 #pragma unroll
       for (int i = 0; i < RPT; ++i)
-        if (rowoff[i] >= 0) cp_async_16_zfill(dst + dsto[i], A + rowoff[i] + (bytes ? k : 0), bytes);
+        if (rowoff[i] >= 0) cp_async_16_zfill(dst + dsto[i], A + rowoff[i] + col, bytes);
       if constexpr (UPD) {
 #pragma unroll
         for (int i = 0; i < RPT; ++i)
           if (prevoff[i] >= 0)
-            cp_async_16_zfill(dst + C::kPrevOff + dsto[i], A + prevoff[i] + (bytes ? k : 0), bytes);
+            cp_async_16_zfill(dst + C::kPrevOff + dsto[i], A + prevoff[i] + col, bytes);
       }
       if (tid < 16)  // the stage's 32 (hi, lo) pairs of v (zero-padded to a multiple of 32)
         cp_async_16_zfill(vring0 + (uint32_t)((t % (2 * NS)) * 256 + tid * 16),
@@ -239,40 +264,43 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       plo[i] = 0.f;
     }
     bool ok = true;
-    for (int t = 0; t < NS - 1; ++t) {
+    // stages in flight ahead of the one being processed: 3xTF32 refills a
+    // slot right after consuming it; plain TF32 refills the slot of the
+    // previous stage once its MMA has completed
+    constexpr int PRE = THREE ? NS : NS - 1;
+    for (int t = 0; t < PRE; ++t) {
       if (t < T) issue(t, t);
       cp_async_commit();
     }
-    auto refill = [&](int t) {  // stage t + NS - 1 into the slot of stage t - 1
-      const int tn = t + NS - 1;
-      if (ok && tn < T) {
-        const int sn = tn % NS;
-        if (tn >= NS) ok = mbar_wait_bounded(&empty[sn], (uint32_t)((tn / NS - 1) & 1), err);
-        if (ok) issue(tn, sn);
+    // Everything above reads only X, the sampled indices and v2, which the
+    // preceding grid (the previous outer step's solve) does not write; Delta
+    // and the partial buffers wait for it.
+    pdl_wait();
+    pdl_trigger();
+    if constexpr (UPD) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = g + 32 * i;
+        const float2 d2 = split_f64(prevoff[i] >= 0 ? __ldcg(u.delta + r) : 0.0);
+        dph[i] = d2.x;
+        dpl[i] = d2.y;
       }
-      cp_async_commit();
-    };
+    }
     for (int t = 0; t < T; ++t) {
-      if constexpr (C::kLateRefill) {
-        cp_async_wait<NS - 2>();
-      } else {
-        refill(t);
-        cp_async_wait<NS - 1>();
-      }
+      cp_async_wait<PRE - 1>();  // this thread's copies of stage t have landed
       const int st = t % NS;
-      unsigned char* big = stages + st * C::kStageTotal;
+      unsigned char* big = raw + st * C::kRawBytes;
       if constexpr (!THREE) {  // the tile is ready for the MMA as loaded
         fence_proxy_async_smem();
         mbar_arrive(&full[st]);
       }
-      // every loader's copies of this stage (incl. the v slice) have landed
-      asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
       float vh[4], vl[4];
       if constexpr (UPD) {
         // deferred update of the previous outer step on this stage's 32
         // columns, v_new = v_old - cU * sum_r Yprev[r][k] Delta_r, in
         // double-float: per-thread sums over its rows, a shuffle over the 4
         // row groups of the warp, one shared-memory exchange between warps
+        // (every warp then forms v_new for all 32 columns itself)
         float up[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
@@ -289,28 +317,26 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
           up[e] += __shfl_xor_sync(0xffffffffu, up[e], 8);
           up[e] += __shfl_xor_sync(0xffffffffu, up[e], 16);
         }
+        float* ub = ured + (t & 1) * (kLoaderWarps * 32);
         if (lane < 8)
-          *reinterpret_cast<float4*>(ured + warp * 32 + 4 * l) =
-              make_float4(up[0], up[1], up[2], up[3]);
+          *reinterpret_cast<float4*>(ub + warp * 32 + 4 * l) = make_float4(up[0], up[1], up[2], up[3]);
+        // every loader's sums and copies (incl. the v slice) are in place
         asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
-        if (warp == 0) {  // lane = column: v_new once per column
-          float sum = 0.f;
+        float sum = 0.f;  // lane = column
 #pragma unroll
-          for (int w2 = 0; w2 < kLoaderWarps; ++w2) sum += ured[32 * w2 + lane];
-          const float2 vo = reinterpret_cast<const float2*>(vring + (t % (2 * NS)) * 256)[lane];
-          const float2 vn = df_add(vo, df_neg(df_mul(u_cU2, make_float2(sum, 0.f))));
-          vn2s[lane] = vn;
-          const long long kk = (a_begin + t) * 32 + lane;
-          if (kk < K) u.v2[kk] = vn;
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
+        for (int w2 = 0; w2 < kLoaderWarps; ++w2) sum += ub[32 * w2 + lane];
+        const float2 vo = reinterpret_cast<const float2*>(vring + (t % (2 * NS)) * 256)[lane];
+        const float2 vn = df_add(vo, df_neg(df_mul(u_cU2, make_float2(sum, 0.f))));
+        const long long kk = (a_begin + t) * 32 + lane;
+        if (warp == 0 && kk < K) u.v2[kk] = vn;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float2 q = vn2s[4 * l + e];
-          vh[e] = q.x;
-          vl[e] = q.y;
+          vh[e] = __shfl_sync(0xffffffffu, vn.x, 4 * l + e);
+          vl[e] = __shfl_sync(0xffffffffu, vn.y, 4 * l + e);
         }
       } else {
+        // every loader's copies of this stage (incl. the v slice) have landed
+        asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
         // projection vector slice as loaded (exact FP32 pairs)
         const float4* vs = reinterpret_cast<const float4*>(vring + (t % (2 * NS)) * 256 + l * 32);
         const float4 va = vs[0], vb = vs[1];
@@ -318,22 +344,17 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         vl[0] = va.y; vl[1] = va.w; vl[2] = vb.y; vl[3] = vb.w;
       }
       // projection on this thread's own chunks (exact FP32 inputs)
+      float4 xs[RPT];
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
-        float4* p4 = reinterpret_cast<float4*>(big + dsto[i]);
-        const float4 x = *p4;
+        const float4 x = *reinterpret_cast<const float4*>(big + dsto[i]);
+        xs[i] = x;
         float a = pacc[i];
         a = fmaf(x.x, vh[0], fmaf(x.x, vl[0], a));
         a = fmaf(x.y, vh[1], fmaf(x.y, vl[1], a));
         a = fmaf(x.z, vh[2], fmaf(x.z, vl[2], a));
         a = fmaf(x.w, vh[3], fmaf(x.w, vl[3], a));
         pacc[i] = a;
-        if constexpr (THREE) {
-          const float4 h = make_float4(tf32_head(x.x), tf32_head(x.y), tf32_head(x.z), tf32_head(x.w));
-          *p4 = h;
-          *reinterpret_cast<float4*>(big + C::kStageBytes + dsto[i]) =
-              make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-        }
       }
       if ((t & 7) == 7) {
 #pragma unroll
@@ -342,11 +363,35 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
           pacc[i] = 0.f;
         }
       }
-      if constexpr (THREE) {  // head / tail tiles written: hand the stage to the MMA
+      if constexpr (THREE) {
+        // head / tail tiles into MMA slot t % MS once the MMA of stage t - MS
+        // has read it; then hand the slot to the MMA
+        const int ms = t % MS;
+        if (ok && t >= MS) ok = mbar_wait_bounded(&empty[ms], (uint32_t)((t / MS - 1) & 1), err);
+        unsigned char* hi = mring + ms * C::kMmaSlotBytes;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const float4 x = xs[i];
+          const float4 h = make_float4(tf32_head(x.x), tf32_head(x.y), tf32_head(x.z), tf32_head(x.w));
+          *reinterpret_cast<float4*>(hi + dsto[i]) = h;
+          *reinterpret_cast<float4*>(hi + C::kTileBytes + dsto[i]) =
+              make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
         fence_proxy_async_smem();
-        mbar_arrive(&full[st]);
+        mbar_arrive(&full[ms]);
+        // this thread's part of load slot st is consumed: refill it
+        if (t + NS < T) issue(t + NS, st);
+        cp_async_commit();
+      } else {
+        // stage t + NS - 1 into the slot of stage t - 1 once its MMA completed
+        const int tn = t + NS - 1;
+        if (ok && tn < T) {
+          const int sn = tn % NS;
+          if (tn >= NS) ok = mbar_wait_bounded(&empty[sn], (uint32_t)((tn / NS - 1) & 1), err);
+          if (ok) issue(tn, sn);
+        }
+        cp_async_commit();
       }
-      if constexpr (C::kLateRefill) refill(t);  // stage t + NS - 1 into the slot of stage t - 1
     }
     cp_async_wait<0>();
     // projection partials: reduce over the 8 lanes sharing a row group
@@ -370,7 +415,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
     if constexpr (C::kSym) {
       // G = D + T + T^T: T goes through the (now idle) stage buffers as a
       // 128 x 129 FP32 array, read back transposed without bank conflicts
-      float* Ts = reinterpret_cast<float*>(stages);
+      float* Ts = reinterpret_cast<float*>(smem);
       for (int cc = 32 * cpar; cc < n1; cc += 64) {
         uint32_t r[32];
         tmem_ld32(tbase + 128u + (uint32_t)cc, r);
@@ -425,13 +470,20 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
     // ---------------- MMA issue (one thread) ----------------
     const uint32_t id1 = idesc_tf32(128, n1);
     const uint32_t id2 = idesc_tf32(128, n2);
-    const uint32_t stage0 = smem_u32(stages);
     for (int t = 0; t < T; ++t) {
-      const int st = t % NS;
-      if (!mbar_wait_bounded(&full[st], (uint32_t)((t / NS) & 1), err)) break;
+      int st, lap;
+      if constexpr (THREE) {
+        st = t % MS;
+        lap = t / MS;
+      } else {
+        st = t % NS;
+        lap = t / NS;
+      }
+      if (!mbar_wait_bounded(&full[st], (uint32_t)(lap & 1), err)) break;
       tc_fence_after();
-      const uint32_t hb = stage0 + (uint32_t)(st * C::kStageTotal);
-      const uint32_t lb = hb + (uint32_t)C::kStageBytes;
+      const uint32_t hb = THREE ? smem_u32(mring) + (uint32_t)(st * C::kMmaSlotBytes)
+                                : smem_u32(raw) + (uint32_t)(st * C::kRawBytes);
+      const uint32_t lb = hb + (uint32_t)C::kTileBytes;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint32_t acc = (t > 0 || kk > 0) ? 1u : 0u;
@@ -472,21 +524,34 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
   }
 }
 
-template <int SBP, bool THREE, bool UPD>
+template <int SBP, bool THREE, bool UPD, bool PANEL>
 int launch_one(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
                const float2* v2, int P, float* part, double* ppart, unsigned* err,
                const GramUpdate& u, cudaStream_t stream) {
   using C = TcCfg<SBP, THREE, UPD>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD>,
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD, PANEL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return (int)e;
     configured = true;
   }
   const long long natoms = (K + 31) / 32;
-  k_gram_tc<SBP, THREE, UPD><<<P, kThreads, C::kSmem, stream>>>(A, lda, N, K, idx, sb, v2, natoms,
-                                                                 part, ppart, err, u);
+  // launched as a programmatic dependent: its CTAs may start (and prefetch)
+  // while the preceding grid in the stream finishes
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = C::kSmem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gram_tc<SBP, THREE, UPD, PANEL>, A, lda, N, K, idx,
+                                           sb, v2, natoms, part, ppart, err, u);
+  if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
 }
 
@@ -496,33 +561,32 @@ int gram_tc_max_sb() { return 256; }
 
 int launch_gram_tc(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
                    const float2* v2, int P, int sbp, float* part, double* ppart, unsigned* err,
-                   int three_pass, cudaStream_t stream, const GramUpdate* upd) {
+                   int three_pass, cudaStream_t stream, const GramUpdate* upd, bool panel) {
   const GramUpdate none{};
-#define CA_TC_CASE(S, T, U, UU)                                                              \
-  if (sbp == S && (three_pass != 0) == T)                                                  \
-    return launch_one<S, T, U>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, UU, stream);
-  if (upd && upd->sb > 0) {  // fused deferred update: s*b <= 128 only
-    if (sbp > 128 || upd->sb > sbp) return (int)cudaErrorInvalidValue;
+  const bool T3 = three_pass != 0;
+#define CA_TC_CASE(S, U, PN, UU)                                                             \
+  if (sbp == S) return T3 ? launch_one<S, true, U, PN>(A, lda, N, K, idx, sb, v2, P, part, ppart, \
+                                                       err, UU, stream)                         \
+                          : launch_one<S, false, U, PN>(A, lda, N, K, idx, sb, v2, P, part,     \
+                                                        ppart, err, UU, stream);
+  if (upd && upd->sb > 0) {  // fused deferred update: panels, s*b <= 128 only
+    if (!panel || sbp > 128 || upd->sb > sbp) return (int)cudaErrorInvalidValue;
     CA_TC_CASE(32, true, true, *upd)
-    CA_TC_CASE(32, false, true, *upd)
     CA_TC_CASE(64, true, true, *upd)
-    CA_TC_CASE(64, false, true, *upd)
     CA_TC_CASE(128, true, true, *upd)
-    CA_TC_CASE(128, false, true, *upd)
     return (int)cudaErrorInvalidValue;
   }
-  CA_TC_CASE(32, true, false, none)
-  CA_TC_CASE(32, false, false, none)
-  CA_TC_CASE(64, true, false, none)
-  CA_TC_CASE(64, false, false, none)
+  if (panel) {
+    CA_TC_CASE(32, false, true, none)
+    CA_TC_CASE(64, false, true, none)
+    CA_TC_CASE(128, false, true, none)
+    CA_TC_CASE(256, false, true, none)
+  } else {
+    CA_TC_CASE(32, false, false, none)
+    CA_TC_CASE(64, false, false, none)
+    CA_TC_CASE(128, false, false, none)
+    CA_TC_CASE(256, false, false, none)
+  }
 #undef CA_TC_CASE
-  if (sbp == 128)
-    return three_pass
-               ? launch_one<128, true, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, none, stream)
-               : launch_one<128, false, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, none, stream);
-  if (sbp == 256)
-    return three_pass
-               ? launch_one<256, true, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, none, stream)
-               : launch_one<256, false, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, none, stream);
   return (int)cudaErrorInvalidValue;
 }

@@ -231,97 +231,130 @@ __device__ void block_solve(const double* __restrict__ R, const double* __restri
 // the end (atomic adds: an index may recur across blocks).
 // ---------------------------------------------------------------------------
 
-// One warp: Cholesky of the SPD b x b block A (shared, row-major; destroyed),
-// then Gamma^{-1} = L^{-T} L^{-1} written to out (row-major b x b).  W is a
-// b x b shared scratch.  Lane p owns row / column p (b <= 32).
 // Gamma_j^{-1} for one b x b block by the Gauss-Jordan sweep operator on a
 // symmetric positive definite matrix (Goodnight, 1979): sweeping pivot k maps
 // a_kk -> -1/a_kk, a_ik -> a_ik/a_kk, a_kj -> a_kj/a_kk and
 // a_ij -> a_ij - a_ik a_kj / a_kk; after all b pivots the matrix is -Gamma^{-1}.
-// A group of GW lanes (GW >= b, a power of two dividing 32) holds one row per
-// lane in registers; pivot rows are broadcast with shuffles; pivots are
-// inverted by Newton-Raphson.  Gamma = cG R_jj + cI I is read from R (FP64,
-// lower triangle, leading dimension ldr); the result goes to out (row-major
-// b x b FP32 pairs).  Returns false on a non-positive pivot.
-template <int BMAX, int GW>
-__device__ bool group_sweep_inverse(const double* __restrict__ R, int ldr, int base, int b, double cG,
-                                    double cI, float2* __restrict__ out) {
-  const int p = threadIdx.x & (GW - 1);
-  const unsigned mask = (GW == 32) ? 0xffffffffu : (((1u << GW) - 1u) << ((threadIdx.x & 31) & ~(GW - 1)));
-  double a[BMAX];
+// The sweep keeps the matrix symmetric, so pivot k needs only column k.  The
+// CTA's 256 threads own one entry each (thread t: entries t + 256 q of the
+// row-major b x b matrix, values in a[q]); before pivot k the owners of column
+// k publish it to shared memory and the owner of a_kk its reciprocal (Newton-
+// Raphson), once (two buffers alternate: one barrier per pivot).  FP64 is
+// scarce on this part, so threads without entries do no FP64 work.  Every
+// thread of the CTA calls this.  Writes Gamma^{-1} (FP32 pairs, row-major) to
+// out; a non-positive pivot raises CA_DEV_ERR_NOT_SPD.
+template <int EPT>
+__device__ void cta_sweep_inverse(double (&a)[EPT], int b, double* __restrict__ colbuf,
+                                  float2* __restrict__ out, unsigned* __restrict__ err) {
+  const int t = threadIdx.x;
+  int ri[EPT], ci[EPT];
 #pragma unroll
-  for (int c = 0; c < BMAX; ++c) {
-    double v = 0.0;
-    if (p < b && c < b) {
-      const int i = p > c ? p : c, jj = p > c ? c : p;  // lower triangle of R
-      v = cG * R[(long long)(base + i) * ldr + (base + jj)] + (p == c ? cI : 0.0);
-    }
-    a[c] = v;
+  for (int q = 0; q < EPT; ++q) {
+    const int e = t + 256 * q;
+    ri[q] = e < b * b ? e / b : -1;
+    ci[q] = e < b * b ? e - ri[q] * b : -1;
   }
-  bool ok = true;
+  const bool active = t < b * b;
+  for (int k = 0; k < b; ++k) {
+    double* ck = colbuf + (k & 1) * 33;  // [0, b): column k; [32]: 1 / a_kk
 #pragma unroll
-  for (int k = 0; k < BMAX; ++k) {
-    if (k < b) {
-      double ak[BMAX];
-#pragma unroll
-      for (int c = 0; c < BMAX; ++c) ak[c] = __shfl_sync(mask, a[c], k, GW);
-      double d = ak[k];
-      if (!(d > 0.0)) {
-        ok = false;
-        d = 1.0;
-      }
-      const double rd = rcp_newton(d);
-      if (p == k) {
-#pragma unroll
-        for (int c = 0; c < BMAX; ++c) a[c] = (c == k) ? -rd : ak[c] * rd;
-      } else {
-        const double f = a[k] * rd;
-#pragma unroll
-        for (int c = 0; c < BMAX; ++c) a[c] = (c == k) ? f : fma(-f, ak[c], a[c]);
+    for (int q = 0; q < EPT; ++q) {
+      if (ci[q] == k) {
+        ck[ri[q]] = a[q];
+        if (ri[q] == k) {
+          double d = a[q];
+          if (!(d > 0.0)) {
+            ca_flag(err, CA_DEV_ERR_NOT_SPD);
+            d = 1.0;
+          }
+          ck[32] = rcp_newton(d);
+        }
       }
     }
-  }
-  if (p < b) {
+    __syncthreads();
+    if (active) {
+      const double rd = ck[32];
 #pragma unroll
-    for (int c = 0; c < BMAX; ++c)
-      if (c < b) out[p * b + c] = split_f64(-a[c]);
+      for (int q = 0; q < EPT; ++q) {
+        const int i = ri[q], j = ci[q];
+        if (i < 0) continue;
+        if (i == k && j == k) a[q] = -rd;
+        else if (i == k) a[q] = ck[j] * rd;
+        else if (j == k) a[q] = ck[i] * rd;
+        else a[q] = fma(-ck[i] * rd, ck[j], a[q]);
+      }
+    }
   }
-  return ok;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q)
+    if (ri[q] >= 0) out[t + 256 * q] = split_f64(-a[q]);
 }
 
+// Sum of the partials c = c0, c0 + step, ... < P of one entry (stride sq
+// between partials); FP32 partials are summed with compensation.
 template <typename PT>
-__device__ __forceinline__ double sum_partials(const PT* __restrict__ src, int P, long long sq,
-                                               int warp) {
+__device__ __forceinline__ double sum_partials(const PT* __restrict__ src, int c0, int P, int step,
+                                               long long sq) {
   if constexpr (sizeof(PT) == 4) {
     float hi = 0.f, lo = 0.f;
 #pragma unroll 8
-    for (int c = warp; c < P; c += 8) comp_add(hi, lo, __ldg(src + c * sq));
+    for (int c = c0; c < P; c += step) comp_add(hi, lo, __ldcg(src + c * sq));
     return (double)hi + (double)lo;
   } else {
     double s = 0.0;
 #pragma unroll 8
-    for (int c = warp; c < P; c += 8) s += __ldg(src + c * sq);
+    for (int c = c0; c < P; c += step) s += __ldcg(src + c * sq);
     return s;
   }
 }
 
-// Reduce the split-K partials into R (lower triangle) and p; Rs receives the
-// cG-scaled FP32 pairs of the entries the chain reads.  32 entries per pass
-// (one per lane); the 8 warps split the P partials.  (Ginv, ndiag: unused,
-// must be nullptr / 0.)
+// Reduce the split-K partials into R (lower triangle) and p.  Rs (when not
+// null) receives the cG-scaled FP32 pairs of the lower-triangle entries,
+// stored transposed (entry (i, j), i >= j, at Rs[j * ldr + i]) so that the
+// chain reads a column block with coalesced loads.  CTAs 0 .. ndiag-1 each
+// reduce one diagonal block Gamma_j = cG R_jj + cI I (b <= 16) and invert it
+// into Ginv[j] (cta_sweep_inverse); the other CTAs take 32 entries per pass
+// (one per lane), the 8 warps splitting the P partials.
 template <typename PT>
-__global__ void __launch_bounds__(256)
-k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, int sbp,
-         double* __restrict__ R, float2* __restrict__ Rs, double* __restrict__ pvec,
-         float2* __restrict__ Ginv, int ndiag, SolveArgs sa, unsigned* __restrict__ err) {
+__device__ void reduce_body(const PT* __restrict__ part, const double* __restrict__ ppart, int P,
+                            int sbp, double* __restrict__ R, float2* __restrict__ Rs,
+                            double* __restrict__ pvec, float2* __restrict__ Ginv, int ndiag,
+                            const SolveArgs& sa, unsigned* __restrict__ err, int cta, int ncta) {
   __shared__ double red[8][32];
+  __shared__ double Mb[256];
+  __shared__ double colbuf[66];
   const int sb = sa.sb, ldr = sa.ldr;
   const long long sq = (long long)sbp * sbp;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  (void)Ginv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (cta < ndiag) {
+    const int b = sa.b, base = cta * b;
+    const int E = b * (b + 1) / 2;
+    const int nsl = 256 / E;  // >= 1 for b <= 16
+    const int sl = tid / E, e = tid - sl * E;
+    double* flat = &red[0][0];
+    if (sl < nsl) {
+      int i, j;
+      tri_decode(e, i, j);
+      flat[tid] = sum_partials(part + (long long)(base + i) * sbp + (base + j), sl, P, nsl, sq);
+    }
+    __syncthreads();
+    if (tid < E) {
+      double t = 0.0;
+      for (int q = 0; q < nsl; ++q) t += flat[q * E + tid];
+      int i, j;
+      tri_decode(tid, i, j);
+      const double v = sa.cG * t + (i == j ? sa.cI : 0.0);
+      Mb[i * b + j] = v;
+      Mb[j * b + i] = v;
+    }
+    __syncthreads();
+    double a[1] = {tid < b * b ? Mb[tid] : 0.0};
+    cta_sweep_inverse<1>(a, b, colbuf, Ginv + (long long)cta * b * b, err);
+    return;
+  }
   const long long nlow = (long long)sb * (sb + 1) / 2;
-  const long long stride = (long long)(gridDim.x - ndiag) * 32;
-  for (long long e0 = (long long)(blockIdx.x - ndiag) * 32; e0 < nlow + sb; e0 += stride) {
+  const long long stride = (long long)(ncta - ndiag) * 32;
+  for (long long e0 = (long long)(cta - ndiag) * 32; e0 < nlow + sb; e0 += stride) {
     const long long e = e0 + lane;
     int i = 0, j = 0;
     int kind = 0;  // 0 none, 1 Gram entry, 2 projection entry
@@ -334,7 +367,7 @@ k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, i
       i = (int)(e - nlow);
     }
     if (kind == 1) {
-      s = sum_partials(part + (long long)i * sbp + j, P, sq, warp);
+      s = sum_partials(part + (long long)i * sbp + j, warp, P, 8, sq);
     } else if (kind == 2) {
 #pragma unroll 4
       for (int c = warp; c < P; c += 8) s += ppart[(long long)c * sbp + i];
@@ -347,7 +380,7 @@ k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, i
       for (int w = 0; w < 8; ++w) t += red[w][lane];
       if (kind == 1) {
         R[(long long)i * ldr + j] = t;
-        if (Rs) Rs[(long long)i * ldr + j] = split_f64(sa.cG * t);
+        if (Rs) Rs[(long long)j * ldr + i] = split_f64(sa.cG * t);
       } else {
         pvec[i] = t;
       }
@@ -356,20 +389,39 @@ k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, i
   }
 }
 
+template <typename PT>
+__global__ void __launch_bounds__(256)
+k_reduce(const PT* __restrict__ part, const double* __restrict__ ppart, int P, int sbp,
+         double* __restrict__ R, float2* __restrict__ Rs, double* __restrict__ pvec,
+         float2* __restrict__ Ginv, int ndiag, SolveArgs sa, unsigned* __restrict__ err) {
+  reduce_body<PT>(part, ppart, P, sbp, R, Rs, pvec, Ginv, ndiag, sa, err, (int)blockIdx.x,
+                  (int)gridDim.x);
+}
+
 template __global__ void k_reduce<double>(const double*, const double*, int, int, double*, float2*,
                                           double*, float2*, int, SolveArgs, unsigned*);
 template __global__ void k_reduce<float>(const float*, const double*, int, int, double*, float2*,
                                          double*, float2*, int, SolveArgs, unsigned*);
 
-// Gamma_j^{-1} for every diagonal block j = blockIdx.x (one warp each; used
-// when b > 16, where the FP64 work of all s blocks would swamp one SM).
-__global__ void __launch_bounds__(32)
+// Gamma_j^{-1} for every diagonal block j = blockIdx.x from R (FP64 lower
+// triangle), one CTA each (b <= 32).
+__global__ void __launch_bounds__(256)
 k_factor(const double* __restrict__ R, SolveArgs sa, float2* __restrict__ Ginv,
          unsigned* __restrict__ err) {
-  const int j = blockIdx.x;
-  if (!group_sweep_inverse<32, 32>(R, sa.ldr, j * sa.b, sa.b, sa.cG, sa.cI,
-                                   Ginv + (long long)j * sa.b * sa.b))
-    if ((threadIdx.x & 31) == 0) ca_flag(err, CA_DEV_ERR_NOT_SPD);
+  __shared__ double colbuf[66];
+  const int b = sa.b, base = (int)blockIdx.x * b;
+  double a[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = (int)threadIdx.x + 256 * q;
+    a[q] = 0.0;
+    if (e < b * b) {
+      const int i = e / b, c = e - (e / b) * b;
+      const int hi = i > c ? i : c, lo = i > c ? c : i;
+      a[q] = sa.cG * R[(long long)(base + hi) * sa.ldr + (base + lo)] + (i == c ? sa.cI : 0.0);
+    }
+  }
+  cta_sweep_inverse<4>(a, b, colbuf, Ginv + (long long)blockIdx.x * b * b, err);
 }
 
 // Sum of n double-float values by a balanced tree (n a power of two).
@@ -382,59 +434,60 @@ __device__ __forceinline__ float2 df_tree_sum(float2 (&v)[N]) {
   return v[0];
 }
 
-// The dependent chain (one CTA of 256 threads), for sb <= 256, b <= BMAX <= 32.
-// Prologue (FACTOR): the s diagonal blocks are inverted by lane groups of
-// BMAX lanes in parallel (group_sweep_inverse); otherwise Ginv is read.
-// Chain, right-looking: thread r owns row r and keeps the sum
+// The dependent chain (one CTA of 256 threads), for sb <= 256, b <= BMAX <= 32,
+// with the diagonal-block inverses Ginv already formed.  Right-looking:
+// thread r owns row r and keeps the sum
 // acc_r = sum_{t solved} (cG R_rt + cI [I_r = I_t]) Delta_t; after block j is
 // solved every later row folds in its b new terms, and the rows of block j+1
-// then hold their complete right-hand sides.  The row slices
-// R[r][jb .. jb+b) arrive pre-scaled by cG as FP32 pairs (Rs); each thread
-// streams its own slices DEPTH steps ahead through a shared-memory ring with
-// cp.async (it reads only what it copied).  Products are summed as trees
-// (short dependency chains); everything on the dependent path is
-// double-float; FP64 converts in at the start and out at the end.
-template <int BMAX, int DEPTH, bool FACTOR>
-__global__ void __launch_bounds__(256)
-k_chain(const double* __restrict__ R, const float2* __restrict__ Rs,
-        const double* __restrict__ pvec, const float2* __restrict__ Ginv, SolveArgs a,
-        unsigned* __restrict__ err) {
-  extern __shared__ double smem_d[];
+// then hold their complete right-hand sides.  The entries cG R[r][jb + q]
+// arrive as FP32 pairs from the transposed Rs (column jb + q contiguous over
+// r): the CTA streams the b columns of step j, DEPTH steps ahead, through a
+// shared-memory ring with 16-byte cp.async.cg copies of row pairs (slot
+// layout [q][row]: coalesced copies, conflict-free reads).  Everything the
+// chain reads that an earlier kernel, or other CTAs of the same kernel, wrote
+// is read through L2 (.cg / __ldcg), never from a possibly stale L1 line.
+// Products are summed as trees (short dependency chains); everything on the
+// dependent path is double-float; FP64 converts in at the start and out at
+// the end.  256 threads; smem_d: the chain's dynamic shared memory.
+template <int BMAX, int DEPTH>
+__device__ void chain_body(const float2* __restrict__ Rs, const double* __restrict__ pvec,
+                           const float2* __restrict__ Ginv, const SolveArgs& a,
+                           unsigned* __restrict__ err, double* smem_d) {
   const int r = threadIdx.x;
   const int b = a.b, sb = a.sb, ldr = a.ldr, s = a.s_cur;
-  float2* ring = reinterpret_cast<float2*>(smem_d);        // DEPTH x 256 x BMAX
+  float2* ring = reinterpret_cast<float2*>(smem_d);        // DEPTH x BMAX x 256
   float2* Gs = ring + (size_t)DEPTH * 256 * BMAX;          // sb*b: Gamma_j^{-1}
   float2* rb = Gs + (size_t)sb * b;                         // 32: rhs of the current block
   float2* dl = rb + 32;                                     // 32: Delta of the current block
   float2* dall = dl + 32;                                   // sb: all Delta
   int* sidx = reinterpret_cast<int*>(dall + sb);            // sb
-  float2* myring = ring + (size_t)r * BMAX;                 // slot d at + d * 256 * BMAX
-  auto fetch = [&](int j) {  // row r's slice for step j into slot j % DEPTH
+  const uint32_t ring0 = smem_u32(ring);
+  // 16-byte copies of row pairs need an even leading dimension (callers use
+  // multiples of 32); otherwise nothing is copied and the call is flagged
+  const bool ld_ok = (ldr & 1) == 0;
+  if (!ld_ok && r == 0) ca_flag(err, CA_DEV_ERR_ARG);
+  auto fetch = [&](int j) {  // columns jb .. jb+b of rows >= jb + b into slot j % DEPTH
     const int jb = j * b;
-    if (j < s && r >= jb + b && r < sb) {
-      const uint32_t dst = smem_u32(myring + (size_t)(j % DEPTH) * 256 * BMAX);
-      const float2* src = Rs + (long long)r * ldr + jb;
-      for (int q = 0; q < b; ++q) cp_async_8(dst + 8u * q, src + q);
+    if (j < s && ld_ok) {
+      const int p0 = (jb + b) >> 1, np = ((sb + 1) >> 1) - p0;  // row pairs 2p, 2p+1
+      for (int u = r; u < b * np; u += 256) {
+        const int q = u / np, pr = 2 * (p0 + u - q * np);
+        cp_async_16_zfill(ring0 + 8u * (uint32_t)(((j % DEPTH) * BMAX + q) * 256 + pr),
+                          Rs + (long long)(jb + q) * ldr + pr, 16u);
+      }
     }
     cp_async_commit();
   };
 #pragma unroll
   for (int d = 0; d < DEPTH; ++d) fetch(d);
-  if constexpr (FACTOR) {
-    constexpr int NG = 256 / BMAX;  // lane groups
-    for (int j = r / BMAX; j < s; j += NG)
-      if (!group_sweep_inverse<BMAX, BMAX>(R, ldr, j * b, b, a.cG, a.cI, Gs + (size_t)j * b * b))
-        if ((r & (BMAX - 1)) == 0) ca_flag(err, CA_DEV_ERR_NOT_SPD);
-  } else {
-    for (int e = r; e < sb * b; e += 256) Gs[e] = Ginv[e];
-  }
+  for (int e = r; e < sb * b; e += 256) Gs[e] = __ldcg(Ginv + e);
   float2 rhs0 = make_float2(0.f, 0.f);
   int gi = -1;
   if (r < sb) {
     gi = a.idx[r];
-    double v = a.cP * pvec[r];
+    double v = a.cP * __ldcg(pvec + r);
     if (gi >= 0 && gi < a.N) {
-      v -= a.cI * a.x[gi];
+      v -= a.cI * __ldcg(a.x + gi);
       if (a.yv) v -= a.cY * a.yv[gi];
     } else {
       ca_flag(err, CA_DEV_ERR_ARG);
@@ -469,25 +522,25 @@ k_chain(const double* __restrict__ R, const float2* __restrict__ Rs,
         dall[jb + grow] = t;
       }
     }
-    cp_async_wait<DEPTH - 1>();  // this thread's slice for step j has landed
-    __syncthreads();
+    cp_async_wait<DEPTH - 1>();  // this thread's copies for step j have landed
+    __syncthreads();             // ... and everyone else's
     if (r >= jb + b && r < sb) {  // fold block j into the later rows
-      const float2* sl = myring + (size_t)(j % DEPTH) * 256 * BMAX;
+      const float2* sl = ring + (size_t)(j % DEPTH) * BMAX * 256 + r;
       float2 pr[BMAX];
 #pragma unroll
       for (int q = 0; q < BMAX; ++q) {
         pr[q] = make_float2(0.f, 0.f);
         if (q < b) {
           const float2 dq = dl[q];
-          pr[q] = df_mul(sl[q], dq);
+          pr[q] = df_mul(sl[q * 256], dq);
           if (sidx[jb + q] == gi) ovl = df_add(ovl, dq);
         }
       }
       acc = df_add(acc, df_tree_sum(pr));
       if (r < jb + 2 * b) rb[r - jb - b] = df_add(rhs0, df_neg(df_add(acc, df_mul(cI2, ovl))));
     }
+    __syncthreads();  // slot j % DEPTH is free only once every thread has folded
     fetch(j + DEPTH);
-    __syncthreads();
   }
   cp_async_wait<0>();
   if (r < sb) {  // Delta out, x += Delta (atomic: an index may recur across blocks)
@@ -499,12 +552,59 @@ k_chain(const double* __restrict__ R, const float2* __restrict__ Rs,
   }
 }
 
-template __global__ void k_chain<8, 4, true>(const double*, const float2*, const double*,
-                                             const float2*, SolveArgs, unsigned*);
-template __global__ void k_chain<16, 3, true>(const double*, const float2*, const double*,
-                                              const float2*, SolveArgs, unsigned*);
-template __global__ void k_chain<32, 2, false>(const double*, const float2*, const double*,
-                                               const float2*, SolveArgs, unsigned*);
+template <int BMAX, int DEPTH>
+__global__ void __launch_bounds__(256)
+k_chain(const float2* __restrict__ Rs, const double* __restrict__ pvec,
+        const float2* __restrict__ Ginv, SolveArgs a, unsigned* __restrict__ err) {
+  extern __shared__ double smem_d[];
+  chain_body<BMAX, DEPTH>(Rs, pvec, Ginv, a, err, smem_d);
+}
+
+// a4 in one launch (b <= 16): the reduction with the diagonal-block
+// inverses (reduce_body), then the CTA that finishes last (ticket counter;
+// no CTA waits for another) runs the chain.  Launched as a programmatic
+// dependent of the Gram pass: it waits for that grid, then lets the next
+// Gram pass launch its CTAs, which prepare and start their loads on the SMs
+// this grid frees while the chain runs.  *ticket is zero on entry and left
+// zero.
+template <typename PT, int BMAX, int DEPTH>
+__global__ void __launch_bounds__(256)
+k_reduce_chain(const PT* __restrict__ part, const double* __restrict__ ppart, int P, int sbp,
+               double* __restrict__ R, float2* __restrict__ Rs, double* __restrict__ pvec,
+               float2* __restrict__ Ginv, int ndiag, SolveArgs sa, unsigned* __restrict__ err,
+               unsigned* __restrict__ ticket) {
+  extern __shared__ double smem_d[];
+  __shared__ int s_last;
+  pdl_wait();
+  pdl_trigger();
+  reduce_body<PT>(part, ppart, P, sbp, R, Rs, pvec, Ginv, ndiag, sa, err, (int)blockIdx.x,
+                  (int)gridDim.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's R, Rs, p, Ginv before its ticket
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+    if (s_last) atomicExch(ticket, 0u);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  chain_body<BMAX, DEPTH>(Rs, pvec, Ginv, sa, err, smem_d);
+}
+
+template __global__ void k_reduce_chain<float, 8, 6>(const float*, const double*, int, int, double*,
+                                                     float2*, double*, float2*, int, SolveArgs,
+                                                     unsigned*, unsigned*);
+template __global__ void k_reduce_chain<float, 16, 3>(const float*, const double*, int, int,
+                                                      double*, float2*, double*, float2*, int,
+                                                      SolveArgs, unsigned*, unsigned*);
+
+template __global__ void k_chain<8, 6>(const float2*, const double*, const float2*, SolveArgs,
+                                       unsigned*);
+template __global__ void k_chain<16, 3>(const float2*, const double*, const float2*, SolveArgs,
+                                        unsigned*);
+template __global__ void k_chain<32, 2>(const float2*, const double*, const float2*, SolveArgs,
+                                        unsigned*);
 
 // The solves alone (sparse path: R and p are formed directly).
 __global__ void __launch_bounds__(256)
@@ -523,7 +623,8 @@ k_solve(const double* __restrict__ R, const double* __restrict__ pvec, SolveArgs
 // CTA = 4 row groups x 64 threads; thread t of group g handles the 4
 // consecutive k at (64 blockIdx + t) * 4 and the rows r = g (mod 4); group 0
 // adds the groups' partial sums and writes v (and its FP32 split v2).
-template <typename T>
+// PANEL (FP32 only): A stored as 32-column panels [K/32][N][32] (zero-padded).
+template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 k_update_dense(const T* __restrict__ A, long long lda, long long N, long long K,
                const int* __restrict__ idx, int sb, const double* __restrict__ delta, double cU,
@@ -561,10 +662,13 @@ k_update_dense(const T* __restrict__ A, long long lda, long long N, long long K,
           if (e < nk) acc[e] = fma((double)row[e], dl, acc[e]);
       }
     } else {
-      const bool vec = (nk == 4) && ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+      const bool vec = PANEL || ((nk == 4) && ((lda & 3) == 0) &&
+                                 ((reinterpret_cast<uintptr_t>(A) & 15) == 0));
+      const long long pbase = (k >> 5) * N * 32 + (k & 31);
 #pragma unroll 8
       for (int r = grp; r < sb; r += 4) {
-        const float* row = reinterpret_cast<const float*>(A) + (long long)sidx[r] * lda + k;
+        const float* row = reinterpret_cast<const float*>(A) +
+                           (PANEL ? pbase + (long long)sidx[r] * 32 : (long long)sidx[r] * lda + k);
         const float2 d2 = sdl2[r];
         float x[4];
         if (vec) {
@@ -610,21 +714,25 @@ k_update_dense(const T* __restrict__ A, long long lda, long long N, long long K,
   }
 }
 
-template __global__ void k_update_dense<double>(const double*, long long, long long, long long,
-                                                const int*, int, const double*, double, double*,
-                                                float2*, unsigned*);
-template __global__ void k_update_dense<float>(const float*, long long, long long, long long,
-                                               const int*, int, const double*, double, double*,
-                                               float2*, unsigned*);
+template __global__ void k_update_dense<double, false>(const double*, long long, long long,
+                                                       long long, const int*, int, const double*,
+                                                       double, double*, float2*, unsigned*);
+template __global__ void k_update_dense<float, false>(const float*, long long, long long, long long,
+                                                      const int*, int, const double*, double,
+                                                      double*, float2*, unsigned*);
+template __global__ void k_update_dense<float, true>(const float*, long long, long long, long long,
+                                                     const int*, int, const double*, double,
+                                                     double*, float2*, unsigned*);
 
 // ---------------------------------------------------------------------------
 // a6: full recompute  v[k] = c0 * y0[k] + c1 * sum_{r < N} A[r][k] x[r]
 // (primal: rho = y - X^T w, or z = X^T w; dual: w = -X alpha/(lambda n)).
 // Grid (K-blocks, row splits); row splits add into v with FP64 atomics after
 // split 0 wrote the c0 * y0 term.  FP32 A: x split in two FP32 halves,
-// FP32 sums over 32 rows, then FP64.
+// FP32 sums over 32 rows, then FP64.  PANEL (FP32 only): A stored as
+// 32-column panels [K/32][N][32] (zero-padded).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long K,
                   const double* __restrict__ x, const float2* __restrict__ x2, double c1,
@@ -646,7 +754,9 @@ k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long
   } else {
     // x split in FP32 halves (x2); FP32 partial sums over 32 rows folded into
     // compensated FP32 pairs
-    const bool vec = (nk == 4) && ((lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    const bool vec = PANEL || ((nk == 4) && ((lda & 3) == 0) &&
+                               ((reinterpret_cast<uintptr_t>(A) & 15) == 0));
+    const long long pbase = (k >> 5) * N * 32 + (k & 31);
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
     for (long long rb = r0; rb < r1; rb += 32) {
       float part[4] = {0.f, 0.f, 0.f, 0.f};
@@ -654,7 +764,7 @@ k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long
 #pragma unroll 8
       for (long long r = rb; r < re; ++r) {
         const float2 xs = __ldg(x2 + r);
-        const float* row = reinterpret_cast<const float*>(A) + r * lda + k;
+        const float* row = reinterpret_cast<const float*>(A) + (PANEL ? pbase + r * 32 : r * lda + k);
         float q[4];
         if (vec) {
           const float4 t = __ldg(reinterpret_cast<const float4*>(row));
@@ -675,10 +785,13 @@ k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long
   for (int e = 0; e < nk; ++e) atomicAdd(v + k + e, c1 * acc[e]);
 }
 
-template __global__ void k_recompute_dense<double>(const double*, long long, long long, long long,
-                                                   const double*, const float2*, double, long long,
-                                                   double*);
-template __global__ void k_recompute_dense<float>(const float*, long long, long long, long long,
+template __global__ void k_recompute_dense<double, false>(const double*, long long, long long,
+                                                          long long, const double*, const float2*,
+                                                          double, long long, double*);
+template __global__ void k_recompute_dense<float, true>(const float*, long long, long long, long long,
+                                                        const double*, const float2*, double,
+                                                        long long, double*);
+template __global__ void k_recompute_dense<float, false>(const float*, long long, long long, long long,
                                                   const double*, const float2*, double, long long,
                                                   double*);
 
@@ -838,57 +951,132 @@ void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, co
                                                Rs, pvec, Ginv, ndiag, sa, err);
 }
 
-void launch_chain(int b, size_t smem, cudaStream_t st, const double* R, const float2* Rs,
-                  const double* pvec, float2* Ginv, const SolveArgs& sa, unsigned* err) {
-  if (b <= 8) {
-    k_chain<8, 4, true><<<1, 256, smem, st>>>(R, Rs, pvec, Ginv, sa, err);
-  } else if (b <= 16) {
-    k_chain<16, 3, true><<<1, 256, smem, st>>>(R, Rs, pvec, Ginv, sa, err);
-  } else {
-    k_factor<<<sa.s_cur, 32, 0, st>>>(R, sa, Ginv, err);
-    k_chain<32, 2, false><<<1, 256, smem, st>>>(R, Rs, pvec, Ginv, sa, err);
-  }
+void launch_chain(int b, size_t smem, cudaStream_t st, const float2* Rs, const double* pvec,
+                  const float2* Ginv, const SolveArgs& sa, unsigned* err) {
+  if (b <= 8)
+    k_chain<8, 6><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
+  else if (b <= 16)
+    k_chain<16, 3><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
+  else
+    k_chain<32, 2><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
 }
 
-// Rs[i][j] = FP32 split of cG R[i][j] for the lower-triangle entries outside
-// the diagonal blocks (the sparse path forms R directly).
+template <typename K, typename... Args>
+cudaError_t launch_programmatic(K kernel, unsigned grid, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+int launch_reduce_chain(int grid, size_t smem, cudaStream_t st, const float* part,
+                        const double* ppart, int P, int sbp, double* R, float2* Rs, double* pvec,
+                        float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err,
+                        unsigned* ticket) {
+  cudaError_t e;
+  if (sa.b <= 8)
+    e = launch_programmatic(k_reduce_chain<float, 8, 6>, (unsigned)grid, smem, st, part, ppart, P,
+                            sbp, R, Rs, pvec, Ginv, ndiag, sa, err, ticket);
+  else if (sa.b <= 16)
+    e = launch_programmatic(k_reduce_chain<float, 16, 3>, (unsigned)grid, smem, st, part, ppart, P,
+                            sbp, R, Rs, pvec, Ginv, ndiag, sa, err, ticket);
+  else
+    e = cudaErrorInvalidValue;
+  return (int)e;
+}
+
+void launch_factor(cudaStream_t st, const double* R, const SolveArgs& sa, float2* Ginv,
+                   unsigned* err) {
+  k_factor<<<sa.s_cur, 256, 0, st>>>(R, sa, Ginv, err);
+}
+
+// Rs[j][i] = FP32 split of cG R[i][j] (transposed, as k_reduce writes it) for
+// the lower-triangle entries outside the diagonal blocks (the sparse path
+// forms R directly).
 __global__ void k_scale_split(const double* __restrict__ R, int ldr, int sb, int b, double cG,
                               float2* __restrict__ Rs) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)sb * sb) return;
   const int i = (int)(e / sb), j = (int)(e % sb);
-  if (j < i && i / b != j / b) Rs[(long long)i * ldr + j] = split_f64(cG * R[(long long)i * ldr + j]);
+  if (j < i && i / b != j / b) Rs[(long long)j * ldr + i] = split_f64(cG * R[(long long)i * ldr + j]);
 }
 
 void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
                          long long lda, long long N, long long K, const int* idx, int sb,
-                         const double* delta, double cU, double* v, float2* v2, unsigned* err) {
+                         const double* delta, double cU, double* v, float2* v2, unsigned* err,
+                         bool panel) {
   if (f64)
-    k_update_dense<double><<<grid, 256, smem, st>>>(static_cast<const double*>(A), lda, N, K, idx,
-                                                     sb, delta, cU, v, v2, err);
+    k_update_dense<double, false><<<grid, 256, smem, st>>>(static_cast<const double*>(A), lda, N, K,
+                                                            idx, sb, delta, cU, v, v2, err);
+  else if (panel)
+    k_update_dense<float, true><<<grid, 256, smem, st>>>(static_cast<const float*>(A), lda, N, K,
+                                                          idx, sb, delta, cU, v, v2, err);
   else
-    k_update_dense<float><<<grid, 256, smem, st>>>(static_cast<const float*>(A), lda, N, K, idx,
-                                                    sb, delta, cU, v, v2, err);
+    k_update_dense<float, false><<<grid, 256, smem, st>>>(static_cast<const float*>(A), lda, N, K,
+                                                           idx, sb, delta, cU, v, v2, err);
 }
 
 void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
                             long long N, long long K, const double* x, const float2* x2, double c1,
-                            long long rows_per_split, double* v) {
+                            long long rows_per_split, double* v, bool panel) {
   if (f64)
-    k_recompute_dense<double><<<grid, 256, 0, st>>>(static_cast<const double*>(A), lda, N, K, x, x2,
-                                                     c1, rows_per_split, v);
+    k_recompute_dense<double, false><<<grid, 256, 0, st>>>(static_cast<const double*>(A), lda, N, K,
+                                                            x, x2, c1, rows_per_split, v);
+  else if (panel)
+    k_recompute_dense<float, true><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K, x,
+                                                          x2, c1, rows_per_split, v);
   else
-    k_recompute_dense<float><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K, x, x2,
-                                                    c1, rows_per_split, v);
+    k_recompute_dense<float, false><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K,
+                                                           x, x2, c1, rows_per_split, v);
+}
+
+// Repack a row-major N x K FP32 matrix (leading dimension lda, 16-byte aligned
+// rows) into 32-column panels: P[(a N + r) 32 + c] = A[r][32 a + c], zero past
+// K.  Units of 128 bytes (one row of one panel), 8 lanes each; consecutive
+// units run along a row, so a warp reads 512 contiguous bytes and writes four
+// full 128-byte lines.
+__global__ void __launch_bounds__(256)
+k_pack_panels(const float* __restrict__ A, long long N, long long K, long long lda,
+              float* __restrict__ Pn) {
+  const long long na = (K + 31) / 32;
+  const long long units = N * na;
+  const int q = threadIdx.x & 7;
+  for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 3; u < units;
+       u += ((long long)gridDim.x * blockDim.x) >> 3) {
+    const long long r = u / na, a = u - r * na;
+    const long long k = a * 32 + 4 * q;
+    const float* src = A + r * lda + k;
+    float4 x;
+    if (k + 4 <= K) {
+      x = __ldg(reinterpret_cast<const float4*>(src));
+    } else {
+      x.x = k < K ? src[0] : 0.f;
+      x.y = k + 1 < K ? src[1] : 0.f;
+      x.z = k + 2 < K ? src[2] : 0.f;
+      x.w = 0.f;
+    }
+    *reinterpret_cast<float4*>(Pn + (a * N + r) * 32 + 4 * q) = x;
+  }
 }
 
 int set_solve_smem_limit(int bytes) {
-  cudaError_t e[6] = {
+  cudaError_t e[8] = {
       cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<8, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<16, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<32, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<8, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
       cudaFuncSetAttribute(k_reduce<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_reduce_chain<float, 8, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes),
+      cudaFuncSetAttribute(k_reduce_chain<float, 16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           bytes),
       cudaFuncSetAttribute(k_reduce<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return (int)x;

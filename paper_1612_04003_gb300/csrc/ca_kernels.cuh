@@ -11,23 +11,36 @@ void launch_gram_simt(bool f64, dim3 grid, cudaStream_t st, const void* A, long 
                       long long N, long long K, const int* idx, int sb, const double* v,
                       long long chunks_per_split, int sbp, double* part, double* ppart,
                       unsigned* err);
-// a4: reduce the split-K partials, then the chain (fast form: it inverts the
-// diagonal blocks itself, or k_factor does for b > 16) or the general solve.
+// a4: reduce the split-K partials (with ndiag > 0 also inverting the diagonal
+// blocks, b <= 16), invert them separately (launch_factor, from R), then the
+// chain (fast form) or the general solve.
 void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, const void* part,
                    const double* ppart, int P, int sbp, double* R, float2* Rs, double* pvec,
                    float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err);
-void launch_chain(int b, size_t smem, cudaStream_t st, const double* R, const float2* Rs,
-                  const double* pvec, float2* Ginv, const SolveArgs& sa, unsigned* err);
+void launch_chain(int b, size_t smem, cudaStream_t st, const float2* Rs, const double* pvec,
+                  const float2* Ginv, const SolveArgs& sa, unsigned* err);
+void launch_factor(cudaStream_t st, const double* R, const SolveArgs& sa, float2* Ginv,
+                   unsigned* err);
+// a4 in one programmatic-dependent launch (FP32 partials, b <= 16): reduce
+// with the diagonal-block inverses (ndiag = s_cur CTAs), then the chain on the
+// CTA that finishes last.  Returns a cudaError_t.
+int launch_reduce_chain(int grid, size_t smem, cudaStream_t st, const float* part,
+                        const double* ppart, int P, int sbp, double* R, float2* Rs, double* pvec,
+                        float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err,
+                        unsigned* ticket);
 __global__ void k_scale_split(const double* R, int ldr, int sb, int b, double cG, float2* Rs);
 __global__ void k_factor(const double* R, SolveArgs sa, float2* Ginv, unsigned* err);
 #define CA_FAST_B 32
 #define CA_FAST_SB 256
+// panel: FP32 A stored as 32-column panels [K/32][N][32] (k_pack_panels).
 void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
                          long long lda, long long N, long long K, const int* idx, int sb,
-                         const double* delta, double cU, double* v, float2* v2, unsigned* err);
+                         const double* delta, double cU, double* v, float2* v2, unsigned* err,
+                         bool panel);
 void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
                             long long N, long long K, const double* x, const float2* x2, double c1,
-                            long long rows_per_split, double* v);
+                            long long rows_per_split, double* v, bool panel);
+__global__ void k_pack_panels(const float* A, long long N, long long K, long long lda, float* Pn);
 int set_solve_smem_limit(int bytes);
 
 __global__ void k_solve(const double* R, const double* pvec, SolveArgs sa, unsigned* err);
@@ -64,7 +77,10 @@ struct GramUpdate {
   float2* v2;           // K entries as FP32 (hi, lo) pairs: read, updated in place
 };
 
+// panel: A is stored as 32-column panels (k_pack_panels), else row-major with
+// leading dimension lda (16-byte aligned rows).  The fused update needs panels.
 int launch_gram_tc(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
                    const float2* v2, int P, int sbp, float* part, double* ppart, unsigned* err,
-                   int three_pass, cudaStream_t stream, const GramUpdate* upd = nullptr);
+                   int three_pass, cudaStream_t stream, const GramUpdate* upd = nullptr,
+                   bool panel = false);
 int gram_tc_max_sb();

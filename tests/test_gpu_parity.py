@@ -289,6 +289,74 @@ def test_dual_dense_f32_tc(ctx, prec):
     assert _rel(a, a_ref) < tol and _rel(w, w_ref) < tol
 
 
+# ---------------------------------------------------------------------------
+# 32-column panel storage of X (the tensor-core path reads X this way)
+# ---------------------------------------------------------------------------
+def _panels_ref(A, K):
+    """Panels of the first K columns of A by their definition:
+    out[a, r, c] = A[r, 32 a + c], zero where 32 a + c >= K."""
+    N = A.shape[0]
+    na = (K + 31) // 32
+    out = np.zeros((na, N, 32), dtype=np.float32)
+    for a in range(na):
+        w = min(32, K - 32 * a)
+        out[a, :, :w] = A[:, 32 * a:32 * a + w]
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("N,K,ld", [(1, 1, 4), (37, 77, 80), (300, 1024, 1024), (5, 33, 36),
+                                    (3, 4100, 4100)])
+def test_pack_panels_layout(ctx, N, K, ld):
+    rng = np.random.default_rng(N + K)
+    A = rng.standard_normal((N, ld)).astype(np.float32)
+    out = torch.full(((K + 31) // 32 * N * 32,), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.ca_pack_panels(_dev(A), out, K=K)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), _panels_ref(A, K))
+
+
+def test_primal_prepacked_panels_match(ctx, mid32):
+    """X handed over already packed gives the iterates of the row-major X that
+    the solve packs itself (same kernels on the same panels; only the
+    order of FP64 atomic additions may differ)."""
+    d, n = mid32.X.shape
+    ld = (n + 3) // 4 * 4
+    Xp = np.zeros((d, ld), dtype=np.float32)
+    Xp[:, :n] = mid32.X
+    X = _dev(Xp)
+    y = _dev(mid32.y)
+    kw = dict(b=8, s=16, H=128, lam=1e-4, seed=3, prec="3xtf32")
+    w1 = torch.zeros(d, dtype=torch.float64, device="cuda")
+    z1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w1, z1, n=n, **kw)
+    P = torch.empty(((n + 31) // 32 * d * 32,), dtype=torch.float32, device="cuda")
+    ctx.ca_pack_panels(X, P, K=n)
+    w2 = torch.zeros(d, dtype=torch.float64, device="cuda")
+    z2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(P, y, w2, z2, panels=(d, n), **kw)
+    assert _rel(w2, w1.cpu().numpy()) < 1e-12 and _rel(z2, z1.cpu().numpy()) < 1e-12
+    import paper_1612_04003_gb300 as ca
+    with pytest.raises(ca.CaError) as ei:  # panels need a tensor-core Gram mode
+        ctx.ca_bcd_solve(P, y, w2, panels=(d, n), b=8, s=4, H=8, lam=1e-4, prec="f64")
+    assert ei.value.status == ca.CA_ERR_ARG
+
+
+def test_dual_prepacked_panels_match(ctx):
+    p = synth.dense_dual(d=1028, n=400, seed=6)
+    XT = _dev(np.ascontiguousarray(p.X.astype(np.float32).T))
+    y = _dev(p.y)
+    kw = dict(b=8, s=16, H=256, lam=1e-2, seed=2, prec="3xtf32")
+    a1 = torch.zeros(400, dtype=torch.float64, device="cuda")
+    w1 = torch.zeros(1028, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(XT, y, a1, w1, **kw)
+    P = torch.empty(((1028 + 31) // 32 * 400 * 32,), dtype=torch.float32, device="cuda")
+    ctx.ca_pack_panels(XT, P)
+    a2 = torch.zeros(400, dtype=torch.float64, device="cuda")
+    w2 = torch.zeros(1028, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(P, y, a2, w2, panels=(400, 1028), **kw)
+    assert _rel(a2, a1.cpu().numpy()) < 1e-12 and _rel(w2, w1.cpu().numpy()) < 1e-12
+
+
 @pytest.fixture(scope="module")
 def sparse_small():
     return synth.sparse_dual(d=4000, n=600, density=0.01, seed=3)
