@@ -253,8 +253,11 @@ int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long lo
 bool fast_solve(int b, int sb) { return b <= CA_FAST_B && sb <= CA_FAST_SB; }
 
 size_t chain_smem(int b, int sb) {
-  const size_t ring = b <= 8 ? 6 * 256 * 8 * 8 : (b <= 16 ? 3 * 256 * 16 * 8 : 2 * 256 * 32 * 8);
-  return ring + (size_t)sb * b * 8 + 64 * 8 + (size_t)sb * 12 + 64;
+  if (b <= 16) {  // lookahead chain: ring | Gamma^{-1} | rhs0 | Delta | hand-over | indices
+    const size_t ring = b <= 8 ? (size_t)4 * 8 * 256 * 8 : (size_t)3 * 16 * 256 * 8;
+    return ring + (size_t)sb * b * 8 + 256 * 8 + 256 * 8 + 64 * 8 + 256 * 4 + 64;
+  }
+  return (size_t)2 * 32 * 256 * 8 + (size_t)sb * b * 8 + 64 * 8 + (size_t)sb * 12 + 64;
 }
 
 // a4: the chain (fast form, from Rs, p and the inverted diagonal blocks

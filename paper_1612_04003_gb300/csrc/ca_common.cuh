@@ -182,11 +182,25 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
 
 __device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
+// (hi, lo) from a compensated-sum pair whose lo may exceed ulp(hi)/2
+__device__ __forceinline__ float2 df_norm(float hi, float lo) {
+  const float h = hi + lo;
+  return make_float2(h, lo - (h - hi));
+}
+
 __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   const float p = a.x * b.x;
   const float e = fmaf(a.x, b.x, -p) + fmaf(a.x, b.y, a.y * b.x);
   const float h = p + e;
   return make_float2(h, e - (h - p));
+}
+
+// 1/d for a positive double-float d: the FP32 reciprocal refined by one
+// Newton step r + r (1 - d r) in double-float arithmetic (~2^-44 relative).
+__device__ __forceinline__ float2 df_rcp(float2 d) {
+  const float r = __frcp_rn(d.x);
+  const float2 e = df_add(make_float2(1.f, 0.f), df_neg(df_mul(d, make_float2(r, 0.f))));
+  return df_add(make_float2(r, 0.f), df_mul(make_float2(r, 0.f), e));
 }
 
 // (shi, slo) += a * b, with a and b double-float values

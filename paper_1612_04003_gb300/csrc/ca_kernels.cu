@@ -237,14 +237,14 @@ __device__ void block_solve(const double* __restrict__ R, const double* __restri
 // a_ij -> a_ij - a_ik a_kj / a_kk; after all b pivots the matrix is -Gamma^{-1}.
 // The sweep keeps the matrix symmetric, so pivot k needs only column k.  The
 // CTA's 256 threads own one entry each (thread t: entries t + 256 q of the
-// row-major b x b matrix, values in a[q]); before pivot k the owners of column
-// k publish it to shared memory and the owner of a_kk its reciprocal (Newton-
-// Raphson), once (two buffers alternate: one barrier per pivot).  FP64 is
-// scarce on this part, so threads without entries do no FP64 work.  Every
-// thread of the CTA calls this.  Writes Gamma^{-1} (FP32 pairs, row-major) to
-// out; a non-positive pivot raises CA_DEV_ERR_NOT_SPD.
+// row-major b x b matrix, values a[q] in double-float); before pivot k the
+// owners of column k publish it to shared memory and the owner of a_kk its
+// reciprocal (two buffers alternate: one barrier per pivot).  Double-float on
+// the FP32 pipe keeps the ~2^-44 accuracy at a fraction of the FP64 latency
+// of this part.  Every thread of the CTA calls this.  Writes Gamma^{-1} (FP32
+// pairs, row-major) to out; a non-positive pivot raises CA_DEV_ERR_NOT_SPD.
 template <int EPT>
-__device__ void cta_sweep_inverse(double (&a)[EPT], int b, double* __restrict__ colbuf,
+__device__ void cta_sweep_inverse(float2 (&a)[EPT], int b, float2* __restrict__ colbuf,
                                   float2* __restrict__ out, unsigned* __restrict__ err) {
   const int t = threadIdx.x;
   int ri[EPT], ci[EPT];
@@ -256,55 +256,79 @@ __device__ void cta_sweep_inverse(double (&a)[EPT], int b, double* __restrict__ 
   }
   const bool active = t < b * b;
   for (int k = 0; k < b; ++k) {
-    double* ck = colbuf + (k & 1) * 33;  // [0, b): column k; [32]: 1 / a_kk
+    float2* ck = colbuf + (k & 1) * 33;  // [0, b): column k; [32]: 1 / a_kk
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       if (ci[q] == k) {
         ck[ri[q]] = a[q];
         if (ri[q] == k) {
-          double d = a[q];
-          if (!(d > 0.0)) {
+          float2 d = a[q];
+          if (!(d.x > 0.f)) {
             ca_flag(err, CA_DEV_ERR_NOT_SPD);
-            d = 1.0;
+            d = make_float2(1.f, 0.f);
           }
-          ck[32] = rcp_newton(d);
+          ck[32] = df_rcp(d);
         }
       }
     }
     __syncthreads();
     if (active) {
-      const double rd = ck[32];
+      const float2 rd = ck[32];
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
         const int i = ri[q], j = ci[q];
         if (i < 0) continue;
-        if (i == k && j == k) a[q] = -rd;
-        else if (i == k) a[q] = ck[j] * rd;
-        else if (j == k) a[q] = ck[i] * rd;
-        else a[q] = fma(-ck[i] * rd, ck[j], a[q]);
+        if (i == k && j == k) a[q] = df_neg(rd);
+        else if (i == k) a[q] = df_mul(ck[j], rd);
+        else if (j == k) a[q] = df_mul(ck[i], rd);
+        else a[q] = df_add(a[q], df_neg(df_mul(df_mul(ck[i], rd), ck[j])));
       }
     }
   }
 #pragma unroll
   for (int q = 0; q < EPT; ++q)
-    if (ri[q] >= 0) out[t + 256 * q] = split_f64(-a[q]);
+    if (ri[q] >= 0) out[t + 256 * q] = df_neg(a[q]);
 }
 
 // Sum of the partials c = c0, c0 + step, ... < P of one entry (stride sq
-// between partials); FP32 partials are summed with compensation.
+// between partials), as a double-float value.  Up to 24 (FP32) or 16 (FP64)
+// loads are in flight at once (independent of the sums); FP32 partials are
+// added in four compensated chains, FP64 partials by a pairwise FP64 tree.
 template <typename PT>
-__device__ __forceinline__ double sum_partials(const PT* __restrict__ src, int c0, int P, int step,
+__device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c0, int P, int step,
                                                long long sq) {
+  constexpr int U = 24;
   if constexpr (sizeof(PT) == 4) {
-    float hi = 0.f, lo = 0.f;
-#pragma unroll 8
-    for (int c = c0; c < P; c += step) comp_add(hi, lo, __ldcg(src + c * sq));
-    return (double)hi + (double)lo;
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int base = c0; base < P; base += U * step) {
+      float v[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const int c = base + i * step;
+        v[i] = c < P ? __ldcg(src + c * sq) : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < U; ++i) comp_add(h[i & 3], l[i & 3], v[i]);
+    }
+    return df_add(df_add(df_norm(h[0], l[0]), df_norm(h[1], l[1])),
+                  df_add(df_norm(h[2], l[2]), df_norm(h[3], l[3])));
   } else {
-    double s = 0.0;
-#pragma unroll 8
-    for (int c = c0; c < P; c += step) s += __ldcg(src + c * sq);
-    return s;
+    constexpr int UD = 16;  // a power of two: the pairwise tree below halves it
+    double acc = 0.0;
+    for (int base = c0; base < P; base += UD * step) {
+      double v[UD];
+#pragma unroll
+      for (int i = 0; i < UD; ++i) {
+        const int c = base + i * step;
+        v[i] = c < P ? __ldcg(src + c * sq) : 0.0;
+      }
+#pragma unroll
+      for (int w = UD / 2; w >= 1; w /= 2)
+#pragma unroll
+        for (int i = 0; i < w; ++i) v[i] += v[i + w];
+      acc += v[0];
+    }
+    return split_f64(acc);
   }
 }
 
@@ -314,24 +338,27 @@ __device__ __forceinline__ double sum_partials(const PT* __restrict__ src, int c
 // chain reads a column block with coalesced loads.  CTAs 0 .. ndiag-1 each
 // reduce one diagonal block Gamma_j = cG R_jj + cI I (b <= 16) and invert it
 // into Ginv[j] (cta_sweep_inverse); the other CTAs take 32 entries per pass
-// (one per lane), the 8 warps splitting the P partials.
+// (one per lane), the 8 warps splitting the P partials.  Sums are
+// double-float; R is written in FP64.
 template <typename PT>
 __device__ void reduce_body(const PT* __restrict__ part, const double* __restrict__ ppart, int P,
                             int sbp, double* __restrict__ R, float2* __restrict__ Rs,
                             double* __restrict__ pvec, float2* __restrict__ Ginv, int ndiag,
                             const SolveArgs& sa, unsigned* __restrict__ err, int cta, int ncta) {
-  __shared__ double red[8][32];
-  __shared__ double Mb[256];
-  __shared__ double colbuf[66];
+  __shared__ float2 red[8][32];
+  __shared__ float2 Mb[256];
+  __shared__ float2 colbuf[66];
+  __shared__ double redp[8][32];
   const int sb = sa.sb, ldr = sa.ldr;
   const long long sq = (long long)sbp * sbp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float2 cG2 = split_f64(sa.cG), cI2 = split_f64(sa.cI);
   if (cta < ndiag) {
     const int b = sa.b, base = cta * b;
     const int E = b * (b + 1) / 2;
     const int nsl = 256 / E;  // >= 1 for b <= 16
     const int sl = tid / E, e = tid - sl * E;
-    double* flat = &red[0][0];
+    float2* flat = &red[0][0];
     if (sl < nsl) {
       int i, j;
       tri_decode(e, i, j);
@@ -339,16 +366,17 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
     }
     __syncthreads();
     if (tid < E) {
-      double t = 0.0;
-      for (int q = 0; q < nsl; ++q) t += flat[q * E + tid];
+      float2 t = make_float2(0.f, 0.f);
+      for (int q = 0; q < nsl; ++q) t = df_add(t, flat[q * E + tid]);
       int i, j;
       tri_decode(tid, i, j);
-      const double v = sa.cG * t + (i == j ? sa.cI : 0.0);
+      float2 v = df_mul(cG2, t);
+      if (i == j) v = df_add(v, cI2);
       Mb[i * b + j] = v;
       Mb[j * b + i] = v;
     }
     __syncthreads();
-    double a[1] = {tid < b * b ? Mb[tid] : 0.0};
+    float2 a[1] = {tid < b * b ? Mb[tid] : make_float2(0.f, 0.f)};
     cta_sweep_inverse<1>(a, b, colbuf, Ginv + (long long)cta * b * b, err);
     return;
   }
@@ -358,7 +386,8 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
     const long long e = e0 + lane;
     int i = 0, j = 0;
     int kind = 0;  // 0 none, 1 Gram entry, 2 projection entry
-    double s = 0.0;
+    float2 s2 = make_float2(0.f, 0.f);
+    double sp = 0.0;
     if (e < nlow) {
       tri_decode(e, i, j);
       kind = 1;
@@ -367,21 +396,24 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
       i = (int)(e - nlow);
     }
     if (kind == 1) {
-      s = sum_partials(part + (long long)i * sbp + j, warp, P, 8, sq);
+      s2 = sum_partials(part + (long long)i * sbp + j, warp, P, 8, sq);
     } else if (kind == 2) {
-#pragma unroll 4
-      for (int c = warp; c < P; c += 8) s += ppart[(long long)c * sbp + i];
+      const float2 q = sum_partials(ppart + i, warp, P, 8, (long long)sbp);
+      sp = (double)q.x + (double)q.y;
     }
-    red[warp][lane] = s;
+    red[warp][lane] = s2;
+    redp[warp][lane] = sp;
     __syncthreads();
     if (warp == 0 && kind) {
-      double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) t += red[w][lane];
       if (kind == 1) {
-        R[(long long)i * ldr + j] = t;
-        if (Rs) Rs[(long long)j * ldr + i] = split_f64(sa.cG * t);
+        float2 t = df_add(df_add(df_add(red[0][lane], red[1][lane]), df_add(red[2][lane], red[3][lane])),
+                          df_add(df_add(red[4][lane], red[5][lane]), df_add(red[6][lane], red[7][lane])));
+        R[(long long)i * ldr + j] = (double)t.x + (double)t.y;
+        if (Rs) Rs[(long long)j * ldr + i] = df_mul(cG2, t);
       } else {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += redp[w][lane];
         pvec[i] = t;
       }
     }
@@ -408,17 +440,17 @@ template __global__ void k_reduce<float>(const float*, const double*, int, int, 
 __global__ void __launch_bounds__(256)
 k_factor(const double* __restrict__ R, SolveArgs sa, float2* __restrict__ Ginv,
          unsigned* __restrict__ err) {
-  __shared__ double colbuf[66];
+  __shared__ float2 colbuf[66];
   const int b = sa.b, base = (int)blockIdx.x * b;
-  double a[4];
+  float2 a[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int e = (int)threadIdx.x + 256 * q;
-    a[q] = 0.0;
+    a[q] = make_float2(0.f, 0.f);
     if (e < b * b) {
       const int i = e / b, c = e - (e / b) * b;
       const int hi = i > c ? i : c, lo = i > c ? c : i;
-      a[q] = sa.cG * R[(long long)(base + hi) * sa.ldr + (base + lo)] + (i == c ? sa.cI : 0.0);
+      a[q] = split_f64(sa.cG * R[(long long)(base + hi) * sa.ldr + (base + lo)] + (i == c ? sa.cI : 0.0));
     }
   }
   cta_sweep_inverse<4>(a, b, colbuf, Ginv + (long long)blockIdx.x * b * b, err);
@@ -427,6 +459,7 @@ k_factor(const double* __restrict__ R, SolveArgs sa, float2* __restrict__ Ginv,
 // Sum of n double-float values by a balanced tree (n a power of two).
 template <int N>
 __device__ __forceinline__ float2 df_tree_sum(float2 (&v)[N]) {
+  static_assert(N > 0 && (N & (N - 1)) == 0, "pairwise tree over a power of two");
 #pragma unroll
   for (int w = N / 2; w >= 1; w /= 2)
 #pragma unroll
@@ -552,12 +585,206 @@ __device__ void chain_body(const float2* __restrict__ Rs, const double* __restri
   }
 }
 
+__device__ __forceinline__ float2 shfl_xor_df(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ float2 shfl_df(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ void named_bar_sync(int id) {
+  asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id) {
+  asm volatile("bar.arrive %0, 256;" ::"r"(id) : "memory");
+}
+
+// The dependent chain with lookahead (one CTA of 256 threads; b <= BMAX <= 16,
+// sb <= 256), from Rs (cG-scaled, transposed), p and the diagonal-block
+// inverses Ginv.  Warp 0 runs only the dependent path: for step j it forms
+// Delta_j = Gamma_j^{-1} rb_j (BMAX x BMAX products over 32 lanes, shuffle
+// sums), publishes it, folds it into the b rows of block j+1 and adds the
+// sums the other warps kept for those rows, which gives rb_{j+1}.  Warps 1-7
+// fold each published Delta_j into the rows >= (j+2) b (two rows per
+// thread), hand over the sums of the rows of block j+2, and stream the Rs
+// columns of later steps through a shared-memory ring (16-byte cp.async.cg
+// copies of row pairs, slot layout [q][row]).  Warp 0 and the others meet at
+// named barriers, two per step alternating by parity (D: Delta_j published;
+// F: the folds of step j done), so neither waits for a full-CTA barrier.  The
+// index-overlap term cI [I_r = I_t] Delta_t (eq. "recur" and its dual
+// analogue) is added where the sampled indices coincide.  All arithmetic on
+// the dependent path is double-float; FP64 converts in and out.
+template <int BMAX, int DEPTH>
+__device__ void chain_la_body(const float2* __restrict__ Rs, const double* __restrict__ pvec,
+                              const float2* __restrict__ Ginv, const SolveArgs& a,
+                              unsigned* __restrict__ err, double* smem_d) {
+  static_assert(BMAX == 8 || BMAX == 16, "lookahead chain: BMAX 8 or 16");
+  constexpr int LPR = 32 / BMAX, CPL = BMAX / LPR;  // warp 0: lanes per row, columns per lane
+  constexpr unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = a.b, sb = a.sb, ldr = a.ldr, s = a.s_cur;
+  float2* ring = reinterpret_cast<float2*>(smem_d);     // DEPTH x BMAX x 256
+  float2* Gs = ring + (size_t)DEPTH * BMAX * 256;       // sb*b: Gamma_j^{-1}
+  float2* rhs0s = Gs + (size_t)sb * b;                   // 256: cP p - cI x0 - cY y
+  float2* dall = rhs0s + 256;                            // 256: all Delta
+  float2* accb = dall + 256;                             // [2][16]: sums handed to warp 0
+  float2* ovlb = accb + 32;                              // [2][16]: overlap sums
+  int* sidx = reinterpret_cast<int*>(ovlb + 32);         // 256
+  const uint32_t ring0 = smem_u32(ring);
+  const bool ld_ok = (ldr & 1) == 0;  // 16-byte row pairs need an even leading dimension
+  if (!ld_ok && tid == 0) ca_flag(err, CA_DEV_ERR_ARG);
+  const int cu = tid - 32;  // index among warps 1-7
+  auto fetch = [&](int j) {  // warps 1-7: columns jb .. jb+b of rows >= jb + b, slot j % DEPTH
+    const int jb = j * b;
+    if (j < s && ld_ok) {
+      const int p0 = (jb + b) >> 1, np = ((sb + 1) >> 1) - p0;
+      for (int u = cu; u < b * np; u += 224) {
+        const int q = u / np, pr = 2 * (p0 + u - q * np);
+        cp_async_16_zfill(ring0 + 8u * (uint32_t)(((j % DEPTH) * BMAX + q) * 256 + pr),
+                          Rs + (long long)(jb + q) * ldr + pr, 16u);
+      }
+    }
+    cp_async_commit();
+  };
+  if (warp > 0)
+    for (int d = 0; d < DEPTH - 1; ++d) fetch(d);
+  for (int e = tid; e < sb * b; e += 256) Gs[e] = __ldcg(Ginv + e);
+  if (tid < sb) {
+    const int gi = a.idx[tid];
+    double v = a.cP * __ldcg(pvec + tid);
+    if (gi >= 0 && gi < a.N) {
+      v -= a.cI * __ldcg(a.x + gi);
+      if (a.yv) v -= a.cY * a.yv[gi];
+    } else {
+      ca_flag(err, CA_DEV_ERR_ARG);
+    }
+    rhs0s[tid] = split_f64(v);
+    sidx[tid] = gi;
+  }
+  if (warp > 0) cp_async_wait<DEPTH - 2>();  // step 0's columns
+  __syncthreads();
+  const float2 cI2 = split_f64(a.cI);
+  const float2 z2 = make_float2(0.f, 0.f);
+  if (warp == 0) {
+    const int i = lane / LPR, c0 = (lane % LPR) * CPL;
+    float2 rbv = i < b ? rhs0s[i] : z2;  // rb of the current block, row i
+    for (int j = 0; j < s; ++j) {
+      const int jb = j * b;
+      float2 pr[CPL];
+#pragma unroll
+      for (int cc = 0; cc < CPL; ++cc) {
+        const int c = c0 + cc;
+        const float2 rbc = shfl_df(rbv, c * LPR);
+        pr[cc] = (i < b && c < b) ? df_mul(Gs[(size_t)j * b * b + i * b + c], rbc) : z2;
+      }
+      float2 dl = df_tree_sum(pr);
+#pragma unroll
+      for (int o = LPR / 2; o >= 1; o /= 2) dl = df_add(dl, shfl_xor_df(dl, o));
+      if (i < b && (lane % LPR) == 0) dall[jb + i] = dl;
+      __syncwarp();
+      named_bar_arrive(2 + (j & 1));  // D(j): Delta_j published
+      if (j + 1 < s) {
+        if (j >= 1) named_bar_sync(4 + ((j - 1) & 1));  // F(j-1): sums of block j+1, columns of step j
+        const int rowp = (j + 1) * b + i;
+        const bool rv = i < b && rowp < sb;
+        const int gp = rv ? sidx[rowp] : -2;
+        const float2* slot = ring + (size_t)(j % DEPTH) * BMAX * 256;
+        float2 u[CPL];
+        float2 ov = z2;
+        bool hit = false;
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc) {
+          const int c = c0 + cc;
+          const float2 dc = shfl_df(dl, c * LPR);
+          u[cc] = z2;
+          if (rv && c < b) {
+            u[cc] = df_mul(slot[c * 256 + rowp], dc);
+            if (sidx[jb + c] == gp) {
+              ov = df_add(ov, dc);
+              hit = true;
+            }
+          }
+        }
+        float2 us = df_tree_sum(u);
+#pragma unroll
+        for (int o = LPR / 2; o >= 1; o /= 2) us = df_add(us, shfl_xor_df(us, o));
+        if (__any_sync(FULL, hit)) {
+#pragma unroll
+          for (int o = LPR / 2; o >= 1; o /= 2) ov = df_add(ov, shfl_xor_df(ov, o));
+        }
+        const int hb = ((j + 1) & 1) * 16 + i;
+        const float2 accv = (j >= 1 && rv) ? accb[hb] : z2;
+        const float2 ovv = (j >= 1 && rv) ? ovlb[hb] : z2;
+        rbv = rv ? df_add(rhs0s[rowp], df_neg(df_add(df_add(accv, us), df_mul(cI2, df_add(ovv, ov)))))
+                 : z2;
+      }
+    }
+  } else {
+    const int r1 = cu, r2 = cu + 224;
+    const int g1 = r1 < sb ? sidx[r1] : -2, g2 = r2 < sb ? sidx[r2] : -2;
+    float2 acc1 = z2, acc2 = z2, ov1 = z2, ov2 = z2;
+    for (int j = 0; j < s; ++j) {
+      const int jb = j * b, lo = (j + 2) * b;
+      named_bar_sync(2 + (j & 1));  // D(j)
+      const float2* slot = ring + (size_t)(j % DEPTH) * BMAX * 256;
+      float2 dq[BMAX];
+      int iq[BMAX];
+#pragma unroll
+      for (int q = 0; q < BMAX; ++q) {
+        dq[q] = q < b ? dall[jb + q] : z2;
+        iq[q] = q < b ? sidx[jb + q] : -3;
+      }
+      auto fold = [&](int r, int g, float2& acc, float2& ov) {
+        float2 pr[BMAX];
+        unsigned m = 0;
+#pragma unroll
+        for (int q = 0; q < BMAX; ++q) {
+          pr[q] = q < b ? df_mul(slot[q * 256 + r], dq[q]) : z2;
+          m |= (iq[q] == g) ? (1u << q) : 0u;
+        }
+        acc = df_add(acc, df_tree_sum(pr));
+        while (m) {  // sampled index shared with an earlier row (rare)
+          const int q = __ffs(m) - 1;
+          ov = df_add(ov, dall[jb + q]);
+          m &= m - 1;
+        }
+      };
+      if (r1 >= lo && r1 < sb) fold(r1, g1, acc1, ov1);
+      if (r2 >= lo && r2 < sb) fold(r2, g2, acc2, ov2);
+      const int hb = ((j + 2) & 1) * 16;
+      if (r1 >= lo && r1 < lo + b && r1 < sb) {
+        accb[hb + r1 - lo] = acc1;
+        ovlb[hb + r1 - lo] = ov1;
+      }
+      if (r2 >= lo && r2 < lo + b && r2 < sb) {
+        accb[hb + r2 - lo] = acc2;
+        ovlb[hb + r2 - lo] = ov2;
+      }
+      fetch(j + DEPTH - 1);        // into the slot of step j-1 (warp 0 is done with it)
+      cp_async_wait<DEPTH - 2>();  // this thread's columns of step j+1 have landed
+      if (j + 2 < s) named_bar_arrive(4 + (j & 1));  // F(j)
+    }
+    cp_async_wait<0>();
+  }
+  __syncthreads();
+  if (tid < sb) {  // Delta out, x += Delta (atomic: an index may recur across blocks)
+    const float2 d2 = dall[tid];
+    const double dv = (double)d2.x + (double)d2.y;
+    if (!isfinite(dv)) ca_flag(err, CA_DEV_ERR_NONFINITE);
+    a.delta[tid] = dv;
+    const int g = sidx[tid];
+    if (g >= 0 && g < a.N) atomicAdd(a.x + g, dv);
+  }
+}
+
 template <int BMAX, int DEPTH>
 __global__ void __launch_bounds__(256)
 k_chain(const float2* __restrict__ Rs, const double* __restrict__ pvec,
         const float2* __restrict__ Ginv, SolveArgs a, unsigned* __restrict__ err) {
   extern __shared__ double smem_d[];
-  chain_body<BMAX, DEPTH>(Rs, pvec, Ginv, a, err, smem_d);
+  if constexpr (BMAX <= 16)
+    chain_la_body<BMAX, DEPTH>(Rs, pvec, Ginv, a, err, smem_d);
+  else
+    chain_body<BMAX, DEPTH>(Rs, pvec, Ginv, a, err, smem_d);
 }
 
 // a4 in one launch (b <= 16): the reduction with the diagonal-block
@@ -589,17 +816,17 @@ k_reduce_chain(const PT* __restrict__ part, const double* __restrict__ ppart, in
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  chain_body<BMAX, DEPTH>(Rs, pvec, Ginv, sa, err, smem_d);
+  chain_la_body<BMAX, DEPTH>(Rs, pvec, Ginv, sa, err, smem_d);
 }
 
-template __global__ void k_reduce_chain<float, 8, 6>(const float*, const double*, int, int, double*,
+template __global__ void k_reduce_chain<float, 8, 4>(const float*, const double*, int, int, double*,
                                                      float2*, double*, float2*, int, SolveArgs,
                                                      unsigned*, unsigned*);
 template __global__ void k_reduce_chain<float, 16, 3>(const float*, const double*, int, int,
                                                       double*, float2*, double*, float2*, int,
                                                       SolveArgs, unsigned*, unsigned*);
 
-template __global__ void k_chain<8, 6>(const float2*, const double*, const float2*, SolveArgs,
+template __global__ void k_chain<8, 4>(const float2*, const double*, const float2*, SolveArgs,
                                        unsigned*);
 template __global__ void k_chain<16, 3>(const float2*, const double*, const float2*, SolveArgs,
                                         unsigned*);
@@ -954,7 +1181,7 @@ void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, co
 void launch_chain(int b, size_t smem, cudaStream_t st, const float2* Rs, const double* pvec,
                   const float2* Ginv, const SolveArgs& sa, unsigned* err) {
   if (b <= 8)
-    k_chain<8, 6><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
+    k_chain<8, 4><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
   else if (b <= 16)
     k_chain<16, 3><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
   else
@@ -982,7 +1209,7 @@ int launch_reduce_chain(int grid, size_t smem, cudaStream_t st, const float* par
                         unsigned* ticket) {
   cudaError_t e;
   if (sa.b <= 8)
-    e = launch_programmatic(k_reduce_chain<float, 8, 6>, (unsigned)grid, smem, st, part, ppart, P,
+    e = launch_programmatic(k_reduce_chain<float, 8, 4>, (unsigned)grid, smem, st, part, ppart, P,
                             sbp, R, Rs, pvec, Ginv, ndiag, sa, err, ticket);
   else if (sa.b <= 16)
     e = launch_programmatic(k_reduce_chain<float, 16, 3>, (unsigned)grid, smem, st, part, ppart, P,
@@ -1069,11 +1296,11 @@ k_pack_panels(const float* __restrict__ A, long long N, long long K, long long l
 int set_solve_smem_limit(int bytes) {
   cudaError_t e[8] = {
       cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<8, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
+      cudaFuncSetAttribute(k_chain<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
       cudaFuncSetAttribute(k_chain<16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
       cudaFuncSetAttribute(k_chain<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
       cudaFuncSetAttribute(k_reduce<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_reduce_chain<float, 8, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_reduce_chain<float, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes),
       cudaFuncSetAttribute(k_reduce_chain<float, 16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            bytes),
