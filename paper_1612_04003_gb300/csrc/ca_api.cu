@@ -320,7 +320,13 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   const int sbm = (int)(std::min<long long>(s, H) * b);
   Carve cv{work};
   (void)work_bytes;
-  const GramPlan g = gram_plan(ctx, pb.xfmt, o->prec, sbm, K);
+  GramPlan g = gram_plan(ctx, pb.xfmt, o->prec, sbm, K);
+  if (g.tc && pb.panel && g.sbp <= 128 && b <= 16 && fast_solve(b, sbm) && ctx->num_sms > 1) {
+    // the chain of step k runs on one SM (last CTA of the reduce launch) while
+    // the Gram CTAs of step k+1 prepare: leave that SM to it, so that no Gram
+    // CTA starts only after the chain
+    g.P = (int)std::min<long long>(ctx->num_sms - 1, (K + 31) / 32);
+  }
   const int sbp = g.sbp, P = g.P;
   void* part = g.tc ? (void*)cv.take<float>((size_t)P * sbp * sbp)
                     : (void*)cv.take<double>((size_t)P * sbp * sbp);

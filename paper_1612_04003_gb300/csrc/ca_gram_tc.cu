@@ -173,7 +173,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
   // zero-filled by the copies (row-major) or zero in the panels.
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {  // (3xTF32 uses the first MS pairs)
-      mbar_init(&full[s], kLoaderThreads);
+      mbar_init(&full[s], kLoaderWarps);  // one arrival per loader warp
       mbar_init(&empty[s], 1);
     }
     mbar_init(done, 1);
@@ -264,6 +264,16 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       plo[i] = 0.f;
     }
     bool ok = true;
+    // one lane waits on the barrier, the warp follows (a wait by every lane
+    // would serialise 32 accesses to the same shared-memory word); once a
+    // wait has timed out no further waits are made
+    auto warp_wait = [&](uint64_t* bar, uint32_t parity, bool ok_in) -> bool {
+      bool r = ok_in;
+      if (lane == 0 && r) r = mbar_wait_bounded(bar, parity, err);
+      r = __shfl_sync(0xffffffffu, r ? 1 : 0, 0) != 0;
+      __syncwarp();
+      return r;
+    };
     // stages in flight ahead of the one being processed: 3xTF32 refills a
     // slot right after consuming it; plain TF32 refills the slot of the
     // previous stage once its MMA has completed
@@ -291,8 +301,9 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       const int st = t % NS;
       unsigned char* big = raw + st * C::kRawBytes;
       if constexpr (!THREE) {  // the tile is ready for the MMA as loaded
-        fence_proxy_async_smem();
-        mbar_arrive(&full[st]);
+        fence_proxy_async_smem();  // this thread's copies, visible to the tensor core
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[st]);
       }
       float vh[4], vl[4];
       if constexpr (UPD) {
@@ -367,7 +378,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         // head / tail tiles into MMA slot t % MS once the MMA of stage t - MS
         // has read it; then hand the slot to the MMA
         const int ms = t % MS;
-        if (ok && t >= MS) ok = mbar_wait_bounded(&empty[ms], (uint32_t)((t / MS - 1) & 1), err);
+        if (t >= MS) ok = warp_wait(&empty[ms], (uint32_t)((t / MS - 1) & 1), ok);
         unsigned char* hi = mring + ms * C::kMmaSlotBytes;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
@@ -377,8 +388,9 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
           *reinterpret_cast<float4*>(hi + C::kTileBytes + dsto[i]) =
               make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
         }
-        fence_proxy_async_smem();
-        mbar_arrive(&full[ms]);
+        fence_proxy_async_smem();  // this thread's tiles, visible to the tensor core
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[ms]);
         // this thread's part of load slot st is consumed: refill it
         if (t + NS < T) issue(t + NS, st);
         cp_async_commit();
@@ -387,30 +399,36 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         const int tn = t + NS - 1;
         if (ok && tn < T) {
           const int sn = tn % NS;
-          if (tn >= NS) ok = mbar_wait_bounded(&empty[sn], (uint32_t)((tn / NS - 1) & 1), err);
+          if (tn >= NS) ok = warp_wait(&empty[sn], (uint32_t)((tn / NS - 1) & 1), ok);
           if (ok) issue(tn, sn);
         }
         cp_async_commit();
       }
     }
     cp_async_wait<0>();
-    // projection partials: reduce over the 8 lanes sharing a row group
+    // projection partials: reduce over the 8 lanes sharing a row group in
+    // double-float (FP64 is slow on this part), one FP64 sum at the end
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
-      double s = (double)phi[i] + ((double)plo[i] + (double)pacc[i]);
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      s += __shfl_xor_sync(0xffffffffu, s, 4);
-      if (l == 0) ppart[(long long)c * SBP + g + 32 * i] = s;
+      comp_add(phi[i], plo[i], pacc[i]);
+      float2 s2 = df_norm(phi[i], plo[i]);
+#pragma unroll
+      for (int o = 1; o <= 4; o <<= 1)
+        s2 = df_add(s2, make_float2(__shfl_xor_sync(0xffffffffu, s2.x, o),
+                                    __shfl_xor_sync(0xffffffffu, s2.y, o)));
+      if (l == 0) ppart[(long long)c * SBP + g + 32 * i] = (double)s2.x + (double)s2.y;
     }
     // ---------------- epilogue: TMEM -> FP32 partial tiles ----------------
-    mbar_wait_bounded(done, 0u, err);
+    warp_wait(done, 0u, true);
     tc_fence_after();
     // warp w reads TMEM lanes 32 (w % 4) .. +31 (= rows of the M = 128 tile)
     // and the 32-column chunks of parity w / 4
     const int lg = warp & 3, cpar = warp >> 2;
     const int trow = lg * 32 + lane;
     const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
+    // partial tiles are stored transposed: entry (row, col) at [col][row], so
+    // that the 32 lanes (32 consecutive rows) of a warp write 128 contiguous
+    // bytes per column
     float* Pc = part + (long long)c * SBP * SBP;
     if constexpr (C::kSym) {
       // G = D + T + T^T: T goes through the (now idle) stage buffers as a
@@ -427,16 +445,11 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         uint32_t r[32];
         tmem_ld32(tbase + (uint32_t)cc, r);
         if (cc <= trow && trow < SBP) {  // rows past a short tile hold garbage
-          float4* dst = reinterpret_cast<float4*>(Pc + (long long)trow * SBP + cc);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float o[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int col = cc + 4 * q + e;
-              o[e] = __uint_as_float(r[4 * q + e]) + Ts[trow * 129 + col] + Ts[col * 129 + trow];
-            }
-            dst[q] = make_float4(o[0], o[1], o[2], o[3]);
+          for (int q = 0; q < 32; ++q) {
+            const int col = cc + q;
+            Pc[(long long)col * SBP + trow] =
+                __uint_as_float(r[q]) + Ts[trow * 129 + col] + Ts[col * 129 + trow];
           }
         }
       }
@@ -445,11 +458,8 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       uint32_t r[32];
       tmem_ld32(tbase + (uint32_t)cc, r);
       if (cc <= trow && trow < SBP) {  // rows past a short tile hold garbage
-        float4* dst = reinterpret_cast<float4*>(Pc + (long long)trow * SBP + cc);
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-          dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                               __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        for (int q = 0; q < 32; ++q) Pc[(long long)(cc + q) * SBP + trow] = __uint_as_float(r[q]);
       }
     }
     if constexpr (SBP == 256) {
@@ -458,11 +468,8 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         uint32_t r[32];
         tmem_ld32(tbase + 128u + (uint32_t)cc, r);
         if (cc <= grow) {
-          float4* dst = reinterpret_cast<float4*>(Pc + (long long)grow * SBP + cc);
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                 __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+          for (int q = 0; q < 32; ++q) Pc[(long long)(cc + q) * SBP + grow] = __uint_as_float(r[q]);
         }
       }
     }

@@ -41,7 +41,8 @@ __global__ void k_sample(unsigned long long seed, long long h0, long long H, int
 // ---------------------------------------------------------------------------
 // a2+a3 on CUDA cores in FP64: Gram partials of the sampled rows and their
 // projection on v, split over K.  Grid (P, tile pairs): CTA (c, t) computes
-// the 64x64 tile (I, J), I >= J, of sum_{k in split c} Y[i][k] Y[j][k];
+// the 64x64 tile (I, J), I >= J, of sum_{k in split c} Y[i][k] Y[j][k],
+// stored transposed (entry (i, j) at [j][i], like the tensor-core partials);
 // diagonal-tile CTAs also form sum_k Y[i][k] v[k].
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -111,7 +112,7 @@ k_gram_simt(const T* __restrict__ A, long long lda, long long N, long long K,
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      P[(long long)(tI * 64 + ty * 4 + p) * sbp + (tJ * 64 + tx * 4 + q)] = acc[p][q];
+      P[(long long)(tJ * 64 + tx * 4 + q) * sbp + (tI * 64 + ty * 4 + p)] = acc[p][q];
   if (diag && tid < 64) ppart[(long long)c * sbp + tI * 64 + tid] = pacc;
 }
 
@@ -303,9 +304,10 @@ __device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c
     for (int base = c0; base < P; base += U * step) {
       float v[U];
 #pragma unroll
-      for (int i = 0; i < U; ++i) {
+      for (int i = 0; i < U; ++i) {  // unconditional loads (clamped index), then select
         const int c = base + i * step;
-        v[i] = c < P ? __ldcg(src + c * sq) : 0.f;
+        const float x = __ldcg(src + (long long)min(c, P - 1) * sq);
+        v[i] = c < P ? x : 0.f;
       }
 #pragma unroll
       for (int i = 0; i < U; ++i) comp_add(h[i & 3], l[i & 3], v[i]);
@@ -320,7 +322,8 @@ __device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c
 #pragma unroll
       for (int i = 0; i < UD; ++i) {
         const int c = base + i * step;
-        v[i] = c < P ? __ldcg(src + c * sq) : 0.0;
+        const double x = __ldcg(src + (long long)min(c, P - 1) * sq);
+        v[i] = c < P ? x : 0.0;
       }
 #pragma unroll
       for (int w = UD / 2; w >= 1; w /= 2)
@@ -332,7 +335,8 @@ __device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c
   }
 }
 
-// Reduce the split-K partials into R (lower triangle) and p.  Rs (when not
+// Reduce the split-K partials (entry (i, j), i >= j, of partial c at
+// part[c][j][i]) into R (lower triangle) and p.  Rs (when not
 // null) receives the cG-scaled FP32 pairs of the lower-triangle entries,
 // stored transposed (entry (i, j), i >= j, at Rs[j * ldr + i]) so that the
 // chain reads a column block with coalesced loads.  CTAs 0 .. ndiag-1 each
@@ -362,7 +366,7 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
     if (sl < nsl) {
       int i, j;
       tri_decode(e, i, j);
-      flat[tid] = sum_partials(part + (long long)(base + i) * sbp + (base + j), sl, P, nsl, sq);
+      flat[tid] = sum_partials(part + (long long)(base + j) * sbp + (base + i), sl, P, nsl, sq);
     }
     __syncthreads();
     if (tid < E) {
@@ -389,14 +393,19 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
     float2 s2 = make_float2(0.f, 0.f);
     double sp = 0.0;
     if (e < nlow) {
-      tri_decode(e, i, j);
+      // column-major over the lower triangle (consecutive lanes: consecutive
+      // i of one column j), matching the transposed partials [j][i]
+      int ir, jr;
+      tri_decode(e, ir, jr);
+      i = sb - 1 - jr;
+      j = sb - 1 - ir;
       kind = 1;
     } else if (e < nlow + sb) {
       kind = 2;
       i = (int)(e - nlow);
     }
     if (kind == 1) {
-      s2 = sum_partials(part + (long long)i * sbp + j, warp, P, 8, sq);
+      s2 = sum_partials(part + (long long)j * sbp + i, warp, P, 8, sq);
     } else if (kind == 2) {
       const float2 q = sum_partials(ppart + i, warp, P, 8, (long long)sbp);
       sp = (double)q.x + (double)q.y;

@@ -63,7 +63,7 @@ __global__ void k_selftest_wait(unsigned long long limit_ns, unsigned* err);
 __global__ void k_symmetrize(const double* R, int ldr, int sb, double* G);
 
 // tcgen05 Gram (ca_gram_tc.cu): host-side launcher.  Returns a cudaError_t.
-// Computes FP32 partials part[c][i][j] (c < P, row stride sbp) of
+// Computes FP32 partials part[c][j][i] (c < P, stride sbp; stored transposed) of
 // sum_{k in split c} Y[i][k] Y[j][k] for the tiles covering j <= i, and FP64
 // partials ppart[c][i] of sum_k Y[i][k] v[k], v given as FP32 pairs
 // (hi, lo) zero-padded to a multiple of 32 entries.  sbp (the tile height and
