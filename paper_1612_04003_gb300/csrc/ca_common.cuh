@@ -195,12 +195,18 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
   return make_float2(h, e - (h - p));
 }
 
-// 1/d for a positive double-float d: the FP32 reciprocal refined by one
-// Newton step r + r (1 - d r) in double-float arithmetic (~2^-44 relative).
+// 1/d for a positive double-float d: the hardware reciprocal estimate r
+// (rcp.approx, within 1 ulp) refined by one Newton step r + r e with the
+// residual e = 1 - d r formed by a fused multiply-add (|e| <= 2^-22, so the
+// FMA's single rounding leaves it accurate to ~2^-46 of 1) and the low part of
+// d; the result (r, r e) is a normalised double-float, ~2^-44 relative.
 __device__ __forceinline__ float2 df_rcp(float2 d) {
-  const float r = __frcp_rn(d.x);
-  const float2 e = df_add(make_float2(1.f, 0.f), df_neg(df_mul(d, make_float2(r, 0.f))));
-  return df_add(make_float2(r, 0.f), df_mul(make_float2(r, 0.f), e));
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d.x));
+  const float e = fmaf(-d.y, r, fmaf(-d.x, r, 1.0f));
+  const float lo = r * e;
+  const float h = r + lo;
+  return make_float2(h, lo - (h - r));
 }
 
 // (shi, slo) += a * b, with a and b double-float values

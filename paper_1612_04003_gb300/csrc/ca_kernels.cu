@@ -239,8 +239,8 @@ __device__ void block_solve(const double* __restrict__ R, const double* __restri
 // The sweep keeps the matrix symmetric, so pivot k needs only column k.  The
 // CTA's 256 threads own one entry each (thread t: entries t + 256 q of the
 // row-major b x b matrix, values a[q] in double-float); before pivot k the
-// owners of column k publish it to shared memory and the owner of a_kk its
-// reciprocal (two buffers alternate: one barrier per pivot).  Double-float on
+// owners of column k publish it to shared memory (two buffers alternate: one
+// barrier per pivot) and every thread forms 1 / a_kk from it.  Double-float on
 // the FP32 pipe keeps the ~2^-44 accuracy at a fraction of the FP64 latency
 // of this part.  Every thread of the CTA calls this.  Writes Gamma^{-1} (FP32
 // pairs, row-major) to out; a non-positive pivot raises CA_DEV_ERR_NOT_SPD.
@@ -257,24 +257,20 @@ __device__ void cta_sweep_inverse(float2 (&a)[EPT], int b, float2* __restrict__ 
   }
   const bool active = t < b * b;
   for (int k = 0; k < b; ++k) {
-    float2* ck = colbuf + (k & 1) * 33;  // [0, b): column k; [32]: 1 / a_kk
+    float2* ck = colbuf + (k & 1) * 33;  // [0, b): column k
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
       if (ci[q] == k) {
         ck[ri[q]] = a[q];
-        if (ri[q] == k) {
-          float2 d = a[q];
-          if (!(d.x > 0.f)) {
-            ca_flag(err, CA_DEV_ERR_NOT_SPD);
-            d = make_float2(1.f, 0.f);
-          }
-          ck[32] = df_rcp(d);
-        }
+        if (ri[q] == k && !(a[q].x > 0.f)) ca_flag(err, CA_DEV_ERR_NOT_SPD);
       }
     }
     __syncthreads();
     if (active) {
-      const float2 rd = ck[32];
+      // every thread forms 1 / a_kk itself (shorter than a broadcast)
+      float2 d = ck[k];
+      if (!(d.x > 0.f)) d = make_float2(1.f, 0.f);
+      const float2 rd = df_rcp(d);
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
         const int i = ri[q], j = ci[q];
@@ -1302,18 +1298,32 @@ k_pack_panels(const float* __restrict__ A, long long N, long long K, long long l
   }
 }
 
+// Raise the dynamic shared-memory limit of the solve kernels to `bytes`, less
+// each kernel's static shared memory (static + dynamic stays within the
+// per-block maximum of the device).
+template <typename K>
+static cudaError_t set_dyn_smem(K kernel, int bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return e;
+  const int cap = optin - (int)fa.sharedSizeBytes;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes < cap ? bytes : cap);
+}
+
 int set_solve_smem_limit(int bytes) {
-  cudaError_t e[8] = {
-      cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_chain<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_reduce<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes),
-      cudaFuncSetAttribute(k_reduce_chain<float, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           bytes),
-      cudaFuncSetAttribute(k_reduce_chain<float, 16, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           bytes),
-      cudaFuncSetAttribute(k_reduce<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)};
+  cudaError_t e[8] = {set_dyn_smem(k_solve, bytes),
+                      set_dyn_smem(k_chain<8, 4>, bytes),
+                      set_dyn_smem(k_chain<16, 3>, bytes),
+                      set_dyn_smem(k_chain<32, 2>, bytes),
+                      set_dyn_smem(k_reduce<float>, bytes),
+                      set_dyn_smem(k_reduce_chain<float, 8, 4>, bytes),
+                      set_dyn_smem(k_reduce_chain<float, 16, 3>, bytes),
+                      set_dyn_smem(k_reduce<double>, bytes)};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return (int)x;
   return 0;
