@@ -223,13 +223,120 @@ def run_reference(args, rank: int, world: int):
     return 0
 
 
+def _device_time(stream, fn, reps):
+    """Average device time (ms) of fn() over reps calls, CUDA events on stream."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary_workloads(ctx, stream):
+    """The other configurations of the benchmark family, measured briefly:
+    the sparse dual (CSR of X^T, CUDA-core Gram) and the tiny FP64 primal
+    (both latency-bound: reported as block updates/s and us per outer step)."""
+    import numpy as np
+    import torch
+    import synth
+    out = []
+    sp = synth.sparse_dual()  # d = 131072 features, n = 16384 samples, 0.5%, Pareto nnz
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, col, val, ys = dev(sp.rowptr), dev(sp.col), dev(sp.val), dev(sp.y)
+    a = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(sp.d, dtype=torch.float64, device="cuda")
+    h_sp = 2048
+    for s_ in (1, 8, 32):
+        def run():
+            a.zero_()
+            ctx.ca_bdcd_solve((rp, col, val), ys, a, w, b=8, s=s_, H=h_sp, lam=1e-5, seed=42,
+                              d=sp.d, prec="f64")
+        run()
+        t = _device_time(stream, run, 3)
+        out.append({"workload": "sparse dual CA-BDCD, CSR of X^T 16384 x 131072 (0.5%, Pareto "
+                                "nnz per feature), lambda 1e-5, b=8, H=2048, CUDA-core Gram",
+                    "nnz": int(sp.rowptr[-1]), "s": s_, "ms_per_solve": t,
+                    "block_updates_per_s": h_sp / (t * 1e-3),
+                    "us_per_outer_step": t * 1e3 / -(-h_sp // s_)})
+    del rp, col, val
+    tp = synth.tiny_primal()
+    Xt, yt = dev(tp.X), dev(tp.y)
+    wt = torch.zeros(64, dtype=torch.float64, device="cuda")
+    for s_ in (1, 4):
+        def run_t():
+            wt.zero_()
+            ctx.ca_bcd_solve(Xt, yt, wt, b=4, s=s_, H=200, lam=1e-3, seed=42, prec="f64")
+        run_t()
+        t = _device_time(stream, run_t, 5)
+        out.append({"workload": "tiny dense primal CA-BCD, X 64 x 1024 FP64, lambda 1e-3, b=4, "
+                                "H=200, FP64 Gram", "s": s_, "ms_per_solve": t,
+                    "block_updates_per_s": 200 / (t * 1e-3),
+                    "us_per_outer_step": t * 1e3 / -(-200 // s_)})
+    return out
+
+
+def precision_study(args) -> int:
+    """--precision-study: the precision configuration of the benchmark family:
+    X 8192 x 131072 FP32 with geometric row scaling (condition 1e2, 1e4, 1e6),
+    lambda 1e-6, b = s = 16, H = 8192, recompute every 8 outer steps.  Each
+    Gram mode's w_H against the FP64 path on the same data (FP64 X, FP64
+    Gram; the path checked against the FP64 oracle), the relative objective
+    difference, and block updates/s.  One JSON line."""
+    import torch
+    import paper_1612_04003_gb300 as ca
+    import synth
+    ca.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = ca.Context(0, stream=stream.cuda_stream)
+    d, n, lam, b, s_, H = 8192, 131072, 1e-6, 16, 16, 8192
+    rows = []
+    for cond in (1e2, 1e4, 1e6):
+        X, y, _ = synth.dense_primal_torch(d, n, cond=cond, seed=1, device="cuda")
+        kw = dict(b=b, s=s_, H=H, lam=lam, seed=42, recompute_every=8)
+
+        def objective(w):
+            r = X.double().T @ w - y
+            return float(0.5 * lam * w.dot(w) + 0.5 / n * r.dot(r))
+
+        X64 = X.double()
+        w_ref = torch.zeros(d, dtype=torch.float64, device="cuda")
+        t64 = _device_time(stream, lambda: ctx.ca_bcd_solve(X64, y, w_ref.zero_(), prec="f64", **kw), 1)
+        del X64
+        f_ref = objective(w_ref)
+        for prec in ("3xtf32", "tf32"):
+            w = torch.zeros(d, dtype=torch.float64, device="cuda")
+            ctx.ca_bcd_solve(X, y, w, prec=prec, **kw)
+            t = _device_time(stream, lambda: ctx.ca_bcd_solve(X, y, w.zero_(), prec=prec, **kw), 2)
+            rel_w = float((w - w_ref).norm() / w_ref.norm())
+            f = objective(w)
+            rows.append({"cond": cond, "gram": prec, "rel_err_w_vs_fp64": rel_w,
+                         "rel_objective_diff": abs(f - f_ref) / abs(f_ref),
+                         "block_updates_per_s": H / (t * 1e-3)})
+        rows.append({"cond": cond, "gram": "f64 (FP64 X, reference)", "rel_err_w_vs_fp64": 0.0,
+                     "rel_objective_diff": 0.0, "block_updates_per_s": H / (t64 * 1e-3)})
+        del X, y
+    print(json.dumps({"study": "precision", "workload": "dense primal CA-BCD, X 8192 x 131072 FP32, "
+                      "lambda 1e-6, b=16, s=16, H=8192, recompute every 8 outer steps",
+                      "rows": rows}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the s sweep and the other workloads")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="run the precision study (8192 x 131072, cond 1e2..1e6) instead")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--s", type=int, default=None, help="unrolling depth (default %d)" % S)
     ap.add_argument("--n", type=int, default=None,
@@ -243,6 +350,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.precision_study:
+        return precision_study(args)
     s_run = args.s or S
     n_run = args.n or N_SAMPLES
     h_run = args.h or H
@@ -358,6 +467,22 @@ def main():
                 sweep.append({"gram": prec_, "b": b_, "s": s_, "ms_per_step": t,
                               "block_updates_per_s": h_run / (t * 1e-3)})
 
+    # the same roofline for the plain TF32 Gram pass (no split), same K solves
+    roof_tf32 = None
+    secondary = []
+    if not args.no_sweep:
+        time_solves(ctx, XP, y, w, z, 1, stream, s=s_run, h=h_run, prec="tf32", panels=pan)
+        ctx.ca_profile_enable(True)
+        time_solves(ctx, XP, y, w, z, args.steps, stream, s=s_run, h=h_run, prec="tf32", panels=pan)
+        p32 = ctx.ca_profile_read()
+        ctx.ca_profile_enable(False)
+        g32 = p32["gram_ms"] / max(1, p32["gram_launches"])
+        ach32 = alg_bytes / (g32 * 1e-3) / 1e9
+        roof_tf32 = {"bound": "hbm", "achieved": ach32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach32 / peaks["hbm_gbs"], "avg_launch_ms": g32,
+                     "kernel": "k_gram_tc<128,tf32,fused update>"}
+        secondary = secondary_workloads(ctx, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(X.cpu().numpy(), y.cpu().numpy())
@@ -372,6 +497,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(), "sweep": sweep,
+            "roofline_tf32_gram": roof_tf32, "other_workloads": secondary,
             "input_layout": "X resident on the device in the library's 32-column panel layout "
                             "(ca_pack_panels once before the timed region, CA_DENSE_F32_PANELS)",
             "value_rowmajor_input": {"value": world * h_run / (ms_step_rm * 1e-3),
