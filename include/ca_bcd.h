@@ -118,7 +118,9 @@ int ca_bcd_init(ca_ctx** ctx, int device, void* cuda_stream, size_t scratch_byte
  *         elements.  For the tcgen05 Gram modes, X and ld*4 bytes must be
  *         16-byte aligned; the solve then first repacks X into 32-column
  *         panels in its scratch (one pass over X; ca_pack_panels layout) and
- *         reads only the panels.  CA_DENSE_F32_PANELS: X is already in that
+ *         reads only the panels.  Host X: pageable memory is copied to the
+ *         device first; page-locked (pinned) memory is read in place by the
+ *         repack.  CA_DENSE_F32_PANELS: X is already in that
  *         layout (ceil(n/32) * d * 32 floats; ld is ignored); TF32 / 3xTF32
  *         only.
  *   y     n labels (FP64).

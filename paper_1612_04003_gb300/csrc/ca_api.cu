@@ -94,6 +94,18 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Device-accessible address of page-locked, mapped host memory (the same
+// address under unified addressing), or nullptr for any other pointer.
+const void* mapped_host_ptr(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int ensure_arena(ca_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->arena_bytes) return CA_OK;
   if (ctx->scratch_max && bytes > ctx->scratch_max) return CA_ERR_OOM;
@@ -553,7 +565,10 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
                 align256((size_t)(n + 31) / 32 * 32 * 8) /* rho split */ +
                 align256((size_t)d * 8) /* w split */ +
                 align256((size_t)o->H * o->b * 4) /* idx */;
-  if (x_host) need += align256(xbytes) + 256;
+  // FP32 X in pinned host memory: the panel repack reads it in place (one
+  // pass over the host link instead of a copy followed by a repack)
+  const void* x_mapped = (x_host && tc && !pre) ? mapped_host_ptr(X) : nullptr;
+  if (x_host && !x_mapped) need += align256(xbytes) + 256;
   if (tc && !pre) need += align256(panel_bytes(d, n)) + 256;
   if (y_host) need += align256((size_t)n * 8);
   if (w_host) need += align256((size_t)d * 8);
@@ -563,7 +578,9 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   Carve cv{static_cast<char*>(ctx->arena)};
   bool st;
   const void* Xd = X;
-  if (x_host) {
+  if (x_mapped) {
+    Xd = x_mapped;
+  } else if (x_host) {
     void* p = cv.take<char>(xbytes);
     CA_TRY_CUDA(cudaMemcpyAsync(p, X, xbytes, cudaMemcpyHostToDevice, ctx->stream));
     Xd = p;
@@ -734,13 +751,16 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   const size_t xbytes = pre ? panel_bytes(n, d) : (size_t)(n - 1) * ld * el + (size_t)d * el;
   need += dense_work_bytes(ctx, o, d, xf) + align256((size_t)(d + 31) / 32 * 32 * 8) +
           align256((size_t)n * 8);
-  if (x_host) need += align256(xbytes) + 256;
+  const void* x_mapped = (x_host && tc && !pre) ? mapped_host_ptr(XT) : nullptr;
+  if (x_host && !x_mapped) need += align256(xbytes) + 256;
   if (tc && !pre) need += align256(panel_bytes(n, d)) + 256;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
   bool st;
   const void* Xd = XT;
-  if (x_host) {
+  if (x_mapped) {
+    Xd = x_mapped;
+  } else if (x_host) {
     void* p = cv.take<char>(xbytes);
     CA_TRY_CUDA(cudaMemcpyAsync(p, XT, xbytes, cudaMemcpyHostToDevice, ctx->stream));
     Xd = p;

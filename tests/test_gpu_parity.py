@@ -244,6 +244,30 @@ def test_primal_host_buffers_match_device(ctx, mid32):
     assert _rel(wh, w_ref) < TOL32 and _rel(zh, z_ref) < TOL32
 
 
+def test_pinned_host_x_is_read_in_place(ctx, mid32):
+    """Page-locked host X is repacked straight from host memory (no staging
+    copy): the iterates equal those of the device-resident X, primal and dual."""
+    d, n = 512, 8192
+    Xh = torch.from_numpy(np.ascontiguousarray(mid32.X[:, :n])).pin_memory()
+    y = _dev(np.ascontiguousarray(mid32.y[:n]))
+    kw = dict(b=8, s=8, H=128, lam=1e-4, seed=5, prec="3xtf32")
+    w_host = torch.zeros(d, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(Xh, y, w_host, **kw)
+    w_dev = torch.zeros(d, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(Xh.cuda(), y, w_dev, **kw)
+    assert _rel(w_host, w_dev.cpu().numpy()) < 1e-12
+    XTh = torch.from_numpy(np.ascontiguousarray(mid32.X[:64, :1024].T)).pin_memory()  # 1024 x 64
+    ys = _dev(np.ascontiguousarray(mid32.y[:1024]))
+    kw2 = dict(b=8, s=4, H=64, lam=1e-2, seed=2, prec="3xtf32")
+    a1 = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    w1 = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(XTh, ys, a1, w1, **kw2)
+    a2 = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    w2 = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(XTh.cuda(), ys, a2, w2, **kw2)
+    assert _rel(a1, a2.cpu().numpy()) < 1e-12 and _rel(w1, w2.cpu().numpy()) < 1e-12
+
+
 # ---------------------------------------------------------------------------
 # Dual CA-BDCD
 # ---------------------------------------------------------------------------
