@@ -38,7 +38,13 @@ sys.path.insert(0, ROOT)
 METRIC = "CA-BCD block-updates/s"
 UNIT = "block-updates/s"
 D, N_SAMPLES, COND, LAM, B, S, H = 4096, 262144, 1e3, 1e-4, 8, 16, 4096
-PREC = "3xtf32"
+# Gram mode of the headline: x = b0 + b1 in BF16, three products, FP32
+# accumulate (meets the FP32 path's 1e-5 iterate tolerance; the fastest mode
+# that does)
+PREC = "bf16x3"
+DTYPE = {"bf16x3": "bf16x3 (bf16 split products, fp32 accumulate; fp64 solves)",
+         "3xtf32": "3xtf32 (fp32-faithful split products; fp64 solves)",
+         "tf32": "tf32 (fp32 accumulate; fp64 solves)"}
 
 
 def workload_config(d=D, n=N_SAMPLES, b=B, s=S, h=H, prec=PREC):
@@ -309,7 +315,7 @@ def precision_study(args) -> int:
         t64 = _device_time(stream, lambda: ctx.ca_bcd_solve(X64, y, w_ref.zero_(), prec="f64", **kw), 1)
         del X64
         f_ref = objective(w_ref)
-        for prec in ("3xtf32", "tf32"):
+        for prec in ("3xtf32", "bf16x3", "tf32"):
             w = torch.zeros(d, dtype=torch.float64, device="cuda")
             ctx.ca_bcd_solve(X, y, w, prec=prec, **kw)
             t = _device_time(stream, lambda: ctx.ca_bcd_solve(X, y, w.zero_(), prec=prec, **kw), 2)
@@ -411,7 +417,7 @@ def main():
     sb = s_run * B
     gram_ms = prof["gram_ms"] / max(1, prof["gram_launches"])
     n_outer = -(-h_run // s_run)
-    fused = sb <= 128 and PREC in ("tf32", "3xtf32")  # a5 of step k rides in the a2+a3 launch of k+1
+    fused = sb <= 128 and PREC in ("tf32", "3xtf32", "bf16x3")  # a5 of step k rides in the a2+a3 launch of k+1
     b_gram = sb * n_run * 4 + n_run * 8          # B_G: Y rows + the projection vector
     b_upd = sb * n_run * 4 + 2 * n_run * 8       # B_U: Y rows + read/write of v
     breakdown = {c: {"ms_per_step": prof[f"{c}_ms"] / args.steps,
@@ -458,7 +464,7 @@ def main():
     # s sweep (same data, fewer steps): s-step against s = 1
     sweep = []
     if not args.no_sweep:
-        for prec_ in ("3xtf32", "tf32"):
+        for prec_ in ("3xtf32", "bf16x3", "tf32"):
             for (b_, s_) in [(8, 1), (8, 4), (8, 8), (8, 16), (8, 32), (32, 1), (32, 4), (32, 8)]:
                 nst = 2 if s_ == 1 else 4
                 time_solves(ctx, XP, y, w, z, 1, stream, b=b_, s=s_, h=h_run, prec=prec_, panels=pan)
@@ -467,20 +473,23 @@ def main():
                 sweep.append({"gram": prec_, "b": b_, "s": s_, "ms_per_step": t,
                               "block_updates_per_s": h_run / (t * 1e-3)})
 
-    # the same roofline for the plain TF32 Gram pass (no split), same K solves
-    roof_tf32 = None
+    # the same roofline for the other Gram modes, same K solves
+    roof_other = {}
     secondary = []
     if not args.no_sweep:
-        time_solves(ctx, XP, y, w, z, 1, stream, s=s_run, h=h_run, prec="tf32", panels=pan)
-        ctx.ca_profile_enable(True)
-        time_solves(ctx, XP, y, w, z, args.steps, stream, s=s_run, h=h_run, prec="tf32", panels=pan)
-        p32 = ctx.ca_profile_read()
-        ctx.ca_profile_enable(False)
-        g32 = p32["gram_ms"] / max(1, p32["gram_launches"])
-        ach32 = alg_bytes / (g32 * 1e-3) / 1e9
-        roof_tf32 = {"bound": "hbm", "achieved": ach32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": ach32 / peaks["hbm_gbs"], "avg_launch_ms": g32,
-                     "kernel": "k_gram_tc<128,tf32,fused update>"}
+        for prec_ in [p for p in ("3xtf32", "bf16x3", "tf32") if p != PREC]:
+            time_solves(ctx, XP, y, w, z, 1, stream, s=s_run, h=h_run, prec=prec_, panels=pan)
+            ctx.ca_profile_enable(True)
+            time_solves(ctx, XP, y, w, z, args.steps, stream, s=s_run, h=h_run, prec=prec_,
+                        panels=pan)
+            p32 = ctx.ca_profile_read()
+            ctx.ca_profile_enable(False)
+            g32 = p32["gram_ms"] / max(1, p32["gram_launches"])
+            ach32 = alg_bytes / (g32 * 1e-3) / 1e9
+            roof_other[prec_] = {"bound": "hbm", "achieved": ach32, "peak": peaks["hbm_gbs"],
+                                 "unit": "GB/s", "frac": ach32 / peaks["hbm_gbs"],
+                                 "avg_launch_ms": g32,
+                                 "kernel": f"k_gram_tc<128,{prec_},fused update>"}
         secondary = secondary_workloads(ctx, stream)
 
     cpu = None
@@ -492,12 +501,13 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "3xtf32 (fp32-faithful)", "data": "synthetic",
+            "dtype": DTYPE[PREC], "data": "synthetic",
             "config": workload_config(n=n_run, s=s_run, h=h_run),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(), "sweep": sweep,
-            "roofline_tf32_gram": roof_tf32, "other_workloads": secondary,
+            **{f"roofline_{p}_gram": r for p, r in roof_other.items()},
+            "other_workloads": secondary,
             "input_layout": "X resident on the device in the library's 32-column panel layout "
                             "(ca_pack_panels once before the timed region, CA_DENSE_F32_PANELS)",
             "value_rowmajor_input": {"value": world * h_run / (ms_step_rm * 1e-3),

@@ -218,6 +218,11 @@ int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const do
   return cuda_status(cudaGetLastError());
 }
 
+// Gram precisions that run on the tcgen05 path (FP32 X only).
+bool tc_prec(int prec) {
+  return prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT || prec == CA_GRAM_BF16X3;
+}
+
 // Split-K plan of the a2+a3 pass for a given s*b bound.
 struct GramPlan {
   bool tc;
@@ -227,8 +232,8 @@ struct GramPlan {
 
 GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
   GramPlan g{};
-  g.tc = (xfmt == CA_DENSE_F32) && (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT);
-  g.three = (prec == CA_GRAM_FP32_EXACT) ? 1 : 0;
+  g.tc = (xfmt == CA_DENSE_F32) && tc_prec(prec);
+  g.three = (prec == CA_GRAM_FP32_EXACT) ? 1 : (prec == CA_GRAM_BF16X3 ? 2 : 0);
   if (g.tc) {
     g.sbp = sbm <= 32 ? 32 : (sbm <= 64 ? 64 : (sbm <= 128 ? 128 : 256));
     g.P = (int)std::min<long long>(ctx->num_sms, (K + 31) / 32);
@@ -412,7 +417,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
 
 size_t dense_work_bytes(ca_ctx* ctx, const ca_opts* o, long long K, int xfmt) {
   const int sbm = (int)(std::min<long long>(o->s, o->H) * o->b);
-  const bool tc = (xfmt == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
+  const bool tc = (xfmt == CA_DENSE_F32) && tc_prec(o->prec);
   size_t sbp, P, el;
   if (tc) {
     sbp = sbm <= 128 ? 128 : 256;
@@ -549,8 +554,8 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32 && !pre) return CA_ERR_ARG;
   CA_TRY(check_opts(o, d));
   const int xf = pre ? (int)CA_DENSE_F32 : xfmt;  // element type of X
-  const bool tc = (xf == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
-  if (o->prec == CA_GRAM_BF16X3 || o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
+  const bool tc = (xf == CA_DENSE_F32) && tc_prec(o->prec);
+  if (o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
   if (pre && !tc) return CA_ERR_ARG;
   if (tc) {
     if ((!pre && (ld & 3) != 0) || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return CA_ERR_ARG;
@@ -739,8 +744,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   const bool pre = xfmt == CA_DENSE_F32_PANELS;
   if (!pre && ld < d) return CA_ERR_ARG;
   const int xf = pre ? (int)CA_DENSE_F32 : xfmt;
-  const bool tc = (xf == CA_DENSE_F32) && (o->prec == CA_GRAM_TF32 || o->prec == CA_GRAM_FP32_EXACT);
-  if (o->prec == CA_GRAM_BF16X3 || o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
+  const bool tc = (xf == CA_DENSE_F32) && tc_prec(o->prec);
+  if (o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
   if (pre && !tc) return CA_ERR_ARG;
   if (tc) {
     if ((!pre && (ld & 3) != 0) || (reinterpret_cast<uintptr_t>(XT) & 15) != 0) return CA_ERR_ARG;
@@ -852,8 +857,8 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
       sb > kMaxSB)
     return CA_ERR_ARG;
   if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32) return CA_ERR_ARG;
-  if (prec < CA_GRAM_F64 || prec > CA_GRAM_TF32) return CA_ERR_ARG;
-  const bool tc = (xfmt == CA_DENSE_F32) && (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT);
+  if (prec < CA_GRAM_F64 || prec > CA_GRAM_BF16X3) return CA_ERR_ARG;
+  const bool tc = (xfmt == CA_DENSE_F32) && tc_prec(prec);
   if (tc) {
     if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return CA_ERR_ARG;
     if (sb > gram_tc_max_sb()) return CA_ERR_UNSUPPORTED;

@@ -43,9 +43,13 @@ constexpr int kLoaderThreads = 32 * kLoaderWarps;    // loaders / projection / e
 constexpr int kMmaWarp = kLoaderWarps;               // TMEM allocation and MMA issue
 constexpr int kThreads = kLoaderThreads + 32;
 
-template <int SBP, bool THREE, bool UPD = false>
+template <int SBP, bool THREE, bool UPD = false, bool BF = false>
 struct TcCfg {
   static constexpr int kTileBytes = SBP * 128;                  // SBP rows x 32 fp32
+  // operand tiles of the split modes: 3xTF32 rows of 32 fp32 (128-byte
+  // swizzle), BF16x3 rows of 32 bf16 (64 bytes, 64-byte swizzle)
+  static constexpr int kOpRow = BF ? 64 : 128;
+  static constexpr int kOpTile = SBP * kOpRow;
   // cp.async slot: [current rows | previous step's rows (fused update)]
   static constexpr int kRawBytes = kTileBytes * (UPD ? 2 : 1);
   static constexpr int kPrevOff = kTileBytes;
@@ -53,7 +57,7 @@ struct TcCfg {
   // kMS slots that the MMA reads, so a load slot is free again as soon as its
   // own thread has consumed it (no wait on the MMA before a refill).  Plain
   // TF32: the MMA reads the load slot itself.
-  static constexpr int kMmaSlotBytes = THREE ? 2 * kTileBytes : 0;
+  static constexpr int kMmaSlotBytes = THREE ? 2 * kOpTile : 0;
   static constexpr int kBudget = 200 * 1024;                    // both rings
   static constexpr int kMS =
       THREE ? ((kBudget - 2 * kMmaSlotBytes) / kRawBytes >= 4 ? 2 : 1) : 0;
@@ -90,6 +94,36 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   // 46-48, swizzle mode 2 = 128-byte swizzle (bits 61-63).
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1u << 16) |
          ((uint64_t)(1024u >> 4) << 32) | ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+
+__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
+  // the same for 64-byte rows: 8-row atoms of 512 bytes, swizzle mode 4 =
+  // 64-byte swizzle (16-byte chunk c of row r stored at c ^ ((r / 2) % 4))
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1u << 16) |
+         ((uint64_t)(512u >> 4) << 32) | ((uint64_t)1u << 46) | ((uint64_t)4u << 61);
+}
+
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16
+  // (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// (lo, hi) rounded to BF16 (nearest even), packed: lo in bits 0-15.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
 __device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
@@ -142,13 +176,13 @@ __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-template <int SBP, bool THREE, bool UPD, bool PANEL>
+template <int SBP, bool THREE, bool UPD, bool PANEL, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
           const int* __restrict__ idx, int sb, const float2* __restrict__ v2, long long natoms,
           float* __restrict__ part, double* __restrict__ ppart, unsigned* __restrict__ err,
           GramUpdate u) {
-  using C = TcCfg<SBP, THREE, UPD>;
+  using C = TcCfg<SBP, THREE, UPD, BF>;
   constexpr int NS = C::kNS, MS = C::kMS, RPT = C::kRPT;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -383,10 +417,26 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           const float4 x = xs[i];
-          const float4 h = make_float4(tf32_head(x.x), tf32_head(x.y), tf32_head(x.z), tf32_head(x.w));
-          *reinterpret_cast<float4*>(hi + dsto[i]) = h;
-          *reinterpret_cast<float4*>(hi + C::kTileBytes + dsto[i]) =
-              make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          if constexpr (BF) {
+            // x = b0 + b1 (+ a remainder below 2^-16 |x|): bf16 head and tail,
+            // 4 columns = 8 bytes, half of a 16-byte chunk of the 64-byte row
+            const int r = g + 32 * i;
+            const uint32_t off = (uint32_t)((r >> 3) * 512 + (r & 7) * 64 +
+                                            ((((l >> 1) ^ ((r >> 1) & 3))) << 4) + (l & 1) * 8);
+            const uint32_t h01 = bf16x2_rn(x.x, x.y), h23 = bf16x2_rn(x.z, x.w);
+            // the tails x - b0 are exact in FP32
+            const uint32_t l01 = bf16x2_rn(x.x - __uint_as_float(h01 << 16),
+                                           x.y - __uint_as_float(h01 & 0xFFFF0000u));
+            const uint32_t l23 = bf16x2_rn(x.z - __uint_as_float(h23 << 16),
+                                           x.w - __uint_as_float(h23 & 0xFFFF0000u));
+            *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
+            *reinterpret_cast<uint2*>(hi + C::kOpTile + off) = make_uint2(l01, l23);
+          } else {
+            const float4 h = make_float4(tf32_head(x.x), tf32_head(x.y), tf32_head(x.z), tf32_head(x.w));
+            *reinterpret_cast<float4*>(hi + dsto[i]) = h;
+            *reinterpret_cast<float4*>(hi + C::kOpTile + dsto[i]) =
+                make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          }
         }
         fence_proxy_async_smem();  // this thread's tiles, visible to the tensor core
         __syncwarp();
@@ -475,8 +525,16 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
     }
   } else if (lane == 0) {
     // ---------------- MMA issue (one thread) ----------------
-    const uint32_t id1 = idesc_tf32(128, n1);
-    const uint32_t id2 = idesc_tf32(128, n2);
+    const uint32_t id1 = BF ? idesc_bf16(128, n1) : idesc_tf32(128, n1);
+    const uint32_t id2 = BF ? idesc_bf16(128, n2) : idesc_tf32(128, n2);
+    // one K step: 8 tf32 or 16 bf16 = 32 bytes of a row
+    auto desc = [](uint32_t a) { return BF ? sw64_kmajor_desc(a) : sw128_kmajor_desc(a); };
+    auto mma = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+      if constexpr (BF) mma_bf16(d, a, b, id, acc);
+      else mma_tf32(d, a, b, id, acc);
+    };
+    constexpr int KSTEPS = BF ? 2 : 4;
+    constexpr uint32_t kHalf = 128u * C::kOpRow;  // rows 128.. of a 256-row tile
     for (int t = 0; t < T; ++t) {
       int st, lap;
       if constexpr (THREE) {
@@ -490,28 +548,28 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       tc_fence_after();
       const uint32_t hb = THREE ? smem_u32(mring) + (uint32_t)(st * C::kMmaSlotBytes)
                                 : smem_u32(raw) + (uint32_t)(st * C::kRawBytes);
-      const uint32_t lb = hb + (uint32_t)C::kTileBytes;
+      const uint32_t lb = hb + (uint32_t)C::kOpTile;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
+      for (int kk = 0; kk < KSTEPS; ++kk) {
         const uint32_t acc = (t > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t h0 = sw128_kmajor_desc(hb + kk * 32);
-        mma_tf32(tmem, h0, h0, id1, acc);
+        const uint64_t h0 = desc(hb + kk * 32);
+        mma(tmem, h0, h0, id1, acc);
         if constexpr (C::kSym) {
-          const uint64_t l0 = sw128_kmajor_desc(lb + kk * 32);
-          mma_tf32(tmem + 128u, h0, l0, id1, acc);  // T = hi lo^T
+          const uint64_t l0 = desc(lb + kk * 32);
+          mma(tmem + 128u, h0, l0, id1, acc);  // T = hi lo^T
         } else if constexpr (THREE) {
-          const uint64_t l0 = sw128_kmajor_desc(lb + kk * 32);
-          mma_tf32(tmem, h0, l0, id1, 1u);
-          mma_tf32(tmem, l0, h0, id1, 1u);
+          const uint64_t l0 = desc(lb + kk * 32);
+          mma(tmem, h0, l0, id1, 1u);
+          mma(tmem, l0, h0, id1, 1u);
         }
         if constexpr (SBP == 256) {
-          const uint64_t h1 = sw128_kmajor_desc(hb + 16384 + kk * 32);
-          mma_tf32(tmem + 128u, h1, h0, id2, acc);
+          const uint64_t h1 = desc(hb + (THREE ? kHalf : 16384u) + kk * 32);
+          mma(tmem + 128u, h1, h0, id2, acc);
           if constexpr (THREE) {
-            const uint64_t l0 = sw128_kmajor_desc(lb + kk * 32);
-            const uint64_t l1 = sw128_kmajor_desc(lb + 16384 + kk * 32);
-            mma_tf32(tmem + 128u, h1, l0, id2, 1u);
-            mma_tf32(tmem + 128u, l1, h0, id2, 1u);
+            const uint64_t l0 = desc(lb + kk * 32);
+            const uint64_t l1 = desc(lb + kHalf + kk * 32);
+            mma(tmem + 128u, h1, l0, id2, 1u);
+            mma(tmem + 128u, l1, h0, id2, 1u);
           }
         }
       }
@@ -531,14 +589,14 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
   }
 }
 
-template <int SBP, bool THREE, bool UPD, bool PANEL>
+template <int SBP, bool THREE, bool UPD, bool PANEL, bool BF>
 int launch_one(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
                const float2* v2, int P, float* part, double* ppart, unsigned* err,
                const GramUpdate& u, cudaStream_t stream) {
-  using C = TcCfg<SBP, THREE, UPD>;
+  using C = TcCfg<SBP, THREE, UPD, BF>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD, PANEL>,
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD, PANEL, BF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return (int)e;
     configured = true;
@@ -556,7 +614,7 @@ int launch_one(const float* A, long long lda, long long N, long long K, const in
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gram_tc<SBP, THREE, UPD, PANEL>, A, lda, N, K, idx,
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gram_tc<SBP, THREE, UPD, PANEL, BF>, A, lda, N, K, idx,
                                            sb, v2, natoms, part, ppart, err, u);
   if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
@@ -570,12 +628,18 @@ int launch_gram_tc(const float* A, long long lda, long long N, long long K, cons
                    const float2* v2, int P, int sbp, float* part, double* ppart, unsigned* err,
                    int three_pass, cudaStream_t stream, const GramUpdate* upd, bool panel) {
   const GramUpdate none{};
-  const bool T3 = three_pass != 0;
-#define CA_TC_CASE(S, U, PN, UU)                                                             \
-  if (sbp == S) return T3 ? launch_one<S, true, U, PN>(A, lda, N, K, idx, sb, v2, P, part, ppart, \
-                                                       err, UU, stream)                         \
-                          : launch_one<S, false, U, PN>(A, lda, N, K, idx, sb, v2, P, part,     \
-                                                        ppart, err, UU, stream);
+  // three_pass: 0 = TF32, 1 = 3xTF32, 2 = BF16x3
+#define CA_TC_CASE(S, U, PN, UU)                                                              \
+  if (sbp == S) {                                                                            \
+    if (three_pass == 0)                                                                     \
+      return launch_one<S, false, U, PN, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err, \
+                                                UU, stream);                                 \
+    if (three_pass == 1)                                                                     \
+      return launch_one<S, true, U, PN, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err,  \
+                                               UU, stream);                                  \
+    return launch_one<S, true, U, PN, true>(A, lda, N, K, idx, sb, v2, P, part, ppart, err,     \
+                                            UU, stream);                                     \
+  }
   if (upd && upd->sb > 0) {  // fused deferred update: panels, s*b <= 128 only
     if (!panel || sbp > 128 || upd->sb > sbp) return (int)cudaErrorInvalidValue;
     CA_TC_CASE(32, true, true, *upd)

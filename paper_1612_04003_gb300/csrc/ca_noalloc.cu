@@ -86,8 +86,9 @@ extern "C" int ca_gram_project_noalloc(void* cuda_stream, int xfmt, int prec, co
   if (!A || !idx || !v || !G || !p || N < 1 || K < 1 || ld < K || sb < 1) return CA_ERR_ARG;
   if (sb > kMaxSb || K > kMaxK) return CA_ERR_UNSUPPORTED;  // beyond the fixed scratch
   if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32) return CA_ERR_ARG;
-  if (prec < CA_GRAM_F64 || prec > CA_GRAM_TF32) return CA_ERR_ARG;
-  const bool tc = (xfmt == CA_DENSE_F32) && (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT);
+  if (prec < CA_GRAM_F64 || prec > CA_GRAM_BF16X3) return CA_ERR_ARG;
+  const bool tc = (xfmt == CA_DENSE_F32) &&
+                  (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT || prec == CA_GRAM_BF16X3);
   if (tc && ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0)) return CA_ERR_ARG;
   for (const void* q : {A, (const void*)idx, (const void*)v, (const void*)G, (const void*)p})
     if (!on_device(q)) return CA_ERR_ARG;
@@ -112,7 +113,7 @@ extern "C" int ca_gram_project_noalloc(void* cuda_stream, int xfmt, int prec, co
     const long long Kp = natoms * 32;
     k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, stream>>>(v, K, Kp, v2);
     if (launch_gram_tc(static_cast<const float*>(A), ld, N, K, idx, sb, v2, P, sbp,
-                       static_cast<float*>(part), ppart, err, prec == CA_GRAM_FP32_EXACT ? 1 : 0,
+                       static_cast<float*>(part), ppart, err, prec == CA_GRAM_FP32_EXACT ? 1 : (prec == CA_GRAM_BF16X3 ? 2 : 0),
                        stream) != 0)
       return CA_ERR_CUDA;
   } else {
