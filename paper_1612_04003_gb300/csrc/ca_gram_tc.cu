@@ -339,7 +339,6 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[st]);
       }
-      float vh[4], vl[4];
       if constexpr (UPD) {
         // deferred update of the previous outer step on this stage's 32
         // columns, v_new = v_old - cU * sum_r Yprev[r][k] Delta_r, in
@@ -362,55 +361,25 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
           up[e] += __shfl_xor_sync(0xffffffffu, up[e], 8);
           up[e] += __shfl_xor_sync(0xffffffffu, up[e], 16);
         }
+        // buffer t & 1 is rewritten at stage t + 2, after the barrier of
+        // stage t + 1, which every warp reaches after its reads of stage t
         float* ub = ured + (t & 1) * (kLoaderWarps * 32);
         if (lane < 8)
           *reinterpret_cast<float4*>(ub + warp * 32 + 4 * l) = make_float4(up[0], up[1], up[2], up[3]);
-        // every loader's sums and copies (incl. the v slice) are in place
-        asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
-        float sum = 0.f;  // lane = column
-#pragma unroll
-        for (int w2 = 0; w2 < kLoaderWarps; ++w2) sum += ub[32 * w2 + lane];
-        const float2 vo = reinterpret_cast<const float2*>(vring + (t % (2 * NS)) * 256)[lane];
-        const float2 vn = df_add(vo, df_neg(df_mul(u_cU2, make_float2(sum, 0.f))));
-        const long long kk = (a_begin + t) * 32 + lane;
-        if (warp == 0 && kk < K) u.v2[kk] = vn;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          vh[e] = __shfl_sync(0xffffffffu, vn.x, 4 * l + e);
-          vl[e] = __shfl_sync(0xffffffffu, vn.y, 4 * l + e);
-        }
-      } else {
-        // every loader's copies of this stage (incl. the v slice) have landed
-        asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
-        // projection vector slice as loaded (exact FP32 pairs)
-        const float4* vs = reinterpret_cast<const float4*>(vring + (t % (2 * NS)) * 256 + l * 32);
-        const float4 va = vs[0], vb = vs[1];
-        vh[0] = va.x; vh[1] = va.z; vh[2] = vb.x; vh[3] = vb.z;
-        vl[0] = va.y; vl[1] = va.w; vl[2] = vb.y; vl[3] = vb.w;
       }
-      // projection on this thread's own chunks (exact FP32 inputs)
+      // this thread's chunks of the current rows (split products: read here
+      // for the conversion; plain TF32: read after the barrier)
       float4 xs[RPT];
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const float4 x = *reinterpret_cast<const float4*>(big + dsto[i]);
-        xs[i] = x;
-        float a = pacc[i];
-        a = fmaf(x.x, vh[0], fmaf(x.x, vl[0], a));
-        a = fmaf(x.y, vh[1], fmaf(x.y, vl[1], a));
-        a = fmaf(x.z, vh[2], fmaf(x.z, vl[2], a));
-        a = fmaf(x.w, vh[3], fmaf(x.w, vl[3], a));
-        pacc[i] = a;
-      }
-      if ((t & 7) == 7) {
-#pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-          comp_add(phi[i], plo[i], pacc[i]);
-          pacc[i] = 0.f;
-        }
-      }
       if constexpr (THREE) {
-        // head / tail tiles into MMA slot t % MS once the MMA of stage t - MS
-        // has read it; then hand the slot to the MMA
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) xs[i] = *reinterpret_cast<const float4*>(big + dsto[i]);
+      }
+      // split products: head / tail tiles into MMA slot t % MS once the MMA
+      // of stage t - MS has read it; then hand the slot to the MMA.  With two
+      // or more MMA slots this runs before the loaders' barrier (the MMA
+      // starts while the loaders finish the stage); with one slot it waits
+      // for the MMA of the previous stage, so it runs after the projection.
+      auto handoff = [&]() {
         const int ms = t % MS;
         if (t >= MS) ok = warp_wait(&empty[ms], (uint32_t)((t / MS - 1) & 1), ok);
         unsigned char* hi = mring + ms * C::kMmaSlotBytes;
@@ -441,6 +410,54 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         fence_proxy_async_smem();  // this thread's tiles, visible to the tensor core
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[ms]);
+      };
+      if constexpr (THREE && MS >= 2) handoff();
+      // every loader's copies of this stage (incl. the v slice) have landed
+      // and (fused update) every warp's column sums are in place
+      asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
+      float vh[4], vl[4];
+      if constexpr (UPD) {
+        const float* ub = ured + (t & 1) * (kLoaderWarps * 32);
+        float sum = 0.f;  // lane = column
+#pragma unroll
+        for (int w2 = 0; w2 < kLoaderWarps; ++w2) sum += ub[32 * w2 + lane];
+        const float2 vo = reinterpret_cast<const float2*>(vring + (t % (2 * NS)) * 256)[lane];
+        const float2 vn = df_add(vo, df_neg(df_mul(u_cU2, make_float2(sum, 0.f))));
+        const long long kk = (a_begin + t) * 32 + lane;
+        if (warp == 0 && kk < K) u.v2[kk] = vn;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          vh[e] = __shfl_sync(0xffffffffu, vn.x, 4 * l + e);
+          vl[e] = __shfl_sync(0xffffffffu, vn.y, 4 * l + e);
+        }
+      } else {
+        // projection vector slice as loaded (exact FP32 pairs)
+        const float4* vs = reinterpret_cast<const float4*>(vring + (t % (2 * NS)) * 256 + l * 32);
+        const float4 va = vs[0], vb = vs[1];
+        vh[0] = va.x; vh[1] = va.z; vh[2] = vb.x; vh[3] = vb.z;
+        vl[0] = va.y; vl[1] = va.w; vl[2] = vb.y; vl[3] = vb.w;
+      }
+      // projection on this thread's own chunks (exact FP32 inputs)
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        if constexpr (!THREE) xs[i] = *reinterpret_cast<const float4*>(big + dsto[i]);
+        const float4 x = xs[i];
+        float a = pacc[i];
+        a = fmaf(x.x, vh[0], fmaf(x.x, vl[0], a));
+        a = fmaf(x.y, vh[1], fmaf(x.y, vl[1], a));
+        a = fmaf(x.z, vh[2], fmaf(x.z, vl[2], a));
+        a = fmaf(x.w, vh[3], fmaf(x.w, vl[3], a));
+        pacc[i] = a;
+      }
+      if ((t & 7) == 7) {
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          comp_add(phi[i], plo[i], pacc[i]);
+          pacc[i] = 0.f;
+        }
+      }
+      if constexpr (THREE && MS < 2) handoff();
+      if constexpr (THREE) {
         // this thread's part of load slot st is consumed: refill it
         if (t + NS < T) issue(t + NS, st);
         cp_async_commit();
