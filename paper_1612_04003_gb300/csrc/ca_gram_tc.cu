@@ -380,36 +380,38 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       // starts while the loaders finish the stage); with one slot it waits
       // for the MMA of the previous stage, so it runs after the projection.
       auto handoff = [&]() {
-        const int ms = t % MS;
-        if (t >= MS) ok = warp_wait(&empty[ms], (uint32_t)((t / MS - 1) & 1), ok);
-        unsigned char* hi = mring + ms * C::kMmaSlotBytes;
+        if constexpr (THREE) {
+          const int ms = t % MS;
+          if (t >= MS) ok = warp_wait(&empty[ms], (uint32_t)((t / MS - 1) & 1), ok);
+          unsigned char* hi = mring + ms * C::kMmaSlotBytes;
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-          const float4 x = xs[i];
-          if constexpr (BF) {
-            // x = b0 + b1 (+ a remainder below 2^-16 |x|): bf16 head and tail,
-            // 4 columns = 8 bytes, half of a 16-byte chunk of the 64-byte row
-            const int r = g + 32 * i;
-            const uint32_t off = (uint32_t)((r >> 3) * 512 + (r & 7) * 64 +
-                                            ((((l >> 1) ^ ((r >> 1) & 3))) << 4) + (l & 1) * 8);
-            const uint32_t h01 = bf16x2_rn(x.x, x.y), h23 = bf16x2_rn(x.z, x.w);
-            // the tails x - b0 are exact in FP32
-            const uint32_t l01 = bf16x2_rn(x.x - __uint_as_float(h01 << 16),
-                                           x.y - __uint_as_float(h01 & 0xFFFF0000u));
-            const uint32_t l23 = bf16x2_rn(x.z - __uint_as_float(h23 << 16),
-                                           x.w - __uint_as_float(h23 & 0xFFFF0000u));
-            *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
-            *reinterpret_cast<uint2*>(hi + C::kOpTile + off) = make_uint2(l01, l23);
-          } else {
-            const float4 h = make_float4(tf32_head(x.x), tf32_head(x.y), tf32_head(x.z), tf32_head(x.w));
-            *reinterpret_cast<float4*>(hi + dsto[i]) = h;
-            *reinterpret_cast<float4*>(hi + C::kOpTile + dsto[i]) =
-                make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          for (int i = 0; i < RPT; ++i) {
+            const float4 x = xs[i];
+            if constexpr (BF) {
+              // x = b0 + b1 (+ a remainder below 2^-16 |x|): bf16 head and tail,
+              // 4 columns = 8 bytes, half of a 16-byte chunk of the 64-byte row
+              const int r = g + 32 * i;
+              const uint32_t off = (uint32_t)((r >> 3) * 512 + (r & 7) * 64 +
+                                              ((((l >> 1) ^ ((r >> 1) & 3))) << 4) + (l & 1) * 8);
+              const uint32_t h01 = bf16x2_rn(x.x, x.y), h23 = bf16x2_rn(x.z, x.w);
+              // the tails x - b0 are exact in FP32
+              const uint32_t l01 = bf16x2_rn(x.x - __uint_as_float(h01 << 16),
+                                             x.y - __uint_as_float(h01 & 0xFFFF0000u));
+              const uint32_t l23 = bf16x2_rn(x.z - __uint_as_float(h23 << 16),
+                                             x.w - __uint_as_float(h23 & 0xFFFF0000u));
+              *reinterpret_cast<uint2*>(hi + off) = make_uint2(h01, h23);
+              *reinterpret_cast<uint2*>(hi + C::kOpTile + off) = make_uint2(l01, l23);
+            } else {
+              const float4 h = make_float4(tf32_head(x.x), tf32_head(x.y), tf32_head(x.z), tf32_head(x.w));
+              *reinterpret_cast<float4*>(hi + dsto[i]) = h;
+              *reinterpret_cast<float4*>(hi + C::kOpTile + dsto[i]) =
+                  make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+            }
           }
+          fence_proxy_async_smem();  // this thread's tiles, visible to the tensor core
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[ms]);
         }
-        fence_proxy_async_smem();  // this thread's tiles, visible to the tensor core
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[ms]);
       };
       if constexpr (THREE && MS >= 2) handoff();
       // every loader's copies of this stage (incl. the v slice) have landed
