@@ -242,16 +242,20 @@ __device__ void block_solve(const double* __restrict__ R, const double* __restri
 // owners of column k publish it to shared memory (two buffers alternate: one
 // barrier per pivot) and every thread forms 1 / a_kk from it.  Double-float on
 // the FP32 pipe keeps the ~2^-44 accuracy at a fraction of the FP64 latency
-// of this part.  Every thread of the CTA calls this.  Writes Gamma^{-1} (FP32
-// pairs, row-major) to out; a non-positive pivot raises CA_DEV_ERR_NOT_SPD.
-template <int EPT>
+// of this part.  NT = 256: every thread of the CTA calls this; NT = 64 (b <= 8,
+// EPT = 1): warps 0-1 alone call it and the barrier per pivot is named
+// barrier 1 over their 64 threads.
+// Writes Gamma^{-1} (FP32 pairs, row-major) to out; a non-positive pivot
+// raises CA_DEV_ERR_NOT_SPD.
+template <int EPT, int NT = 256>
 __device__ void cta_sweep_inverse(float2 (&a)[EPT], int b, float2* __restrict__ colbuf,
                                   float2* __restrict__ out, unsigned* __restrict__ err) {
-  const int t = threadIdx.x;
+  static_assert(NT == 256 || NT == 64, "a CTA of 256 threads or its first two warps");
+  const int t = threadIdx.x % NT;
   int ri[EPT], ci[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; ++q) {
-    const int e = t + 256 * q;
+    const int e = t + NT * q;
     ri[q] = e < b * b ? e / b : -1;
     ci[q] = e < b * b ? e - ri[q] * b : -1;
   }
@@ -265,7 +269,8 @@ __device__ void cta_sweep_inverse(float2 (&a)[EPT], int b, float2* __restrict__ 
         if (ri[q] == k && !(a[q].x > 0.f)) ca_flag(err, CA_DEV_ERR_NOT_SPD);
       }
     }
-    __syncthreads();
+    if constexpr (NT == 64) asm volatile("bar.sync 1, 64;" ::: "memory");
+    else __syncthreads();
     if (active) {
       // every thread forms 1 / a_kk itself (shorter than a broadcast)
       float2 d = ck[k];
@@ -284,17 +289,17 @@ __device__ void cta_sweep_inverse(float2 (&a)[EPT], int b, float2* __restrict__ 
   }
 #pragma unroll
   for (int q = 0; q < EPT; ++q)
-    if (ri[q] >= 0) out[t + 256 * q] = df_neg(a[q]);
+    if (ri[q] >= 0) out[t + NT * q] = df_neg(a[q]);
 }
 
 // Sum of the partials c = c0, c0 + step, ... < P of one entry (stride sq
-// between partials), as a double-float value.  Up to 24 (FP32) or 16 (FP64)
-// loads are in flight at once (independent of the sums); FP32 partials are
+// between partials), as a double-float value.  Up to U (FP32; FP64: U when
+// U >= 32, else 16) loads are in flight at once (independent of the sums); FP32 partials are
 // added in four compensated chains, FP64 partials by a pairwise FP64 tree.
-template <typename PT>
+template <typename PT, int U = 24>
 __device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c0, int P, int step,
                                                long long sq) {
-  constexpr int U = 24;
+  static_assert(U % 4 == 0, "four compensated chains");
   if constexpr (sizeof(PT) == 4) {
     float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
     for (int base = c0; base < P; base += U * step) {
@@ -311,7 +316,7 @@ __device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c
     return df_add(df_add(df_norm(h[0], l[0]), df_norm(h[1], l[1])),
                   df_add(df_norm(h[2], l[2]), df_norm(h[3], l[3])));
   } else {
-    constexpr int UD = 16;  // a power of two: the pairwise tree below halves it
+    constexpr int UD = U >= 32 ? U : 16;
     double acc = 0.0;
     for (int base = c0; base < P; base += UD * step) {
       double v[UD];
@@ -321,10 +326,14 @@ __device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c
         const double x = __ldcg(src + (long long)min(c, P - 1) * sq);
         v[i] = c < P ? x : 0.0;
       }
+      // pairwise tree over UD <= 128 values: at width w, v[i + w] folds onto
+      // v[i] where it exists
+      static_assert(UD <= 128, "tree depth");
 #pragma unroll
-      for (int w = UD / 2; w >= 1; w /= 2)
+      for (int w = 64; w >= 1; w /= 2)
 #pragma unroll
-        for (int i = 0; i < w; ++i) v[i] += v[i + w];
+        for (int i = 0; i < w; ++i)
+          if (i + w < UD) v[i] += v[i + w];
       acc += v[0];
     }
     return split_f64(acc);
@@ -337,9 +346,11 @@ __device__ __forceinline__ float2 sum_partials(const PT* __restrict__ src, int c
 // stored transposed (entry (i, j), i >= j, at Rs[j * ldr + i]) so that the
 // chain reads a column block with coalesced loads.  CTAs 0 .. ndiag-1 each
 // reduce one diagonal block Gamma_j = cG R_jj + cI I (b <= 16) and invert it
-// into Ginv[j] (cta_sweep_inverse); the other CTAs take 32 entries per pass
-// (one per lane), the 8 warps splitting the P partials.  Sums are
-// double-float; R is written in FP64.
+// into Ginv[j] (cta_sweep_inverse; two warps for b <= 8); the other CTAs take
+// 64 entries per pass (warps 0-3: the first 32, one per lane; warps 4-7: the
+// next 32), the 4 warps of a group splitting the P partials, so that every
+// load of a pass is in flight at once.  Sums are double-float; R is written
+// in FP64.
 template <typename PT>
 __device__ void reduce_body(const PT* __restrict__ part, const double* __restrict__ ppart, int P,
                             int sbp, double* __restrict__ R, float2* __restrict__ Rs,
@@ -353,6 +364,32 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
   const long long sq = (long long)sbp * sbp;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float2 cG2 = split_f64(sa.cG), cI2 = split_f64(sa.cI);
+  if (cta < ndiag && sa.b <= 8) {
+    // thread t sums row i = t % 8 of column jc = (t / 8) % 8 of the block
+    // over the partials c = t / 64 (mod 4): a warp's load covers 4 columns x
+    // 8 rows of one partial, four 32-byte sectors (entry (i, jc) of partial
+    // c at part[c][base + jc][base + i])
+    const int b = sa.b, base = cta * b;
+    const int i = tid & 7, jc = (tid >> 3) & 7, sl = tid >> 6;
+    float2* flat = &red[0][0];  // [4][64]
+    flat[tid] = (i < b && jc < b && i >= jc)
+                    ? sum_partials<PT, 40>(part + (long long)(base + jc) * sbp + (base + i), sl, P, 4, sq)
+                    : make_float2(0.f, 0.f);
+    __syncthreads();
+    if (tid < 64 && i < b && jc < b && i >= jc) {
+      const float2 t = df_add(df_add(flat[tid], flat[64 + tid]), df_add(flat[128 + tid], flat[192 + tid]));
+      float2 v = df_mul(cG2, t);
+      if (i == jc) v = df_add(v, cI2);
+      Mb[i * b + jc] = v;
+      Mb[jc * b + i] = v;
+    }
+    __syncthreads();
+    if (tid < 64) {
+      float2 a[1] = {tid < b * b ? Mb[tid] : make_float2(0.f, 0.f)};
+      cta_sweep_inverse<1, 64>(a, b, colbuf, Ginv + (long long)cta * b * b, err);
+    }
+    return;
+  }
   if (cta < ndiag) {
     const int b = sa.b, base = cta * b;
     const int E = b * (b + 1) / 2;
@@ -381,9 +418,10 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
     return;
   }
   const long long nlow = (long long)sb * (sb + 1) / 2;
-  const long long stride = (long long)(ncta - ndiag) * 32;
-  for (long long e0 = (long long)(cta - ndiag) * 32; e0 < nlow + sb; e0 += stride) {
-    const long long e = e0 + lane;
+  const long long stride = (long long)(ncta - ndiag) * 64;
+  const int grp = warp >> 2, sub = warp & 3;
+  for (long long e0 = (long long)(cta - ndiag) * 64; e0 < nlow + sb; e0 += stride) {
+    const long long e = e0 + grp * 32 + lane;
     int i = 0, j = 0;
     int kind = 0;  // 0 none, 1 Gram entry, 2 projection entry
     float2 s2 = make_float2(0.f, 0.f);
@@ -401,25 +439,23 @@ __device__ void reduce_body(const PT* __restrict__ part, const double* __restric
       i = (int)(e - nlow);
     }
     if (kind == 1) {
-      s2 = sum_partials(part + (long long)j * sbp + i, warp, P, 8, sq);
+      s2 = sum_partials<PT, 40>(part + (long long)j * sbp + i, sub, P, 4, sq);
     } else if (kind == 2) {
-      const float2 q = sum_partials(ppart + i, warp, P, 8, (long long)sbp);
+      const float2 q = sum_partials<double, 40>(ppart + i, sub, P, 4, (long long)sbp);
       sp = (double)q.x + (double)q.y;
     }
     red[warp][lane] = s2;
     redp[warp][lane] = sp;
     __syncthreads();
-    if (warp == 0 && kind) {
+    if (sub == 0 && kind) {  // warps 0 and 4: the group's four sums
+      const int w = warp;
       if (kind == 1) {
-        float2 t = df_add(df_add(df_add(red[0][lane], red[1][lane]), df_add(red[2][lane], red[3][lane])),
-                          df_add(df_add(red[4][lane], red[5][lane]), df_add(red[6][lane], red[7][lane])));
+        const float2 t = df_add(df_add(red[w][lane], red[w + 1][lane]),
+                                df_add(red[w + 2][lane], red[w + 3][lane]));
         R[(long long)i * ldr + j] = (double)t.x + (double)t.y;
         if (Rs) Rs[(long long)j * ldr + i] = df_mul(cG2, t);
       } else {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) t += redp[w][lane];
-        pvec[i] = t;
+        pvec[i] = (redp[w][lane] + redp[w + 1][lane]) + (redp[w + 2][lane] + redp[w + 3][lane]);
       }
     }
     __syncthreads();
