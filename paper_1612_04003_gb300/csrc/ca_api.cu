@@ -38,7 +38,8 @@ struct ca_ctx {
   void* arena = nullptr;
   size_t arena_bytes = 0;
   unsigned* d_err = nullptr;     // device error word
-  unsigned* d_ticket = nullptr;  // last-CTA ticket of the reduce/solve kernel
+  unsigned* d_ticket = nullptr;  // count of the reducing CTAs of the reduce/solve kernel
+                                 // (d_err + 32; both cleared where a call starts)
   unsigned* h_err = nullptr;     // pinned copy
   Profile prof;
   char last_error[256] = {0};    // text of the last failing CUDA call
@@ -300,9 +301,11 @@ int launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const 
   const int G = (int)std::max(1LL, std::min<long long>(passes, 8LL * ctx->num_sms));
   const int ndiag = (fast && sa.b <= 16) ? sa.s_cur : 0;
   if (g.tc && ndiag) {
-    // one launch: reduce (+ diagonal inverses), then the chain on the last
-    // CTA; one CTA per SM (the chain's shared memory), so at most num_sms
-    const int grid = (int)std::min<long long>(passes + ndiag, ctx->num_sms);
+    // one launch: reducing CTAs (64 entries per pass, + the diagonal
+    // inverses) and one more CTA for the chain; at most one CTA per SM
+    const int grid =
+        (int)std::max<long long>(1, std::min<long long>((entries + 63) / 64 + ndiag,
+                                                        ctx->num_sms - 1)) + 1;
     prof_mark(ctx, PC_SOLVE);
     const int e = launch_reduce_chain(grid, chain_smem(sa.b, sa.sb), ctx->stream,
                                       static_cast<const float*>(part), ppart, g.P, g.sbp, R, Rs,
@@ -605,7 +608,7 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   float2* w2s = cv.take<float2>((size_t)d);
   int* idx = cv.take<int>((size_t)o->H * o->b);
   char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
-  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
 
   DenseProblem pb;
   pb.xfmt = xf;
@@ -693,7 +696,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* delta = cv.take<double>(sbp);
     float2* Ginv = cv.take<float2>(sbp * CA_FAST_B);
     float2* Rs = cv.take<float2>(sbp * sbp);
-    CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+    CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
     auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
       k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
       k_scatter_csr<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, nullptr, n, d,
@@ -784,7 +787,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   float2* a2s = cv.take<float2>((size_t)n);
   int* idx = cv.take<int>((size_t)o->H * o->b);
   char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
-  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
   DenseProblem pb;
   pb.xfmt = xf;
   pb.A = Xd;
@@ -880,7 +883,7 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   double* ppart = cv.take<double>((size_t)g.P * g.sbp);
   double* R = cv.take<double>((size_t)g.sbp * g.sbp);
   float2* v2 = cv.take<float2>((size_t)Kp);
-  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
   k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, ctx->stream>>>(v, K, Kp, v2);
   CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, v2, part, ppart));
   SolveArgs sa{idx, N, 1, 0, sb, g.sbp, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
@@ -894,7 +897,7 @@ int ca_selftest_wait_timeout(ca_ctx* ctx, long long limit_ns) {
   t_cur_ctx = ctx;
   if (!ctx || limit_ns < 1 || limit_ns > 1000000000LL) return CA_ERR_ARG;
   CA_TRY_CUDA(cudaSetDevice(ctx->device));
-  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(unsigned), ctx->stream));
+  CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
   k_selftest_wait<<<1, 32, 0, ctx->stream>>>((unsigned long long)limit_ns, ctx->d_err);
   CA_TRY_CUDA(cudaGetLastError());
   return finish(ctx);

@@ -657,7 +657,8 @@ __device__ __forceinline__ void named_bar_arrive(int id) {
 template <int BMAX, int DEPTH>
 __device__ void chain_la_body(const float2* __restrict__ Rs, const double* __restrict__ pvec,
                               const float2* __restrict__ Ginv, const SolveArgs& a,
-                              unsigned* __restrict__ err, double* smem_d) {
+                              unsigned* __restrict__ err, double* smem_d,
+                              unsigned* __restrict__ ticket = nullptr, unsigned nready = 0) {
   static_assert(BMAX == 8 || BMAX == 16, "lookahead chain: BMAX 8 or 16");
   constexpr int LPR = 32 / BMAX, CPL = BMAX / LPR;  // warp 0: lanes per row, columns per lane
   constexpr unsigned FULL = 0xffffffffu;
@@ -686,21 +687,35 @@ __device__ void chain_la_body(const float2* __restrict__ Rs, const double* __res
     }
     cp_async_commit();
   };
-  if (warp > 0)
-    for (int d = 0; d < DEPTH - 1; ++d) fetch(d);
-  for (int e = tid; e < sb * b; e += 256) Gs[e] = __ldcg(Ginv + e);
+  // the sampled indices and x0, y there do not depend on the reduction
+  double xy = 0.0;  // -cI x0[I] - cY y[I]
   if (tid < sb) {
     const int gi = a.idx[tid];
-    double v = a.cP * __ldcg(pvec + tid);
     if (gi >= 0 && gi < a.N) {
-      v -= a.cI * __ldcg(a.x + gi);
-      if (a.yv) v -= a.cY * a.yv[gi];
+      xy = -a.cI * __ldcg(a.x + gi);
+      if (a.yv) xy -= a.cY * a.yv[gi];
     } else {
       ca_flag(err, CA_DEV_ERR_ARG);
     }
-    rhs0s[tid] = split_f64(v);
     sidx[tid] = gi;
   }
+  if (ticket) {  // the reducing CTAs of this grid: R, Rs, p and Ginv complete
+    if (tid == 0) {
+      const uint64_t t0 = ca_globaltimer();
+      for (uint32_t it = 1; *(volatile unsigned*)ticket < nready; ++it)
+        if ((it & 255u) == 0u && ca_globaltimer() - t0 > CA_WAIT_LIMIT_NS) {
+          ca_flag(err, CA_DEV_ERR_TIMEOUT);
+          break;
+        }
+      *ticket = 0u;  // for the next launch (which starts after this grid ends)
+      __threadfence();
+    }
+    __syncthreads();
+  }
+  if (warp > 0)
+    for (int d = 0; d < DEPTH - 1; ++d) fetch(d);
+  for (int e = tid; e < sb * b; e += 256) Gs[e] = __ldcg(Ginv + e);
+  if (tid < sb) rhs0s[tid] = split_f64(a.cP * __ldcg(pvec + tid) + xy);
   if (warp > 0) cp_async_wait<DEPTH - 2>();  // step 0's columns
   __syncthreads();
   const float2 cI2 = split_f64(a.cI);
@@ -828,13 +843,16 @@ k_chain(const float2* __restrict__ Rs, const double* __restrict__ pvec,
     chain_body<BMAX, DEPTH>(Rs, pvec, Ginv, a, err, smem_d);
 }
 
-// a4 in one launch (b <= 16): the reduction with the diagonal-block
-// inverses (reduce_body), then the CTA that finishes last (ticket counter;
-// no CTA waits for another) runs the chain.  Launched as a programmatic
-// dependent of the Gram pass: it waits for that grid, then lets the next
-// Gram pass launch its CTAs, which prepare and start their loads on the SMs
-// this grid frees while the chain runs.  *ticket is zero on entry and left
-// zero.
+// a4 in one launch (b <= 16): CTAs 0 .. G-2 reduce (reduce_body, with the
+// diagonal-block inverses) and count themselves done on *ticket; the last CTA
+// runs the chain: it gathers what does not depend on the reduction (sampled
+// indices, x0 and y there) while the others reduce, then waits (bounded) for
+// the count.  Every CTA of the grid is resident before the next grid in the
+// stream can start, and none of them waits for anything but this grid's
+// reducing CTAs.  Launched as a programmatic dependent of the Gram pass: it
+// waits for that grid, then lets the next Gram pass launch its CTAs, which
+// prepare and start their loads on the SMs this grid frees while the chain
+// runs.  *ticket is zero on entry and left zero.
 template <typename PT, int BMAX, int DEPTH>
 __global__ void __launch_bounds__(256)
 k_reduce_chain(const PT* __restrict__ part, const double* __restrict__ ppart, int P, int sbp,
@@ -842,22 +860,19 @@ k_reduce_chain(const PT* __restrict__ part, const double* __restrict__ ppart, in
                float2* __restrict__ Ginv, int ndiag, SolveArgs sa, unsigned* __restrict__ err,
                unsigned* __restrict__ ticket) {
   extern __shared__ double smem_d[];
-  __shared__ int s_last;
   pdl_wait();
   pdl_trigger();
-  reduce_body<PT>(part, ppart, P, sbp, R, Rs, pvec, Ginv, ndiag, sa, err, (int)blockIdx.x,
-                  (int)gridDim.x);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();  // this CTA's R, Rs, p, Ginv before its ticket
-    const unsigned t = atomicAdd(ticket, 1u);
-    s_last = (t == gridDim.x - 1);
-    if (s_last) atomicExch(ticket, 0u);
+  const int nred = (int)gridDim.x - 1;
+  if ((int)blockIdx.x < nred) {
+    reduce_body<PT>(part, ppart, P, sbp, R, Rs, pvec, Ginv, ndiag, sa, err, (int)blockIdx.x, nred);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this CTA's R, Rs, p, Ginv before its count
+      atomicAdd(ticket, 1u);
+    }
+    return;
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  chain_la_body<BMAX, DEPTH>(Rs, pvec, Ginv, sa, err, smem_d);
+  chain_la_body<BMAX, DEPTH>(Rs, pvec, Ginv, sa, err, smem_d, ticket, (unsigned)nred);
 }
 
 template __global__ void k_reduce_chain<float, 8, 4>(const float*, const double*, int, int, double*,
