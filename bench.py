@@ -43,6 +43,7 @@ D, N_SAMPLES, COND, LAM, B, S, H = 4096, 262144, 1e3, 1e-4, 8, 16, 4096
 # that does)
 PREC = "bf16x3"
 DTYPE = {"bf16x3": "bf16x3 (bf16 split products, fp32 accumulate; fp64 solves)",
+         "fp16_scaled": "fp16 (per-row power-of-two scaling, fp32 accumulate; fp64 solves)",
          "3xtf32": "3xtf32 (fp32-faithful split products; fp64 solves)",
          "tf32": "tf32 (fp32 accumulate; fp64 solves)"}
 
@@ -286,6 +287,33 @@ def secondary_workloads(ctx, stream):
     return out
 
 
+def gram_conditioning(ctx, X, lam, b, n_outer=64, s_list=(1, 2, 4, 8, 16)):
+    """Condition numbers of the s*b x s*b Gram matrices Y Y^T / n + lambda I
+    that the solve factors (the first n_outer outer steps of the seed-42
+    index stream, for each s), from the library's sampler and its FP64 Gram
+    of the FP32 X; the condition number itself is analysis (torch, FP64).
+    Returns min / median / max per s."""
+    import torch
+    d, n = X.shape
+    smax = max(s_list)
+    idx_all = torch.empty(n_outer * smax * b, dtype=torch.int32, device="cuda")
+    ctx.ca_sample_indices(42, 0, n_outer * smax, b, d, idx_all)
+    v0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = {}
+    for s_ in s_list:
+        sb = s_ * b
+        G = torch.empty((sb, sb), dtype=torch.float64, device="cuda")
+        p = torch.empty(sb, dtype=torch.float64, device="cuda")
+        eye = torch.eye(sb, dtype=torch.float64, device="cuda")
+        cs = []
+        for k in range(n_outer):
+            ctx.ca_gram_project(X, idx_all[k * sb:(k + 1) * sb], v0, G, p, prec="f64")
+            cs.append(float(torch.linalg.cond(G / n + lam * eye)))
+        cs.sort()
+        out[f"s={s_}"] = {"min": cs[0], "median": cs[len(cs) // 2], "max": cs[-1]}
+    return {"b": b, "outer_steps": n_outer, "cond_gram": out}
+
+
 def precision_study(args) -> int:
     """--precision-study: the precision configuration of the benchmark family:
     X 8192 x 131072 FP32 with geometric row scaling (condition 1e2, 1e4, 1e6),
@@ -301,7 +329,7 @@ def precision_study(args) -> int:
     torch.cuda.set_stream(stream)
     ctx = ca.Context(0, stream=stream.cuda_stream)
     d, n, lam, b, s_, H = 8192, 131072, 1e-6, 16, 16, 8192
-    rows = []
+    rows, gram_cond = [], []
     for cond in (1e2, 1e4, 1e6):
         X, y, _ = synth.dense_primal_torch(d, n, cond=cond, seed=1, device="cuda")
         kw = dict(b=b, s=s_, H=H, lam=lam, seed=42, recompute_every=8)
@@ -315,7 +343,7 @@ def precision_study(args) -> int:
         t64 = _device_time(stream, lambda: ctx.ca_bcd_solve(X64, y, w_ref.zero_(), prec="f64", **kw), 1)
         del X64
         f_ref = objective(w_ref)
-        for prec in ("3xtf32", "bf16x3", "tf32"):
+        for prec in ("3xtf32", "bf16x3", "tf32", "fp16_scaled"):
             w = torch.zeros(d, dtype=torch.float64, device="cuda")
             ctx.ca_bcd_solve(X, y, w, prec=prec, **kw)
             t = _device_time(stream, lambda: ctx.ca_bcd_solve(X, y, w.zero_(), prec=prec, **kw), 2)
@@ -326,10 +354,11 @@ def precision_study(args) -> int:
                          "block_updates_per_s": H / (t * 1e-3)})
         rows.append({"cond": cond, "gram": "f64 (FP64 X, reference)", "rel_err_w_vs_fp64": 0.0,
                      "rel_objective_diff": 0.0, "block_updates_per_s": H / (t64 * 1e-3)})
+        gram_cond.append({"cond": cond, **gram_conditioning(ctx, X, lam, b)})
         del X, y
     print(json.dumps({"study": "precision", "workload": "dense primal CA-BCD, X 8192 x 131072 FP32, "
                       "lambda 1e-6, b=16, s=16, H=8192, recompute every 8 outer steps",
-                      "rows": rows}), flush=True)
+                      "rows": rows, "gram_conditioning": gram_cond}), flush=True)
     ctx.close()
     return 0
 

@@ -81,7 +81,14 @@ typedef enum {
   CA_GRAM_BF16X3 = 3,     /* FP32 X: x = b0 + b1 in BF16, b0 b0^T + b0 b1^T +
                            * b1 b0^T on tcgen05 (kind::f16), FP32 accumulate;
                            * each product within about 2^-16 |x| |y|          */
-  CA_GRAM_FP16_SCALED = 4 /* reserved (CA_ERR_UNSUPPORTED)                     */
+  CA_GRAM_FP16_SCALED = 4 /* FP32 X: each row of A times a power of two that
+                           * brings its largest magnitude into [2^14, 2^15),
+                           * rounded to FP16, one product on tcgen05
+                           * (kind::f16), FP32 accumulate, scales removed
+                           * exactly; per-entry rounding 2^-11 (like TF32).
+                           * The solve computes the scales in one pass over
+                           * X.  Not in ca_gram_project_noalloc
+                           * (CA_ERR_UNSUPPORTED).                           */
 } ca_prec;
 
 /* Solve options. */
@@ -161,8 +168,8 @@ int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long l
  * (leading dimension ld), writes G = Y Y^T (sb x sb, row-major, FP64, full
  * symmetric, no scaling and no lambda) and p = Y v (sb, FP64), where v has K
  * entries.  A, idx, v, G and p must be device memory.  xfmt and prec as for
- * the solves (TF32 / 3xTF32 / BF16x3 need FP32 A, 16-byte aligned rows,
- * sb <= 256).
+ * the solves (TF32 / 3xTF32 / BF16x3 / scaled FP16 need FP32 A, 16-byte
+ * aligned rows, sb <= 256).
  * Errors: CA_ERR_ARG, CA_ERR_UNSUPPORTED, CA_ERR_OOM, CA_ERR_CUDA. */
 int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N, long long K,
                     long long ld, const int* idx, int sb, const double* v, double* G, double* p);

@@ -37,7 +37,7 @@ CA_GRAM_BF16X3 = 3
 CA_GRAM_FP16_SCALED = 4
 
 PREC = {"f64": CA_GRAM_F64, "fp32_exact": CA_GRAM_FP32_EXACT, "3xtf32": CA_GRAM_FP32_EXACT,
-        "tf32": CA_GRAM_TF32, "bf16x3": CA_GRAM_BF16X3}
+        "tf32": CA_GRAM_TF32, "bf16x3": CA_GRAM_BF16X3, "fp16_scaled": CA_GRAM_FP16_SCALED}
 
 
 class ca_opts(ctypes.Structure):

@@ -183,6 +183,7 @@ struct DenseProblem {
   long long N, K, lda;
   double* v;                // K: projection vector (rho or w), device
   float2* v2;               // its (hi, lo) FP32 split, zero-padded to a multiple of 32
+  const float* rscale = nullptr;  // scaled FP16 Gram: per-row multipliers of A (N)
   double* x;                // N: variable updated by the solves (w or alpha), device
   float2* x2;               // N: scratch for the (hi, lo) FP32 split of x (recompute)
   const double* yv;         // dual: y (device), primal: nullptr
@@ -221,7 +222,8 @@ int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const do
 
 // Gram precisions that run on the tcgen05 path (FP32 X only).
 bool tc_prec(int prec) {
-  return prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT || prec == CA_GRAM_BF16X3;
+  return prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT || prec == CA_GRAM_BF16X3 ||
+         prec == CA_GRAM_FP16_SCALED;
 }
 
 // Split-K plan of the a2+a3 pass for a given s*b bound.
@@ -234,7 +236,10 @@ struct GramPlan {
 GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
   GramPlan g{};
   g.tc = (xfmt == CA_DENSE_F32) && tc_prec(prec);
-  g.three = (prec == CA_GRAM_FP32_EXACT) ? 1 : (prec == CA_GRAM_BF16X3 ? 2 : 0);
+  g.three = prec == CA_GRAM_FP32_EXACT ? 1
+            : prec == CA_GRAM_BF16X3    ? 2
+            : prec == CA_GRAM_FP16_SCALED ? 3
+                                          : 0;
   if (g.tc) {
     g.sbp = sbm <= 32 ? 32 : (sbm <= 64 ? 64 : (sbm <= 128 ? 128 : 256));
     g.P = (int)std::min<long long>(ctx->num_sms, (K + 31) / 32);
@@ -256,11 +261,13 @@ GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
 // a2+a3: split-K partials of Y Y^T and Y v for the sampled rows idx[0..sb).
 int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long long lda, long long N,
                 long long K, const int* idx, int sb, const double* v, const float2* v2, void* part,
-                double* ppart, bool panel = false) {
+                double* ppart, bool panel = false, const float* rscale = nullptr) {
   if (g.tc) {
+    GramUpdate none{};
+    none.rscale = rscale;
     const int e = launch_gram_tc(static_cast<const float*>(A), lda, N, K, idx, sb, v2, g.P, g.sbp,
                                  static_cast<float*>(part), ppart, ctx->d_err, g.three, ctx->stream,
-                                 nullptr, panel);
+                                 &none, panel);
     return e == 0 ? CA_OK : CA_ERR_CUDA;
   }
   launch_gram_simt(xfmt == CA_DENSE_F64, dim3(g.P, g.ntiles), ctx->stream, A, lda, N, K, idx, sb, v,
@@ -388,7 +395,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
       if (due(k - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));  // a6
     }
     // a2 + a3 (and a5 of step k-1 when fused)
-    GramUpdate gu{prev_idx, pending ? prev_sb : 0, prev_delta, pb.cU, pb.v2};
+    GramUpdate gu{prev_idx, pending ? prev_sb : 0, prev_delta, pb.cU, pb.v2, pb.rscale};
     prof_mark(ctx, PC_GRAM);
     if (pending) {
       const int e = launch_gram_tc(static_cast<const float*>(pb.A), pb.lda, pb.N, K, idx, sb, pb.v2,
@@ -398,7 +405,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
       pending = false;
     } else {
       CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart,
-                         pb.panel));
+                         pb.panel, pb.rscale));
     }
     prof_mark(ctx, PC_GRAM);
     ctx->prof.kernel_launches += 1;
@@ -558,7 +565,6 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   CA_TRY(check_opts(o, d));
   const int xf = pre ? (int)CA_DENSE_F32 : xfmt;  // element type of X
   const bool tc = (xf == CA_DENSE_F32) && tc_prec(o->prec);
-  if (o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
   if (pre && !tc) return CA_ERR_ARG;
   if (tc) {
     if ((!pre && (ld & 3) != 0) || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return CA_ERR_ARG;
@@ -578,6 +584,8 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   const void* x_mapped = (x_host && tc && !pre) ? mapped_host_ptr(X) : nullptr;
   if (x_host && !x_mapped) need += align256(xbytes) + 256;
   if (tc && !pre) need += align256(panel_bytes(d, n)) + 256;
+  const bool f16 = tc && o->prec == CA_GRAM_FP16_SCALED;
+  if (f16) need += align256((size_t)d * 4) + 256;
   if (y_host) need += align256((size_t)n * 8);
   if (w_host) need += align256((size_t)d * 8);
   if (z_host) need += align256((size_t)n * 8);
@@ -600,6 +608,12 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
     Xd = pk;
     panel = true;
   }
+  float* rsc = nullptr;  // scaled FP16 Gram: per-feature multipliers (one pass over X)
+  if (f16) {
+    rsc = cv.take<float>((size_t)d);
+    launch_row_scale(ctx->stream, static_cast<const float*>(Xd), ld, d, n, panel, rsc);
+    ctx->prof.kernel_launches += 1;
+  }
   const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
   double* wd = stage(ctx, cv, w, (size_t)d, true, &st);
   double* zd = z ? stage(ctx, cv, z, (size_t)n, false, &st) : nullptr;
@@ -619,6 +633,7 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   pb.lda = ld;
   pb.v = rho;
   pb.v2 = rho2;
+  pb.rscale = rsc;
   pb.x = wd;
   pb.x2 = w2s;
   pb.yv = nullptr;
@@ -748,7 +763,6 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   if (!pre && ld < d) return CA_ERR_ARG;
   const int xf = pre ? (int)CA_DENSE_F32 : xfmt;
   const bool tc = (xf == CA_DENSE_F32) && tc_prec(o->prec);
-  if (o->prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;
   if (pre && !tc) return CA_ERR_ARG;
   if (tc) {
     if ((!pre && (ld & 3) != 0) || (reinterpret_cast<uintptr_t>(XT) & 15) != 0) return CA_ERR_ARG;
@@ -762,6 +776,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   const void* x_mapped = (x_host && tc && !pre) ? mapped_host_ptr(XT) : nullptr;
   if (x_host && !x_mapped) need += align256(xbytes) + 256;
   if (tc && !pre) need += align256(panel_bytes(n, d)) + 256;
+  const bool f16 = tc && o->prec == CA_GRAM_FP16_SCALED;
+  if (f16) need += align256((size_t)n * 4) + 256;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
   bool st;
@@ -780,6 +796,12 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     Xd = pk;
     panel = true;
   }
+  float* rsc = nullptr;  // scaled FP16 Gram: per-sample multipliers (one pass over X)
+  if (f16) {
+    rsc = cv.take<float>((size_t)n);
+    launch_row_scale(ctx->stream, static_cast<const float*>(Xd), ld, n, d, panel, rsc);
+    ctx->prof.kernel_launches += 1;
+  }
   const double* yd = stage(ctx, cv, y, (size_t)n, true, &st);
   double* ad = stage(ctx, cv, alpha, (size_t)n, true, &st);
   double* wd = stage(ctx, cv, w, (size_t)d, false, &st);
@@ -797,6 +819,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   pb.lda = ld;
   pb.v = wd;
   pb.v2 = w2;
+  pb.rscale = rsc;
   pb.x = ad;
   pb.x2 = a2s;
   pb.yv = yd;
@@ -860,7 +883,7 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
       sb > kMaxSB)
     return CA_ERR_ARG;
   if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32) return CA_ERR_ARG;
-  if (prec < CA_GRAM_F64 || prec > CA_GRAM_BF16X3) return CA_ERR_ARG;
+  if (prec < CA_GRAM_F64 || prec > CA_GRAM_FP16_SCALED) return CA_ERR_ARG;
   const bool tc = (xfmt == CA_DENSE_F32) && tc_prec(prec);
   if (tc) {
     if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return CA_ERR_ARG;
@@ -875,9 +898,11 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   const long long Kp = (K + 31) / 32 * 32;
   const size_t need = align256((size_t)g.P * g.sbp * g.sbp * el) + align256((size_t)g.P * g.sbp * 8) +
                       align256((size_t)g.sbp * g.sbp * 8) + align256((size_t)g.sbp * 8) +
-                      align256((size_t)Kp * 8) + 1024;
+                      align256((size_t)Kp * 8) + align256((size_t)N * 4) + 1024;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
+  const bool f16 = g.tc && prec == CA_GRAM_FP16_SCALED;
+  float* rsc = f16 ? cv.take<float>((size_t)N) : nullptr;  // per-row FP16 multipliers
   void* part = g.tc ? (void*)cv.take<float>((size_t)g.P * g.sbp * g.sbp)
                     : (void*)cv.take<double>((size_t)g.P * g.sbp * g.sbp);
   double* ppart = cv.take<double>((size_t)g.P * g.sbp);
@@ -885,7 +910,8 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   float2* v2 = cv.take<float2>((size_t)Kp);
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
   k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, ctx->stream>>>(v, K, Kp, v2);
-  CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, v2, part, ppart));
+  if (f16) launch_row_scale(ctx->stream, static_cast<const float*>(A), ld, N, K, false, rsc);
+  CA_TRY(launch_gram(ctx, g, xfmt, A, ld, N, K, idx, sb, v, v2, part, ppart, false, rsc));
   SolveArgs sa{idx, N, 1, 0, sb, g.sbp, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr, nullptr};
   CA_TRY(launch_reduce_solve(ctx, g, part, ppart, R, nullptr, p, nullptr, sa));
   k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(R, g.sbp, sb, G);

@@ -43,7 +43,7 @@ constexpr int kLoaderThreads = 32 * kLoaderWarps;    // loaders / projection / e
 constexpr int kMmaWarp = kLoaderWarps;               // TMEM allocation and MMA issue
 constexpr int kThreads = kLoaderThreads + 32;
 
-template <int SBP, bool THREE, bool UPD = false, bool BF = false>
+template <int SBP, bool THREE, bool UPD = false, bool BF = false, bool F16 = false>
 struct TcCfg {
   static constexpr int kTileBytes = SBP * 128;                  // SBP rows x 32 fp32
   // operand tiles of the split modes: 3xTF32 rows of 32 fp32 (128-byte
@@ -57,7 +57,8 @@ struct TcCfg {
   // kMS slots that the MMA reads, so a load slot is free again as soon as its
   // own thread has consumed it (no wait on the MMA before a refill).  Plain
   // TF32: the MMA reads the load slot itself.
-  static constexpr int kMmaSlotBytes = THREE ? 2 * kOpTile : 0;
+  // (scaled FP16: one tile, x s_r rounded to FP16, one product)
+  static constexpr int kMmaSlotBytes = THREE ? (F16 ? 1 : 2) * kOpTile : 0;
   static constexpr int kBudget = 200 * 1024;                    // both rings
   static constexpr int kMS =
       THREE ? ((kBudget - 2 * kMmaSlotBytes) / kRawBytes >= 4 ? 2 : 1) : 0;
@@ -66,7 +67,7 @@ struct TcCfg {
   static constexpr int kMmaRing = kMS * kMmaSlotBytes;
   // SBP <= 128 with the 3-product split keeps two accumulators: D = hi hi^T
   // and T = hi lo^T (lo hi^T = T^T is added in the epilogue)
-  static constexpr bool kSym = (SBP <= 128) && THREE;
+  static constexpr bool kSym = (SBP <= 128) && THREE && !F16;
   static constexpr int kTmemCols = (SBP == 256) ? 512 : (kSym ? 256 : 128);
   // the M = 128 MMA reads 128 rows of its A tile; with SBP < 128 the rows past
   // the tile are whatever follows in shared memory (their accumulator rows
@@ -126,6 +127,18 @@ __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
   return d;
 }
 
+// (lo, hi) rounded to FP16 (nearest even), packed: lo in bits 0-15.
+__device__ __forceinline__ uint32_t f16x2_rn(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
+  // kind::f16 instruction descriptor with A = B = FP16 (format 0), D = F32
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
   // kind::tf32 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = TF32
   // (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
@@ -176,15 +189,18 @@ __device__ __forceinline__ float tf32_head(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-template <int SBP, bool THREE, bool UPD, bool PANEL, bool BF>
+template <int SBP, bool THREE, bool UPD, bool PANEL, bool BF, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
           const int* __restrict__ idx, int sb, const float2* __restrict__ v2, long long natoms,
           float* __restrict__ part, double* __restrict__ ppart, unsigned* __restrict__ err,
           GramUpdate u) {
-  using C = TcCfg<SBP, THREE, UPD, BF>;
+  using C = TcCfg<SBP, THREE, UPD, BF, F16>;
+  static_assert(!F16 || (THREE && BF), "scaled FP16 uses the 16-bit operand ring");
   constexpr int NS = C::kNS, MS = C::kMS, RPT = C::kRPT;
   extern __shared__ unsigned char smem_raw[];
+  // scaled FP16: 1 / multiplier of each tile row (exact powers of two)
+  __shared__ float s_rinv[F16 ? SBP : 1];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* mring = smem;                    // MS x [head tile | tail tile] (3xTF32)
@@ -244,6 +260,17 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       if (r < sb && !in_range) ca_flag(err, CA_DEV_ERR_ARG);  // skipped, never read
       rowoff[i] = in_range ? gi * (PANEL ? 32 : lda) : -1;
       dsto[i] = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((l ^ (r & 7)) << 4));
+    }
+    // scaled FP16: the multiplier of each of this thread's rows (a power of
+    // two that brings the row's largest magnitude into [2^14, 2^15))
+    float rsc[F16 ? RPT : 1];
+    if constexpr (F16) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const int r = g + 32 * i;
+        rsc[i] = rowoff[i] >= 0 ? __ldg(u.rscale + idx[r]) : 1.f;
+        if (l == 0) s_rinv[r] = 1.f / rsc[i];
+      }
     }
     // fused update: this thread's rows of the previous outer step (their
     // Delta is read once the preceding grid has finished, below)
@@ -387,7 +414,15 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
 #pragma unroll
           for (int i = 0; i < RPT; ++i) {
             const float4 x = xs[i];
-            if constexpr (BF) {
+            if constexpr (F16) {
+              // x s_r rounded to FP16, 4 columns = 8 bytes (64-byte rows)
+              const int r = g + 32 * i;
+              const uint32_t off = (uint32_t)((r >> 3) * 512 + (r & 7) * 64 +
+                                              ((((l >> 1) ^ ((r >> 1) & 3))) << 4) + (l & 1) * 8);
+              const float sc = rsc[i];
+              *reinterpret_cast<uint2*>(hi + off) =
+                  make_uint2(f16x2_rn(x.x * sc, x.y * sc), f16x2_rn(x.z * sc, x.w * sc));
+            } else if constexpr (BF) {
               // x = b0 + b1 (+ a remainder below 2^-16 |x|): bf16 head and tail,
               // 4 columns = 8 bytes, half of a 16-byte chunk of the 64-byte row
               const int r = g + 32 * i;
@@ -499,6 +534,14 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
     // that the 32 lanes (32 consecutive rows) of a warp write 128 contiguous
     // bytes per column
     float* Pc = part + (long long)c * SBP * SBP;
+    if constexpr (F16) {  // every loader's s_rinv entries are in place
+      asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
+    }
+    // scaled FP16: entry (row, col) of the accumulator carries s_row s_col
+    auto unscale = [&](float v, int row, int col) {
+      if constexpr (F16) return v * s_rinv[row] * s_rinv[col];
+      else return v;
+    };
     if constexpr (C::kSym) {
       // G = D + T + T^T: T goes through the (now idle) stage buffers as a
       // 128 x 129 FP32 array, read back transposed without bank conflicts
@@ -528,7 +571,8 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       tmem_ld32(tbase + (uint32_t)cc, r);
       if (cc <= trow && trow < SBP) {  // rows past a short tile hold garbage
 #pragma unroll
-        for (int q = 0; q < 32; ++q) Pc[(long long)(cc + q) * SBP + trow] = __uint_as_float(r[q]);
+        for (int q = 0; q < 32; ++q)
+          Pc[(long long)(cc + q) * SBP + trow] = unscale(__uint_as_float(r[q]), trow, cc + q);
       }
     }
     if constexpr (SBP == 256) {
@@ -538,14 +582,15 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         tmem_ld32(tbase + 128u + (uint32_t)cc, r);
         if (cc <= grow) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) Pc[(long long)(cc + q) * SBP + grow] = __uint_as_float(r[q]);
+          for (int q = 0; q < 32; ++q)
+            Pc[(long long)(cc + q) * SBP + grow] = unscale(__uint_as_float(r[q]), grow, cc + q);
         }
       }
     }
   } else if (lane == 0) {
     // ---------------- MMA issue (one thread) ----------------
-    const uint32_t id1 = BF ? idesc_bf16(128, n1) : idesc_tf32(128, n1);
-    const uint32_t id2 = BF ? idesc_bf16(128, n2) : idesc_tf32(128, n2);
+    const uint32_t id1 = F16 ? idesc_f16(128, n1) : (BF ? idesc_bf16(128, n1) : idesc_tf32(128, n1));
+    const uint32_t id2 = F16 ? idesc_f16(128, n2) : (BF ? idesc_bf16(128, n2) : idesc_tf32(128, n2));
     // one K step: 8 tf32 or 16 bf16 = 32 bytes of a row
     auto desc = [](uint32_t a) { return BF ? sw64_kmajor_desc(a) : sw128_kmajor_desc(a); };
     auto mma = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
@@ -576,7 +621,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         if constexpr (C::kSym) {
           const uint64_t l0 = desc(lb + kk * 32);
           mma(tmem + 128u, h0, l0, id1, acc);  // T = hi lo^T
-        } else if constexpr (THREE) {
+        } else if constexpr (THREE && !F16) {
           const uint64_t l0 = desc(lb + kk * 32);
           mma(tmem, h0, l0, id1, 1u);
           mma(tmem, l0, h0, id1, 1u);
@@ -584,7 +629,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         if constexpr (SBP == 256) {
           const uint64_t h1 = desc(hb + (THREE ? kHalf : 16384u) + kk * 32);
           mma(tmem + 128u, h1, h0, id2, acc);
-          if constexpr (THREE) {
+          if constexpr (THREE && !F16) {
             const uint64_t l0 = desc(lb + kk * 32);
             const uint64_t l1 = desc(lb + kHalf + kk * 32);
             mma(tmem + 128u, h1, l0, id2, 1u);
@@ -608,14 +653,14 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
   }
 }
 
-template <int SBP, bool THREE, bool UPD, bool PANEL, bool BF>
+template <int SBP, bool THREE, bool UPD, bool PANEL, bool BF, bool F16 = false>
 int launch_one(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
                const float2* v2, int P, float* part, double* ppart, unsigned* err,
                const GramUpdate& u, cudaStream_t stream) {
-  using C = TcCfg<SBP, THREE, UPD, BF>;
+  using C = TcCfg<SBP, THREE, UPD, BF, F16>;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD, PANEL, BF>,
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD, PANEL, BF, F16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return (int)e;
     configured = true;
@@ -633,7 +678,7 @@ int launch_one(const float* A, long long lda, long long N, long long K, const in
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gram_tc<SBP, THREE, UPD, PANEL, BF>, A, lda, N, K, idx,
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_gram_tc<SBP, THREE, UPD, PANEL, BF, F16>, A, lda, N, K, idx,
                                            sb, v2, natoms, part, ppart, err, u);
   if (e != cudaSuccess) return (int)e;
   return (int)cudaGetLastError();
@@ -646,8 +691,10 @@ int gram_tc_max_sb() { return 256; }
 int launch_gram_tc(const float* A, long long lda, long long N, long long K, const int* idx, int sb,
                    const float2* v2, int P, int sbp, float* part, double* ppart, unsigned* err,
                    int three_pass, cudaStream_t stream, const GramUpdate* upd, bool panel) {
-  const GramUpdate none{};
-  // three_pass: 0 = TF32, 1 = 3xTF32, 2 = BF16x3
+  // three_pass: 0 = TF32, 1 = 3xTF32, 2 = BF16x3, 3 = scaled FP16 (needs upd->rscale)
+  GramUpdate none{};
+  if (upd) none.rscale = upd->rscale;
+  if (three_pass == 3 && !none.rscale) return (int)cudaErrorInvalidValue;
 #define CA_TC_CASE(S, U, PN, UU)                                                              \
   if (sbp == S) {                                                                            \
     if (three_pass == 0)                                                                     \
@@ -656,6 +703,9 @@ int launch_gram_tc(const float* A, long long lda, long long N, long long K, cons
     if (three_pass == 1)                                                                     \
       return launch_one<S, true, U, PN, false>(A, lda, N, K, idx, sb, v2, P, part, ppart, err,  \
                                                UU, stream);                                  \
+    if (three_pass == 3)                                                                     \
+      return launch_one<S, true, U, PN, true, true>(A, lda, N, K, idx, sb, v2, P, part, ppart,  \
+                                                    err, UU, stream);                        \
     return launch_one<S, true, U, PN, true>(A, lda, N, K, idx, sb, v2, P, part, ppart, err,     \
                                             UU, stream);                                     \
   }

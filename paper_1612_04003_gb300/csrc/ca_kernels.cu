@@ -1275,6 +1275,48 @@ int launch_reduce_chain(int grid, size_t smem, cudaStream_t st, const float* par
   return (int)e;
 }
 
+// Scaled FP16 Gram: for each row r of the N x K FP32 matrix A (row-major,
+// leading dimension lda, or 32-column panels), the power of two
+// rscale[r] = 2^(15 - e), where max_k |A[r][k]| = m 2^e with m in [0.5, 1):
+// the row times rscale[r] has its largest magnitude in [2^14, 2^15), inside
+// the FP16 range (largest finite 65504), and G_ij of the scaled rows is the
+// true one times rscale[i] rscale[j] exactly.  A zero or non-finite row gets
+// 1.  One warp per row.
+__global__ void __launch_bounds__(256)
+k_row_scale(const float* __restrict__ A, long long lda, long long N, long long K, int panel,
+            float* __restrict__ rscale) {
+  const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= N) return;
+  float m[4] = {0.f, 0.f, 0.f, 0.f};
+  if (panel) {  // element (r, 32 a + c) at A[(a N + r) 32 + c], zero past K
+    const long long natoms = (K + 31) / 32;
+#pragma unroll 4
+    for (long long a = 0; a < natoms; ++a)
+      m[a & 3] = fmaxf(m[a & 3], fabsf(__ldg(A + (a * N + r) * 32 + lane)));
+  } else {
+#pragma unroll 4
+    for (long long k = lane; k < K; k += 32)
+      m[(k >> 5) & 3] = fmaxf(m[(k >> 5) & 3], fabsf(__ldg(A + r * lda + k)));
+  }
+  float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    float sc = 1.f;
+    if (mx > 0.f && mx <= 3.4028234e38f) {
+      int e = 0;
+      frexpf(mx, &e);
+      sc = ldexpf(1.f, min(max(15 - e, -120), 120));
+    }
+    rscale[r] = sc;
+  }
+}
+
+void launch_row_scale(cudaStream_t st, const float* A, long long lda, long long N, long long K,
+                      bool panel, float* rscale) {
+  k_row_scale<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(A, lda, N, K, panel ? 1 : 0, rscale);
+}
+
 void launch_factor(cudaStream_t st, const double* R, const SolveArgs& sa, float2* Ginv,
                    unsigned* err) {
   k_factor<<<sa.s_cur, 256, 0, st>>>(R, sa, Ginv, err);

@@ -75,7 +75,12 @@ struct GramUpdate {
   const double* delta;  // their Delta
   double cU;            // v -= cU * Yprev^T Delta
   float2* v2;           // K entries as FP32 (hi, lo) pairs: read, updated in place
+  const float* rscale;  // scaled FP16 Gram: power-of-two multiplier of each row of A
 };
+
+// Scaled FP16 Gram: per-row power-of-two multipliers of A (k_row_scale).
+void launch_row_scale(cudaStream_t st, const float* A, long long lda, long long N, long long K,
+                      bool panel, float* rscale);
 
 // panel: A is stored as 32-column panels (k_pack_panels), else row-major with
 // leading dimension lda (16-byte aligned rows).  The fused update needs panels.

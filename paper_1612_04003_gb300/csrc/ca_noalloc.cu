@@ -86,6 +86,7 @@ extern "C" int ca_gram_project_noalloc(void* cuda_stream, int xfmt, int prec, co
   if (!A || !idx || !v || !G || !p || N < 1 || K < 1 || ld < K || sb < 1) return CA_ERR_ARG;
   if (sb > kMaxSb || K > kMaxK) return CA_ERR_UNSUPPORTED;  // beyond the fixed scratch
   if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32) return CA_ERR_ARG;
+  if (prec == CA_GRAM_FP16_SCALED) return CA_ERR_UNSUPPORTED;  // per-row scales: no fixed room
   if (prec < CA_GRAM_F64 || prec > CA_GRAM_BF16X3) return CA_ERR_ARG;
   const bool tc = (xfmt == CA_DENSE_F32) &&
                   (prec == CA_GRAM_TF32 || prec == CA_GRAM_FP32_EXACT || prec == CA_GRAM_BF16X3);

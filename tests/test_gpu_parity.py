@@ -9,7 +9,9 @@ Element-wise comparisons on the same seeded inputs.  Tolerances (relative
     BF16) drops b1 c1 and the split remainders, at most 3 * 2^-18 |x||y|:
     each Gram entry is within ~1e-5 sqrt(G_ii G_jj), and the iterates
     (measured 2e-7 .. 4e-6 on these cases) stay inside the FP32 bound;
-  * TF32 Gram (inputs rounded to 11 significant bits): each Gram entry is off
+  * TF32 Gram (inputs rounded to 11 significant bits) and the scaled FP16
+    Gram (each row times a power of two, rounded to FP16's 11 significant
+    bits; the scales come off exactly): each Gram entry is off
     by ~2^-11 relative, which perturbs the path of the iteration but not its
     fixed point (the projection and vectors stay FP32/FP64-accurate).  The
     deviation from the exact path is ~1e-3 after a few sweeps and decays as
@@ -33,7 +35,8 @@ TOL_TF32_SHORT = 2e-3
 
 
 def _tol(prec):
-    return {"3xtf32": TOL32, "bf16x3": TOL32, "tf32": TOL_TF32_SHORT}[prec]
+    return {"3xtf32": TOL32, "bf16x3": TOL32, "tf32": TOL_TF32_SHORT,
+            "fp16_scaled": TOL_TF32_SHORT}[prec]
 
 
 def _rel(a, b):
@@ -153,7 +156,7 @@ def mid32():
     return synth.dense_primal(d=512, n=8205, cond=1e3, seed=2)
 
 
-@pytest.mark.parametrize("prec", ["tf32", "3xtf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32", "bf16x3", "fp16_scaled"])
 @pytest.mark.parametrize("b,s", [(8, 1), (8, 4), (8, 13), (8, 16), (8, 17), (8, 32), (32, 4),
                                  (32, 8), (3, 7)])
 def test_primal_f32_tc(ctx, mid32, prec, b, s):
@@ -176,7 +179,7 @@ def test_primal_f32_tc(ctx, mid32, prec, b, s):
     assert _rel(z, z_ref) < tol
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3", "fp16_scaled"])
 @pytest.mark.parametrize("s", [8, 32])
 def test_primal_tf32_converged(ctx, mid32, s, prec):
     """TF32 Gram: once the iteration has converged (H = 2048, 32 sweeps of
@@ -206,7 +209,8 @@ def long_k_oracle(long_k):
 
 @pytest.mark.parametrize("prec,s", [("3xtf32", 16), ("3xtf32", 8), ("3xtf32", 32), ("3xtf32", 3),
                                     ("tf32", 16), ("tf32", 32), ("tf32", 4),
-                                    ("bf16x3", 16), ("bf16x3", 32), ("bf16x3", 5)])
+                                    ("bf16x3", 16), ("bf16x3", 32), ("bf16x3", 5),
+                                    ("fp16_scaled", 16), ("fp16_scaled", 32)])
 def test_primal_f32_long_k(ctx, long_k, long_k_oracle, prec, s):
     """Fused update (s*b <= 128) and the plain Gram pass with deep stage rings,
     against the oracle's Algorithm 1 (s = 1)."""
@@ -311,7 +315,7 @@ def test_dual_dense_f64_full_block(ctx, wide):
     assert _rel(a, X.T @ wstar - wide.y) < 1e-9
 
 
-@pytest.mark.parametrize("prec", ["tf32", "3xtf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32", "bf16x3", "fp16_scaled"])
 def test_dual_dense_f32_tc(ctx, prec):
     p = synth.dense_dual(d=1028, n=400, seed=6)
     X32 = p.X.astype(np.float32)
@@ -484,9 +488,11 @@ def gram_data():
 # terms per split (1000 * 2^-24 ~ 6e-5 worst case, 2e-5 used); TF32: 2^-11
 # input rounding; BF16x3: the dropped b1 c1 and split remainders, 3 * 2^-18
 # ~ 1.1e-5 (Cauchy-Schwarz over the sum), plus the same FP32 accumulation
-# allowance: 4e-5.
+# allowance: 4e-5; scaled FP16: each scaled element rounded to 11
+# significant bits (2^-11 relative), a product within ~2^-10, as TF32: 3e-3.
 @pytest.mark.parametrize("prec,tolG,tolp", [("f64", 1e-13, 1e-13), ("3xtf32", 2e-5, 1e-6),
-                                            ("tf32", 3e-3, 1e-6), ("bf16x3", 4e-5, 1e-6)])
+                                            ("tf32", 3e-3, 1e-6), ("bf16x3", 4e-5, 1e-6),
+                                            ("fp16_scaled", 3e-3, 1e-6)])
 @pytest.mark.parametrize("sb", [1, 8, 32, 100, 128, 129, 136, 256])
 def test_gram_project_kernel(ctx, gram_data, prec, tolG, tolp, sb):
     A, K, ld, v = gram_data
@@ -511,6 +517,45 @@ def test_gram_project_kernel(ctx, gram_data, prec, tolG, tolp, sb):
     assert Gerr.max() < tolG, Gerr.max()
     perr = np.abs(p.cpu().numpy() - p_ref) / (nrm * np.linalg.norm(v))
     assert perr.max() < tolp, perr.max()
+
+
+@pytest.mark.parametrize("prec", ["fp16_scaled", "bf16x3"])
+def test_gram_project_wide_magnitudes(ctx, prec):
+    """Rows whose magnitudes span 1e-12 .. 1e12 (far outside FP16's range of
+    6e-8 .. 65504 unscaled): the per-row power-of-two scaling keeps every
+    entry within the bound of the mode."""
+    rng = np.random.default_rng(5)
+    N, K = 96, 4104  # the last 4 columns zero (a ragged 32-column tail)
+    A = np.zeros((N, K), dtype=np.float32)
+    A[:, :4100] = (rng.standard_normal((N, 4100)) *
+                   (10.0 ** rng.uniform(-12, 12, size=(N, 1)))).astype(np.float32)
+    v = np.zeros(K)
+    v[:4100] = rng.standard_normal(4100)
+    idx = rng.permutation(N)[:64].astype(np.int32)
+    Ad, idx_d, v_d = _dev(A), _dev(idx), _dev(v)
+    G = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
+    p = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_gram_project(Ad, idx_d, v_d, G, p, prec=prec)
+    Y = A[idx].astype(np.float64)
+    G_ref = Y @ Y.T
+    nrm = np.sqrt(np.diag(G_ref))
+    Gerr = np.abs(G.cpu().numpy() - G_ref) / np.outer(nrm, nrm)
+    assert np.isfinite(G.cpu().numpy()).all()
+    assert Gerr.max() < (3e-3 if prec == "fp16_scaled" else 4e-5), Gerr.max()
+
+
+def test_noalloc_refuses_scaled_fp16(ctx, gram_data):
+    """The fixed-scratch entry has no room for per-row scales."""
+    import paper_1612_04003_gb300 as ca
+    A, K, ld, v = gram_data
+    Ad, v_d = _dev(A), _dev(v)
+    idx_d = _dev(np.arange(8, dtype=np.int32))
+    G = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    p = torch.zeros(8, dtype=torch.float64, device="cuda")
+    st = ctx._lib.ca_gram_project_noalloc(None, ca.CA_DENSE_F32, ca.CA_GRAM_FP16_SCALED,
+                                          Ad.data_ptr(), A.shape[0], K, ld, idx_d.data_ptr(), 8,
+                                          v_d.data_ptr(), G.data_ptr(), p.data_ptr())
+    assert st == ca.CA_ERR_UNSUPPORTED
 
 
 # ---------------------------------------------------------------------------
