@@ -493,7 +493,7 @@ def main():
     # s sweep (same data, fewer steps): s-step against s = 1
     sweep = []
     if not args.no_sweep:
-        for prec_ in ("3xtf32", "bf16x3", "tf32"):
+        for prec_ in ("3xtf32", "bf16x3", "tf32", "fp16_scaled"):
             for (b_, s_) in [(8, 1), (8, 4), (8, 8), (8, 16), (8, 32), (32, 1), (32, 4), (32, 8)]:
                 nst = 2 if s_ == 1 else 4
                 time_solves(ctx, XP, y, w, z, 1, stream, b=b_, s=s_, h=h_run, prec=prec_, panels=pan)
@@ -506,7 +506,7 @@ def main():
     roof_other = {}
     secondary = []
     if not args.no_sweep:
-        for prec_ in [p for p in ("3xtf32", "bf16x3", "tf32") if p != PREC]:
+        for prec_ in [p for p in ("3xtf32", "bf16x3", "tf32", "fp16_scaled") if p != PREC]:
             time_solves(ctx, XP, y, w, z, 1, stream, s=s_run, h=h_run, prec=prec_, panels=pan)
             ctx.ca_profile_enable(True)
             time_solves(ctx, XP, y, w, z, args.steps, stream, s=s_run, h=h_run, prec=prec_,

@@ -101,7 +101,28 @@ typedef struct {
   int prec;             /* ca_prec for the Gram of dense FP32 X                */
   int recompute_every;  /* a6 period in outer steps; 0 = never                  */
   long long h0;         /* index of the first block (resume point), >= 0      */
+  /* Stopping criterion (Sec. 5.1.5): every check_every outer steps (0 = no
+   * check) the full residual r of the current iterate is formed in one pass
+   * over X -- primal: (1/n) X (y - X^T w) - lambda w, the negative gradient;
+   * dual: X^T w - alpha - y, the dual residual up to sign; its rows at the
+   * sampled indices are each block subproblem's right-hand side -- and the
+   * solve ends once ||r||_2 <= tol ||r_0||_2 (tol = 0: never; the norms are
+   * still reported).  r_0 is taken at the starting iterate; a check waits
+   * for the GPU.  ca_solve_info reports what happened.                     */
+  double tol;
+  int check_every;
 } ca_opts;
+
+/* What the last solve on a context did. */
+typedef struct {
+  long long h_done;     /* block updates performed: H unless the stopping test
+                         * ended the solve (then a multiple of s); resume at
+                         * h0 + h_done                                          */
+  int checks;           /* full residuals formed after the start (the last one
+                         * at the end of the solve when it ran to H)          */
+  double res0;          /* ||r_0||_2 (0 without checks)                        */
+  double res;           /* ||r||_2 at the last check                           */
+} ca_info;
 
 /* Dual CSR input: CSR of X^T with n rows (samples) and d columns (features).
  * rowptr has n+1 entries (int64), col and val have rowptr[n] entries; column
@@ -162,6 +183,10 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
  * out may be host or device memory.  Errors: CA_ERR_ARG, CA_ERR_CUDA. */
 int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long long H, int b,
                       long long N, int* out);
+
+/* Outcome of the last ca_bcd_solve / ca_bdcd_solve on ctx (after it
+ * returned CA_OK).  Errors: CA_ERR_ARG. */
+int ca_solve_info(const ca_ctx* ctx, ca_info* out);
 
 /* Steps a2+a3 alone for given sampled rows (Alg. 2 / 4, "compute the Gram
  * matrix"): for the sb rows idx[0..sb) of the N x K row-major matrix A

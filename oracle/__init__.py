@@ -12,7 +12,9 @@ with the CUDA library in ``paper_1612_04003_gb300`` and never imports it.
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed form vs a library solve, one-step exactness at b = d / b' = n, s-step
 equivalence, monotone objectives, duality identity, the sampler's generator
-against numpy's Philox, Floyd's algorithm by exhaustive enumeration).
+against numpy's Philox, Floyd's algorithm by exhaustive enumeration; the
+residuals of the stopping test against finite differences of the objectives,
+their zeros at the optimum and on the block just solved).
 """
 from __future__ import annotations
 
@@ -248,3 +250,72 @@ def bdcd(X, y, lam, b, H, seed, h0=0, recompute_every=0, alpha0=None):
                             recompute_every, _ptr(alpha, ctypes.c_double),
                             _ptr(w, ctypes.c_double)), "bdcd")
     return alpha, w
+
+
+# --------------------------------------------------------------------------
+# Stopping criterion (Sec. 5.1.5): the full primal / dual residual
+# --------------------------------------------------------------------------
+def primal_residual(X, y, lam, w) -> np.ndarray:
+    """The full primal residual of Sec. 5.1.5, the d-vector whose rows at the
+    sampled indices are the right-hand side of the BCD subproblem:
+    -lam w - (1/n) X (X^T w - y), the negative gradient of the primal objective."""
+    X, y, w = _f64(X), _f64(y), _f64(w)
+    n = X.shape[1]
+    return -lam * w - X @ (X.T @ w - y) / n
+
+
+def _xt_times(X, w) -> np.ndarray:
+    """X^T w for the d x n matrix X, or for X given by the CSR of X^T."""
+    if isinstance(X, CSR):
+        out = np.zeros(X.n)
+        for i in range(X.n):
+            a, b = X.rowptr[i], X.rowptr[i + 1]
+            out[i] = X.val[a:b] @ w[X.col[a:b]]
+        return out
+    return _f64(X).T @ w
+
+
+def dual_residual(X, y, alpha, w) -> np.ndarray:
+    """The full dual residual of Sec. 5.1.5, the n-vector -X^T w + alpha + y
+    (X dense d x n or the CSR of X^T), whose rows at the sampled indices are
+    the BDCD subproblem's right-hand side."""
+    return -_xt_times(X, _f64(w)) + _f64(alpha) + _f64(y)
+
+
+def ca_bcd_stopped(X, y, lam, b, s, H, seed, tol, check_every):
+    """Algorithm 2 with the stopping test of Sec. 5.1.5: after every
+    check_every outer steps (s block updates each) the full primal residual;
+    the run ends once ||r|| <= tol ||r_0|| (tol = 0: never), and at H.
+    Returns (w, h_done, ||r_0||, [||r|| after each check])."""
+    X, y = _f64(X), _f64(y)
+    w = np.zeros(X.shape[0])
+    r0 = float(np.linalg.norm(primal_residual(X, y, lam, w)))
+    h, norms = 0, []
+    while h < H:
+        m = min(check_every * s, H - h)
+        w, _ = ca_bcd(X, y, lam, b, s, m, seed, h0=h, w0=w)
+        h += m
+        norms.append(float(np.linalg.norm(primal_residual(X, y, lam, w))))
+        if h < H and tol > 0 and norms[-1] <= tol * r0:
+            break
+    return w, h, r0, norms
+
+
+def ca_bdcd_stopped(X, y, lam, b, s, H, seed, tol, check_every):
+    """Algorithm 4 with the stopping test of Sec. 5.1.5 on the full dual
+    residual (as ca_bcd_stopped).  Returns (alpha, w, h_done, ||r_0||,
+    [||r|| after each check])."""
+    A = _as_csr(X)
+    y = _f64(y)
+    alpha = np.zeros(A.n)
+    w = np.zeros(A.d)
+    r0 = float(np.linalg.norm(dual_residual(A, y, alpha, w)))
+    h, norms = 0, []
+    while h < H:
+        m = min(check_every * s, H - h)
+        alpha, w = ca_bdcd(A, y, lam, b, s, m, seed, h0=h, alpha0=alpha)
+        h += m
+        norms.append(float(np.linalg.norm(dual_residual(A, y, alpha, w))))
+        if h < H and tol > 0 and norms[-1] <= tol * r0:
+            break
+    return alpha, w, h, r0, norms

@@ -43,7 +43,13 @@ PREC = {"f64": CA_GRAM_F64, "fp32_exact": CA_GRAM_FP32_EXACT, "3xtf32": CA_GRAM_
 class ca_opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("s", ctypes.c_int), ("H", ctypes.c_longlong),
                 ("lam", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("prec", ctypes.c_int),
-                ("recompute_every", ctypes.c_int), ("h0", ctypes.c_longlong)]
+                ("recompute_every", ctypes.c_int), ("h0", ctypes.c_longlong),
+                ("tol", ctypes.c_double), ("check_every", ctypes.c_int)]
+
+
+class ca_info(ctypes.Structure):
+    _fields_ = [("h_done", ctypes.c_longlong), ("checks", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double)]
 
 
 class ca_csr(ctypes.Structure):
@@ -93,6 +99,8 @@ def load():
     lib.ca_last_error.argtypes = [vp]
     lib.ca_last_error.restype = ctypes.c_char_p
     lib.ca_gram_project.argtypes = [vp, i32, i32, vp, i64, i64, i64, vp, i32, vp, vp, vp]
+    lib.ca_solve_info.argtypes = [vp, ctypes.POINTER(ca_info)]
+    lib.ca_solve_info.restype = i32
     lib.ca_gram_project.restype = i32
     lib.ca_pack_panels.argtypes = [vp, vp, i64, i64, i64, vp]
     lib.ca_pack_panels.restype = i32
@@ -186,13 +194,23 @@ class Context:
         return self._lib.ca_last_error(self.handle).decode()
 
     @staticmethod
-    def _opts(b, s, H, lam, seed, prec, recompute_every, h0):
+    def _opts(b, s, H, lam, seed, prec, recompute_every, h0, tol=0.0, check_every=0):
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         return ca_opts(int(b), int(s), int(H), float(lam), int(seed), p, int(recompute_every),
-                       int(h0))
+                       int(h0), float(tol), int(check_every))
+
+    def solve_info(self) -> dict:
+        """Outcome of the last solve: block updates done (h_done), number of
+        full-residual checks, ||r_0|| and ||r|| at the last check."""
+        info = ca_info()
+        st = self._lib.ca_solve_info(self.handle, ctypes.byref(info))
+        if st != CA_OK:
+            raise CaError(st, "ca_solve_info")
+        return {"h_done": info.h_done, "checks": info.checks, "res0": info.res0, "res": info.res}
 
     def ca_bcd_solve(self, X, y, w, z=None, *, b, s=1, H, lam, seed=42, prec="tf32",
-                     recompute_every=0, h0=0, n=None, ld=None, panels=None):
+                     recompute_every=0, h0=0, n=None, ld=None, panels=None, tol=0.0,
+                     check_every=0):
         """Primal CA-BCD: w (in: w0, out: w_H) and optionally z = X^T w_H.
         X is d x ld (ld = X.shape[1]); n (default ld) columns are used.
         panels=(d, n): X holds the 32-column panels of a d x n matrix
@@ -200,7 +218,7 @@ class Context:
         for a in (y, w) + ((z,) if z is not None else ()):
             if not _dtype_is_f64(a):
                 raise TypeError("y, w, z must be float64")
-        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0)
+        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0, tol, check_every)
         if panels is not None:
             d, n = (int(v) for v in panels)
             xf, ld = CA_DENSE_F32_PANELS, 0
@@ -216,14 +234,15 @@ class Context:
         return w, z
 
     def ca_bdcd_solve(self, XT, y, alpha, w, *, b, s=1, H, lam, seed=42, prec="tf32",
-                      recompute_every=0, h0=0, d=None, ld=None, panels=None):
+                      recompute_every=0, h0=0, d=None, ld=None, panels=None, tol=0.0,
+                      check_every=0):
         """Dual CA-BDCD.  XT is X^T (n x d, dense), a (rowptr, col, val) CSR
         triple of X^T (then d must be given), or with panels=(n, d) the
         32-column panels of X^T (ca_pack_panels)."""
         for a in (y, alpha, w):
             if not _dtype_is_f64(a):
                 raise TypeError("y, alpha, w must be float64")
-        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0)
+        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0, tol, check_every)
         if panels is not None:
             n, dd = (int(v) for v in panels)
             st = self._lib.ca_bdcd_solve(self.handle, CA_DENSE_F32_PANELS, _ptr(XT), dd, n, 0,

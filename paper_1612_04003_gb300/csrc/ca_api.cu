@@ -40,8 +40,9 @@ struct ca_ctx {
   unsigned* d_err = nullptr;     // device error word
   unsigned* d_ticket = nullptr;  // count of the reducing CTAs of the reduce/solve kernel
                                  // (d_err + 32; both cleared where a call starts)
-  unsigned* h_err = nullptr;     // pinned copy
+  unsigned* h_err = nullptr;     // pinned copy (64 bytes: error word; residual at +32)
   Profile prof;
+  ca_info info{};                // outcome of the last solve
   char last_error[256] = {0};    // text of the last failing CUDA call
 };
 
@@ -167,6 +168,7 @@ int check_opts(const ca_opts* o, long long N) {
   if (o->b < 1 || (long long)o->b > N || o->s < 1 || o->H < 1 || o->h0 < 0) return CA_ERR_ARG;
   if (!(o->lam > 0.0) || !std::isfinite(o->lam)) return CA_ERR_ARG;
   if (o->recompute_every < 0) return CA_ERR_ARG;
+  if (o->check_every < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol)) return CA_ERR_ARG;
   if (o->prec < CA_GRAM_F64 || o->prec > CA_GRAM_FP16_SCALED) return CA_ERR_ARG;
   if (N > 2147483647LL) return CA_ERR_UNSUPPORTED;
   if (o->b > kMaxB) return CA_ERR_UNSUPPORTED;
@@ -191,7 +193,30 @@ struct DenseProblem {
   // recompute of v: v = c0 * y0 + c1 * sum_r A[r] x[r]
   const double* y0;
   double c0, c1;
+  // stopping test: N doubles of scratch (zero between uses) and one accumulator
+  double* rq = nullptr;
+  double* racc = nullptr;
 };
+
+// ||r||_2 of the current iterate, r = cP A v - cI x - cY y (Sec. 5.1.5):
+// one pass over A, then a wait for the GPU.
+int full_residual(ca_ctx* ctx, const void* A, bool f64, bool panel, long long lda, long long N,
+                  long long K, const double* v, const float2* v2, const ca_csr_dev* csr,
+                  double* rq, double* racc, const double* x, const double* yv, double cP,
+                  double cI, double cY, double* out) {
+  CA_TRY_CUDA(cudaMemsetAsync(racc, 0, sizeof(double), ctx->stream));
+  prof_mark(ctx, PC_OTHER);
+  launch_residual(ctx->stream, ctx->num_sms, A, f64, panel, lda, N, K, v, v2, csr, rq, x, yv, cP,
+                  cI, cY, racc);
+  prof_mark(ctx, PC_OTHER);
+  ctx->prof.kernel_launches += 2;
+  CA_TRY_CUDA(cudaGetLastError());
+  double* h = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->h_err) + 32);
+  CA_TRY_CUDA(cudaMemcpyAsync(h, racc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+  *out = std::sqrt(*h);
+  return CA_OK;
+}
 
 int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const double* y0,
                      double c0, double c1) {
@@ -368,6 +393,17 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   // last step, and before a due recomputation it runs on its own.
   const bool fuse = g.tc && g.sbp <= 128 && pb.panel;
   auto due = [&](long long k) { return o->recompute_every > 0 && (k + 1) % o->recompute_every == 0; };
+  // stopping test (Sec. 5.1.5)
+  const bool chk = o->check_every > 0;
+  ctx->info = ca_info{H, 0, 0.0, 0.0};
+  auto residual = [&](double* out) {
+    return full_residual(ctx, pb.A, pb.xfmt == CA_DENSE_F64, pb.panel, pb.lda, pb.N, K, pb.v,
+                         pb.v2, nullptr, pb.rq, pb.racc, pb.x, pb.yv, pb.cP, pb.cI, pb.cY, out);
+  };
+  if (chk) {
+    CA_TRY(residual(&ctx->info.res0));
+    ctx->info.res = ctx->info.res0;
+  }
   bool pending = false;  // an update (prev_*) not yet applied
   const int* prev_idx = nullptr;
   int prev_sb = 0;
@@ -417,10 +453,25 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     prev_idx = idx;
     prev_sb = sb;
     prev_delta = delta;
+    if (chk && (k + 1) % o->check_every == 0 && k + 1 < n_outer) {
+      // the deferred update of this step first: the residual needs v current
+      CA_TRY(update_alone());
+      if (due(k)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
+      CA_TRY(residual(&ctx->info.res));
+      ++ctx->info.checks;
+      if (o->tol > 0.0 && ctx->info.res <= o->tol * ctx->info.res0) {
+        ctx->info.h_done = (k + 1) * (long long)s;
+        return CA_OK;
+      }
+    }
   }
   if (pending) {
     CA_TRY(update_alone());
     if (due(n_outer - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
+  }
+  if (chk) {
+    CA_TRY(residual(&ctx->info.res));
+    ++ctx->info.checks;
   }
   return CA_OK;
 }
@@ -586,6 +637,7 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   if (tc && !pre) need += align256(panel_bytes(d, n)) + 256;
   const bool f16 = tc && o->prec == CA_GRAM_FP16_SCALED;
   if (f16) need += align256((size_t)d * 4) + 256;
+  if (o->check_every > 0) need += align256((size_t)d * 8) + 512;
   if (y_host) need += align256((size_t)n * 8);
   if (w_host) need += align256((size_t)d * 8);
   if (z_host) need += align256((size_t)n * 8);
@@ -621,7 +673,14 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   float2* rho2 = cv.take<float2>((size_t)(n + 31) / 32 * 32);
   float2* w2s = cv.take<float2>((size_t)d);
   int* idx = cv.take<int>((size_t)o->H * o->b);
-  char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
+  double* rq = nullptr;  // stopping test: N doubles (zero between uses) and an accumulator
+  double* racc = nullptr;
+  if (o->check_every > 0) {
+    rq = cv.take<double>((size_t)d);
+    racc = cv.take<double>(1);
+    CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)d * 8, ctx->stream));
+  }
+  char* work = static_cast<char*>(ctx->arena) + align256(cv.off);  // after every carve above
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
 
   DenseProblem pb;
@@ -634,6 +693,8 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   pb.v = rho;
   pb.v2 = rho2;
   pb.rscale = rsc;
+  pb.rq = rq;
+  pb.racc = racc;
   pb.x = wd;
   pb.x2 = w2s;
   pb.yv = nullptr;
@@ -696,6 +757,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     // row pairs of the transposed Rs)
     const size_t sbp = (size_t)(sbm + 31) / 32 * 32;
     need += 2 * align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
+    if (o->check_every > 0) need += align256((size_t)n * 8) + 512;
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
     bool st;
@@ -712,6 +774,18 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     float2* Ginv = cv.take<float2>(sbp * CA_FAST_B);
     float2* Rs = cv.take<float2>(sbp * sbp);
     CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
+    double* rq = nullptr;
+    double* racc = nullptr;
+    if (o->check_every > 0) {  // stopping test scratch (zero between uses)
+      rq = cv.take<double>((size_t)n);
+      racc = cv.take<double>(1);
+      CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)n * 8, ctx->stream));
+    }
+    const ca_csr_dev cdev{rp, col, val};
+    auto residual = [&](double* out) {  // X^T w - alpha - y (Sec. 5.1.5)
+      return full_residual(ctx, nullptr, false, false, 0, n, d, wd, nullptr, &cdev, rq, racc, ad,
+                           yd, 1.0, 1.0, 1.0, out);
+    };
     auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
       k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
       k_scatter_csr<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, nullptr, n, d,
@@ -724,6 +798,11 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     CA_TRY_CUDA(cudaGetLastError());
     const int b = o->b, s = o->s;
     const long long n_outer = (o->H + s - 1) / s;
+    ctx->info = ca_info{o->H, 0, 0.0, 0.0};
+    if (o->check_every > 0) {
+      CA_TRY(residual(&ctx->info.res0));
+      ctx->info.res = ctx->info.res0;
+    }
     for (long long k = 0; k < n_outer; ++k) {
       const int sk = (int)std::min<long long>(s, o->H - (long long)s * k);
       const int sb = sk * b;
@@ -751,6 +830,14 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       ctx->prof.kernel_launches += 4;
       CA_TRY_CUDA(cudaGetLastError());
       if (o->recompute_every > 0 && (k + 1) % o->recompute_every == 0) recompute();
+      if (o->check_every > 0 && ((k + 1) % o->check_every == 0 || k + 1 == n_outer)) {
+        CA_TRY(residual(&ctx->info.res));
+        ++ctx->info.checks;
+        if (k + 1 < n_outer && o->tol > 0.0 && ctx->info.res <= o->tol * ctx->info.res0) {
+          ctx->info.h_done = (k + 1) * (long long)s;
+          break;
+        }
+      }
     }
     if (a_host)
       CA_TRY_CUDA(cudaMemcpyAsync(alpha, ad, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -778,6 +865,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   if (tc && !pre) need += align256(panel_bytes(n, d)) + 256;
   const bool f16 = tc && o->prec == CA_GRAM_FP16_SCALED;
   if (f16) need += align256((size_t)n * 4) + 256;
+  if (o->check_every > 0) need += align256((size_t)n * 8) + 512;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
   bool st;
@@ -808,7 +896,14 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   float2* w2 = cv.take<float2>((size_t)(d + 31) / 32 * 32);
   float2* a2s = cv.take<float2>((size_t)n);
   int* idx = cv.take<int>((size_t)o->H * o->b);
-  char* work = static_cast<char*>(ctx->arena) + align256(cv.off);
+  double* rq = nullptr;  // stopping test: N doubles (zero between uses) and an accumulator
+  double* racc = nullptr;
+  if (o->check_every > 0) {
+    rq = cv.take<double>((size_t)n);
+    racc = cv.take<double>(1);
+    CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)n * 8, ctx->stream));
+  }
+  char* work = static_cast<char*>(ctx->arena) + align256(cv.off);  // after every carve above
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
   DenseProblem pb;
   pb.xfmt = xf;
@@ -820,6 +915,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   pb.v = wd;
   pb.v2 = w2;
   pb.rscale = rsc;
+  pb.rq = rq;
+  pb.racc = racc;
   pb.x = ad;
   pb.x2 = a2s;
   pb.yv = yd;
@@ -917,6 +1014,12 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(R, g.sbp, sb, G);
   CA_TRY_CUDA(cudaGetLastError());
   return finish(ctx);
+}
+
+int ca_solve_info(const ca_ctx* ctx, ca_info* out) {
+  if (!ctx || !out) return CA_ERR_ARG;
+  *out = ctx->info;
+  return CA_OK;
 }
 
 int ca_selftest_wait_timeout(ca_ctx* ctx, long long limit_ns) {

@@ -4,6 +4,7 @@
 // rows are sampled (primal: A = X, N = d, K = n; dual: A = X^T, N = n, K = d),
 // Y = the s'*b sampled rows of A, v the K-vector the Gram pass projects on
 // (primal: rho = y - z with z = X^T w; dual: w).
+#include <algorithm>
 #include <type_traits>
 
 #include "ca_kernels.cuh"
@@ -1273,6 +1274,149 @@ int launch_reduce_chain(int grid, size_t smem, cudaStream_t st, const float* par
   else
     e = cudaErrorInvalidValue;
   return (int)e;
+}
+
+// ---------------------------------------------------------------------------
+// Stopping criterion (Sec. 5.1.5): the full residual of the current iterate,
+// r = cP A v - cI x - cY y over all N rows of A, whose rows at the sampled
+// indices are the right-hand side of each block subproblem.  Primal (A = X,
+// v = rho = y - X^T w, x = w): (1/n) X rho - lambda w, the negative gradient
+// of the objective; dual (A = X^T, v = w, x = alpha): X^T w - alpha - y, the
+// dual residual up to its sign.
+// ---------------------------------------------------------------------------
+
+// q[r] += sum_k A[r][k] v[k] over the 32-column chunks [a0, a1) of this CTA's
+// split (blockIdx.y); 8 warps x 8 rows per CTA, lane c takes column 32 a + c
+// (a coalesced 128-byte row segment per load, panels or row-major).  FP32 A:
+// products with the (hi, lo) FP32 split of v, FP32 sums folded every 8 chunks
+// into a compensated pair (v2 zero-padded to a multiple of 32); FP64 A: FP64.
+// v and v2 change between calls (the solves update them): read through L2
+// (ld.global.cg), never the non-coherent read-only path; A is constant.
+// q starts at zero (k_residual_norm clears it after use).
+template <typename T, bool PANEL>
+__global__ void __launch_bounds__(256)
+k_rowdot_dense(const T* __restrict__ A, long long lda, long long N, long long K,
+               const double* __restrict__ v, const float2* __restrict__ v2,
+               long long chunks_per_split, double* __restrict__ q) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r0 = (long long)blockIdx.x * 64 + warp * 8;
+  const long long natoms = (K + 31) / 32;
+  const long long a0 = (long long)blockIdx.y * chunks_per_split;
+  const long long a1 = min(natoms, a0 + chunks_per_split);
+  if constexpr (sizeof(T) == 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long a = a0; a < a1; ++a) {
+      const long long k = a * 32 + lane;
+      const double vk = k < K ? __ldcg(v + k) : 0.0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (r0 + j < N && k < K) acc[j] = fma((double)__ldg(A + (r0 + j) * lda + k), vk, acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      double t = acc[j];
+      for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0 && r0 + j < N) atomicAdd(q + r0 + j, t);
+    }
+  } else {
+    float pacc[8], hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pacc[j] = hi[j] = lo[j] = 0.f;
+    for (long long a = a0; a < a1; ++a) {
+      const float2 vk = __ldcg(v2 + a * 32 + lane);
+      const long long k = a * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const long long r = r0 + j;
+        float x = 0.f;
+        if (r < N) {
+          if constexpr (PANEL) x = __ldg(reinterpret_cast<const float*>(A) + (a * N + r) * 32 + lane);
+          else if (k < K) x = __ldg(reinterpret_cast<const float*>(A) + r * lda + k);
+        }
+        pacc[j] = fmaf(x, vk.x, fmaf(x, vk.y, pacc[j]));
+      }
+      if (((a - a0) & 7) == 7) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          comp_add(hi[j], lo[j], pacc[j]);
+          pacc[j] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      comp_add(hi[j], lo[j], pacc[j]);
+      float2 t = df_norm(hi[j], lo[j]);
+      for (int o = 16; o; o >>= 1)
+        t = df_add(t, make_float2(__shfl_xor_sync(0xffffffffu, t.x, o),
+                                  __shfl_xor_sync(0xffffffffu, t.y, o)));
+      if (lane == 0 && r0 + j < N) atomicAdd(q + r0 + j, (double)t.x + (double)t.y);
+    }
+  }
+}
+
+// q[r] = (row r of the CSR matrix) . v, one warp per row, FP64 sums.
+__global__ void __launch_bounds__(256)
+k_rowdot_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
+             const float* __restrict__ val, long long N, const double* __restrict__ v,
+             double* __restrict__ q) {
+  const long long r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= N) return;
+  double acc = 0.0;
+  for (long long p = rowptr[r] + lane; p < rowptr[r + 1]; p += 32)
+    acc = fma((double)val[p], __ldcg(v + col[p]), acc);
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) q[r] = acc;
+}
+
+// *out += sum_r (cP q[r] - cI x[r] - cY y[r])^2 (FP64; y may be null), and
+// q is cleared for the next use.
+__global__ void __launch_bounds__(256)
+k_residual_norm(double* __restrict__ q, const double* __restrict__ x, const double* __restrict__ y,
+                long long N, double cP, double cI, double cY, double* __restrict__ out) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (long long r = (long long)blockIdx.x * 256 + threadIdx.x; r < N;
+       r += (long long)gridDim.x * 256) {
+    double t = cP * q[r] - cI * x[r];
+    if (y) t -= cY * y[r];
+    acc = fma(t, t, acc);
+    q[r] = 0.0;
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    atomicAdd(out, t);
+  }
+}
+
+void launch_residual(cudaStream_t st, int num_sms, const void* A, bool f64, bool panel,
+                     long long lda, long long N, long long K, const double* v, const float2* v2,
+                     const ca_csr_dev* csr, double* q, const double* x, const double* y,
+                     double cP, double cI, double cY, double* out) {
+  if (csr) {
+    k_rowdot_csr<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(csr->rowptr, csr->col, csr->val, N, v, q);
+  } else {
+    const long long natoms = (K + 31) / 32, gx = (N + 63) / 64;
+    const long long ys = std::max(1LL, std::min<long long>(natoms, (4LL * num_sms + gx - 1) / gx));
+    const long long cps = (natoms + ys - 1) / ys;
+    const dim3 grid((unsigned)gx, (unsigned)((natoms + cps - 1) / cps));
+    if (f64)
+      k_rowdot_dense<double, false><<<grid, 256, 0, st>>>(static_cast<const double*>(A), lda, N, K,
+                                                         v, v2, cps, q);
+    else if (panel)
+      k_rowdot_dense<float, true><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K, v,
+                                                       v2, cps, q);
+    else
+      k_rowdot_dense<float, false><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K,
+                                                        v, v2, cps, q);
+  }
+  const long long rg = std::max(1LL, std::min<long long>((N + 255) / 256, 2LL * num_sms));
+  k_residual_norm<<<(unsigned)rg, 256, 0, st>>>(q, x, y, N, cP, cI, cY, out);
 }
 
 // Scaled FP16 Gram: for each row r of the N x K FP32 matrix A (row-major,

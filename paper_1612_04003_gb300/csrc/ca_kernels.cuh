@@ -78,6 +78,20 @@ struct GramUpdate {
   const float* rscale;  // scaled FP16 Gram: power-of-two multiplier of each row of A
 };
 
+// Stopping criterion: *out += ||cP A v - cI x - cY y||^2 over the N rows of
+// A (dense: row-major FP64 / FP32 or FP32 panels, v2 the FP32 split of v for
+// FP32 A; csr: rows of the CSR matrix, FP64 v).  q: N doubles, zero on entry
+// and on return.  *out must be zeroed by the caller.
+struct ca_csr_dev {
+  const long long* rowptr;
+  const int* col;
+  const float* val;
+};
+void launch_residual(cudaStream_t st, int num_sms, const void* A, bool f64, bool panel,
+                     long long lda, long long N, long long K, const double* v, const float2* v2,
+                     const ca_csr_dev* csr, double* q, const double* x, const double* y,
+                     double cP, double cI, double cY, double* out);
+
 // Scaled FP16 Gram: per-row power-of-two multipliers of A (k_row_scale).
 void launch_row_scale(cudaStream_t st, const float* A, long long lda, long long N, long long K,
                       bool panel, float* rscale);

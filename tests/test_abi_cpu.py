@@ -33,13 +33,14 @@ def test_status_strings(lib):
 
 
 def test_null_arguments_rejected_without_gpu(lib):
-    o = ca.ca_opts(4, 4, 200, 1e-3, 42, ca.CA_GRAM_F64, 0, 0)
+    o = ca.ca_opts(4, 4, 200, 1e-3, 42, ca.CA_GRAM_F64, 0, 0, 0.0, 0)
     assert lib.ca_bcd_solve(None, 0, None, 64, 1024, 1024, None, ctypes.byref(o), None, None) == \
         ca.CA_ERR_ARG
     assert lib.ca_bdcd_solve(None, 0, None, 64, 1024, 64, None, ctypes.byref(o), None, None) == \
         ca.CA_ERR_ARG
     assert lib.ca_sample_indices(None, 1, 0, 1, 1, 1, None) == ca.CA_ERR_ARG
     assert lib.ca_profile_enable(None, 1) == ca.CA_ERR_ARG
+    assert lib.ca_solve_info(None, None) == ca.CA_ERR_ARG
     lib.ca_bcd_destroy(None)  # no-op
 
 
@@ -50,8 +51,25 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         ca.load()
 
 
-def test_opts_layout_matches_header():
-    # b, s (int), H (long long), lam (double), seed (u64), prec, recompute_every (int), h0
-    assert ctypes.sizeof(ca.ca_opts) == 4 + 4 + 8 + 8 + 8 + 4 + 4 + 8
-    assert ca.ca_opts.H.offset == 8 and ca.ca_opts.lam.offset == 16
-    assert ca.ca_opts.prec.offset == 32 and ca.ca_opts.h0.offset == 40
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof of a header struct, from a C program built with gcc."""
+    import os
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"ca_bcd.h\"\n"
+                   f"int main(void) {{\n  printf(\"%zu\\n\", sizeof({struct}));\n{body}  return 0;\n}}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+@pytest.mark.parametrize("py,c", [(lambda: ca.ca_opts, "ca_opts"), (lambda: ca.ca_info, "ca_info")])
+def test_struct_layout_matches_header(tmp_path, py, c):
+    cls = py()
+    names = [f[0] for f in cls._fields_]
+    got = _c_layout(tmp_path, c, names)
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f in names]

@@ -559,6 +559,101 @@ def test_noalloc_refuses_scaled_fp16(ctx, gram_data):
 
 
 # ---------------------------------------------------------------------------
+# Stopping test (Sec. 5.1.5): full residuals every check_every outer steps,
+# the early end once ||r|| <= tol ||r_0||
+# ---------------------------------------------------------------------------
+def _tol_between(norms, r0, gap=1.1):
+    """A tolerance whose first crossing is unambiguous: between two checks
+    j, j+1 with norms[j+1] < norms[j] / gap and every earlier norm above."""
+    for j in range(1, len(norms) - 1):
+        if norms[j + 1] * gap < norms[j] and min(norms[:j + 1]) > norms[j + 1] * gap:
+            return float(np.sqrt(norms[j] * norms[j + 1]) / r0), j + 1
+    raise AssertionError("no clear crossing")
+
+
+def test_stopping_primal_f64(ctx, tiny):
+    X, y, lam = tiny.X, tiny.y, 1e-3
+    kw = dict(b=4, s=4, H=400, seed=42)
+    _, _, r0, norms = oracle.ca_bcd_stopped(X, y, lam, tol=0.0, check_every=5, **kw)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(_dev(X), _dev(y), w, lam=lam, prec="f64", check_every=5, **kw)
+    info = ctx.solve_info()
+    assert info["h_done"] == 400 and info["checks"] == len(norms) == 20
+    assert abs(info["res0"] - r0) < 1e-12 * r0
+    assert abs(info["res"] - norms[-1]) < 1e-8 * norms[-1]
+    tol, jstop = _tol_between(norms, r0)
+    w_ref, h_ref, _, _ = oracle.ca_bcd_stopped(X, y, lam, tol=tol, check_every=5, **kw)
+    assert h_ref == 20 * (jstop + 1)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(_dev(X), _dev(y), w, lam=lam, prec="f64", check_every=5, tol=tol, **kw)
+    info = ctx.solve_info()
+    assert info["h_done"] == h_ref and info["checks"] == jstop + 1
+    assert _rel(w, w_ref) < TOL64
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "3xtf32"])
+def test_stopping_primal_tensor_core(ctx, mid32, prec):
+    """The fused tensor-core path (b = 8, s = 16, s*b = 128): the deferred
+    update is applied before each check.  The residual of the GPU's own
+    iterate, formed on the CPU in FP64, checks the residual pass itself."""
+    X32 = mid32.X[:, :8192]
+    X64, y = X32.astype(np.float64), mid32.y[:8192]
+    lam = 1e-4
+    kw = dict(b=8, s=16, H=1024, seed=7)
+    _, _, r0, norms = oracle.ca_bcd_stopped(X64, y, lam, tol=0.0, check_every=2, **kw)
+    w = torch.zeros(512, dtype=torch.float64, device="cuda")
+    Xd, yd = _dev(X32), _dev(y)
+    ctx.ca_bcd_solve(Xd, yd, w, lam=lam, prec=prec, check_every=2, **kw)
+    info = ctx.solve_info()
+    assert info["h_done"] == 1024 and info["checks"] == len(norms) == 32
+    assert abs(info["res0"] - r0) < 1e-6 * r0
+    r_own = np.linalg.norm(oracle.primal_residual(X64, y, lam, w.cpu().numpy()))
+    assert abs(info["res"] - r_own) < 1e-4 * r_own
+    assert abs(info["res"] - norms[-1]) < 1e-3 * norms[-1]
+    tol, jstop = _tol_between(norms, r0, gap=1.3)
+    w_ref, h_ref, _, _ = oracle.ca_bcd_stopped(X64, y, lam, tol=tol, check_every=2, **kw)
+    w = torch.zeros(512, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(Xd, yd, w, lam=lam, prec=prec, check_every=2, tol=tol, **kw)
+    info = ctx.solve_info()
+    assert info["h_done"] == h_ref and info["checks"] == jstop + 1
+    assert _rel(w, w_ref) < TOL32
+
+
+def test_stopping_dual_dense_and_csr(ctx, wide, sparse_small):
+    lam = 1e-2
+    X, y = wide.X, wide.y
+    d, n = X.shape
+    kw = dict(b=6, s=3, H=150, seed=9)
+    _, _, _, r0, norms = oracle.ca_bdcd_stopped(X, y, lam, tol=0.0, check_every=5, **kw)
+    a = torch.zeros(n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(d, dtype=torch.float64, device="cuda")
+    XT = _dev(np.ascontiguousarray(X.T))
+    ctx.ca_bdcd_solve(XT, _dev(y), a, w, lam=lam, prec="f64", check_every=5, **kw)
+    info = ctx.solve_info()
+    assert info["h_done"] == 150 and info["checks"] == len(norms) == 10
+    assert abs(info["res0"] - r0) < 1e-12 * r0 and abs(info["res"] - norms[-1]) < 1e-8 * norms[-1]
+    tol, jstop = _tol_between(norms, r0)
+    a_ref, w_ref, h_ref, _, _ = oracle.ca_bdcd_stopped(X, y, lam, tol=tol, check_every=5, **kw)
+    a.zero_()
+    w.zero_()
+    ctx.ca_bdcd_solve(XT, _dev(y), a, w, lam=lam, prec="f64", check_every=5, tol=tol, **kw)
+    info = ctx.solve_info()
+    assert info["h_done"] == h_ref and _rel(a, a_ref) < TOL64 and _rel(w, w_ref) < TOL64
+    # sparse dual (CSR of X^T)
+    sp = sparse_small
+    A = oracle.CSR(sp.rowptr, sp.col, sp.val.astype(np.float64), sp.d)
+    kw = dict(b=8, s=8, H=192, seed=4)
+    _, _, _, r0, norms = oracle.ca_bdcd_stopped(A, sp.y, 1e-3, tol=0.0, check_every=3, **kw)
+    a = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(sp.d, dtype=torch.float64, device="cuda")
+    csr = (_dev(sp.rowptr), _dev(sp.col), _dev(sp.val))
+    ctx.ca_bdcd_solve(csr, _dev(sp.y), a, w, lam=1e-3, d=sp.d, check_every=3, **kw)
+    info = ctx.solve_info()
+    assert info["h_done"] == 192 and info["checks"] == len(norms) == 8
+    assert abs(info["res0"] - r0) < 1e-12 * r0 and abs(info["res"] - norms[-1]) < 1e-8 * norms[-1]
+
+
+# ---------------------------------------------------------------------------
 # Full size, in the configuration bench.py times: X 4096 x 262144 FP32
 # (cond 1e3), lambda 1e-4, b = 8, s = 32, H = 4096.  The oracle runs its
 # Algorithm 1 (s = 1), which the s-step method reproduces (Sec. 3.1).
