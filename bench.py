@@ -363,6 +363,103 @@ def precision_study(args) -> int:
     return 0
 
 
+def serve_study(args) -> int:
+    """--serve: the serving loop (include/ca_serve.h) on a Poisson stream of
+    dense ridge requests shaped like the served-batch workload, scaled to a
+    short run: d log-uniform in [256, 2048], n log-uniform in [4096, 32768],
+    FP32 X N(0,1), lambda log-uniform in [1e-6, 1e-1], half primal / half
+    dual, b in {4, 8, 16}, s = min(16, 128 / b), H = min(2048, 4 N / b)
+    block updates (4 sweeps of the sampled dimension), BF16x3 Gram, the
+    stopping test every 8 outer steps at ||r|| <= 1e-6 ||r_0||.  Reports
+    latency percentiles, throughput and peak concurrency, and the same
+    requests run one after another on one context.  One JSON line."""
+    import math
+    import numpy as np
+    import torch
+    import paper_1612_04003_gb300 as ca
+    ca.build()
+    rng = np.random.default_rng(11)
+    M, rate = args.serve_requests, args.serve_rate
+    reqs = []
+    for i in range(M):
+        # rounded to multiples of 32 (16-byte rows for the tensor-core Gram)
+        d = int(math.exp(rng.uniform(math.log(256), math.log(2048)))) // 32 * 32
+        n = int(math.exp(rng.uniform(math.log(4096), math.log(32768)))) // 32 * 32
+        lam = float(math.exp(rng.uniform(math.log(1e-6), math.log(1e-1))))
+        method = "primal" if i % 2 == 0 else "dual"
+        b = int(rng.choice([4, 8, 16]))
+        N = d if method == "primal" else n
+        s_ = min(16, 128 // b)
+        H = int(min(2048, 4 * N // b))
+        g = torch.Generator(device="cuda").manual_seed(100 + i)
+        if method == "primal":
+            X = torch.randn(d, n, device="cuda", generator=g)
+            y = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+            xs, auxs = d, n
+        else:
+            X = torch.randn(n, d, device="cuda", generator=g)  # X^T
+            y = torch.sign(torch.randn(n, dtype=torch.float64, device="cuda", generator=g))
+            xs, auxs = n, d
+        reqs.append(dict(method=method, X=X, y=y, xs=xs, auxs=auxs,
+                         kw=dict(b=b, s=s_, H=H, lam=lam, seed=7 + i, prec="bf16x3",
+                                 check_every=8, tol=1e-6)))
+    torch.cuda.synchronize()
+
+    def fresh(r):
+        return (torch.zeros(r["xs"], dtype=torch.float64, device="cuda"),
+                torch.zeros(r["auxs"], dtype=torch.float64, device="cuda"))
+
+    # one after another on one context (the plain form)
+    ctx = ca.Context(0)
+    for r in reqs[:2]:  # warm
+        x, aux = fresh(r)
+        (ctx.ca_bcd_solve if r["method"] == "primal" else ctx.ca_bdcd_solve)(
+            r["X"], r["y"], x, aux, **r["kw"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h_seq = 0
+    for r in reqs:
+        x, aux = fresh(r)
+        (ctx.ca_bcd_solve if r["method"] == "primal" else ctx.ca_bdcd_solve)(
+            r["X"], r["y"], x, aux, **r["kw"])
+        h_seq += ctx.solve_info()["h_done"]
+    seq_s = time.perf_counter() - t0
+    ctx.close()
+    # served: Poisson arrivals
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=M))
+    srv = ca.Server(0, workers=args.serve_workers, budget_bytes=args.serve_budget_gb << 30)
+    outs, ids = [], []
+    t0 = time.perf_counter()
+    for r, at in zip(reqs, arrivals):
+        delay = at - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        x, aux = fresh(r)
+        outs.append((x, aux))
+        ids.append(srv.submit(r["method"], r["X"], r["y"], x, aux, **r["kw"]))
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    ok = sum(1 for v in res if v["status"] == ca.CA_OK)
+    print(json.dumps({
+        "study": "serve", "workload": "Poisson stream of %d dense ridge requests at %.0f/s "
+        "(d 256-2048, n 4096-32768 log-uniform, half primal / half dual, BF16x3 Gram, "
+        "stopping at 1e-6 relative residual)" % (M, rate),
+        "workers": args.serve_workers, "budget_gb": args.serve_budget_gb,
+        "completed": st["completed"], "ok": ok, "rejected": st["rejected"],
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+        "max_ms": st["max_ms"], "wall_s": st["wall_s"],
+        "requests_per_s": st["completed"] / max(st["wall_s"], 1e-9),
+        "block_updates_per_s": st["block_updates_per_s"],
+        "peak_concurrency": st["peak_concurrency"],
+        "peak_footprint_gb": st["peak_footprint"] / 2**30,
+        "stopped_early": sum(1 for v, r in zip(res, reqs) if v["h_done"] < r["kw"]["H"]),
+        "sequential": {"wall_s": seq_s, "block_updates_per_s": h_seq / seq_s,
+                       "how": "the same requests one after another on one context"},
+        "arrival_span_s": float(arrivals[-1])}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,6 +470,12 @@ def main():
     ap.add_argument("--precision-study", action="store_true",
                     help="run the precision study (8192 x 131072, cond 1e2..1e6) instead")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the serving study (Poisson stream of ridge requests) instead")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-rate", type=float, default=400.0, help="arrivals per second")
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=int, default=32)
     ap.add_argument("--s", type=int, default=None, help="unrolling depth (default %d)" % S)
     ap.add_argument("--n", type=int, default=None,
                     help="samples (columns of X); smaller than the default only for profiler captures")
@@ -387,6 +490,8 @@ def main():
         return run_reference(args, rank, world)
     if args.precision_study:
         return precision_study(args)
+    if args.serve:
+        return serve_study(args)
     s_run = args.s or S
     n_run = args.n or N_SAMPLES
     h_run = args.h or H

@@ -188,6 +188,19 @@ int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long l
  * returned CA_OK).  Errors: CA_ERR_ARG. */
 int ca_solve_info(const ca_ctx* ctx, ca_info* out);
 
+/* Device scratch (bytes) a dense solve takes from ctx's arena when X, y and
+ * the iterates are device memory: method 0 = ca_bcd_solve (X d x n), 1 =
+ * ca_bdcd_solve (X^T n x d); xfmt CA_DENSE_F64, CA_DENSE_F32 or
+ * CA_DENSE_F32_PANELS; o as for the solve.  The solve grows the arena to at
+ * least this (host-resident inputs add their staging).  Used to admit work
+ * by HBM footprint.  Errors: CA_ERR_ARG, CA_ERR_UNSUPPORTED. */
+int ca_solve_scratch_bytes(ca_ctx* ctx, int method, int xfmt, long long d, long long n,
+                           const ca_opts* o, size_t* bytes);
+
+/* Free ctx's scratch arena (after the work on its stream ends); the next
+ * call allocates what it needs again.  Errors: CA_ERR_ARG, CA_ERR_CUDA. */
+int ca_bcd_release_scratch(ca_ctx* ctx);
+
 /* Steps a2+a3 alone for given sampled rows (Alg. 2 / 4, "compute the Gram
  * matrix"): for the sb rows idx[0..sb) of the N x K row-major matrix A
  * (leading dimension ld), writes G = Y Y^T (sb x sb, row-major, FP64, full

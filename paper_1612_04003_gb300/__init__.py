@@ -52,6 +52,29 @@ class ca_info(ctypes.Structure):
                 ("res", ctypes.c_double)]
 
 
+class ca_request(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("xfmt", ctypes.c_int), ("X", ctypes.c_void_p),
+                ("d", ctypes.c_longlong), ("n", ctypes.c_longlong), ("ld", ctypes.c_longlong),
+                ("y", ctypes.c_void_p), ("x", ctypes.c_void_p), ("aux", ctypes.c_void_p),
+                ("opts", ca_opts)]
+
+
+class ca_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("worker", ctypes.c_int), ("h_done", ctypes.c_longlong),
+                ("res0", ctypes.c_double), ("res", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("scratch_bytes", ctypes.c_size_t)]
+
+
+class ca_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("block_updates_per_s", ctypes.c_double), ("peak_footprint", ctypes.c_size_t),
+                ("peak_concurrency", ctypes.c_int)]
+
+
 class ca_csr(ctypes.Structure):
     _fields_ = [("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
 
@@ -101,6 +124,23 @@ def load():
     lib.ca_gram_project.argtypes = [vp, i32, i32, vp, i64, i64, i64, vp, i32, vp, vp, vp]
     lib.ca_solve_info.argtypes = [vp, ctypes.POINTER(ca_info)]
     lib.ca_solve_info.restype = i32
+    lib.ca_solve_scratch_bytes.argtypes = [vp, i32, i32, i64, i64, ctypes.POINTER(ca_opts),
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    lib.ca_solve_scratch_bytes.restype = i32
+    lib.ca_bcd_release_scratch.argtypes = [vp]
+    lib.ca_bcd_release_scratch.restype = i32
+    lib.ca_server_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.c_size_t]
+    lib.ca_server_create.restype = i32
+    lib.ca_server_submit.argtypes = [vp, ctypes.POINTER(ca_request), ctypes.POINTER(i64)]
+    lib.ca_server_submit.restype = i32
+    lib.ca_server_wait.argtypes = [vp, i64, ctypes.POINTER(ca_result)]
+    lib.ca_server_wait.restype = i32
+    lib.ca_server_drain.argtypes = [vp]
+    lib.ca_server_drain.restype = i32
+    lib.ca_server_get_stats.argtypes = [vp, ctypes.POINTER(ca_server_stats)]
+    lib.ca_server_get_stats.restype = i32
+    lib.ca_server_destroy.argtypes = [vp]
+    lib.ca_server_destroy.restype = None
     lib.ca_gram_project.restype = i32
     lib.ca_pack_panels.argtypes = [vp, vp, i64, i64, i64, vp]
     lib.ca_pack_panels.restype = i32
@@ -313,3 +353,77 @@ class Context:
             out[f"{name}_ms"] = ms[i]
             out[f"{name}_launches"] = n[i]
         return out
+
+
+class Server:
+    """Serving loop (include/ca_serve.h): `workers` contexts on their own
+    streams, FIFO admission by scratch footprint within `budget_bytes`.
+    submit() returns at once with an id; wait(id) blocks until that request
+    ended.  The arrays of a request stay referenced here until it ended."""
+
+    def __init__(self, device: int = 0, workers: int = 4, budget_bytes: int = 8 << 30):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        st = self._lib.ca_server_create(ctypes.byref(h), device, int(workers), int(budget_bytes))
+        if st != CA_OK:
+            raise CaError(st, "ca_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, method, X, y, x, aux=None, *, b, s=1, H, lam, seed=42, prec="tf32",
+               recompute_every=0, tol=0.0, check_every=0, d=None, n=None, ld=None,
+               panels=None) -> int:
+        """method "primal" (X d x ld, x = w, aux = z or None) or "dual"
+        (X = X^T n x ld, x = alpha, aux = w); panels=(rows, cols) for
+        pre-packed FP32 panels."""
+        m = {"primal": 0, "dual": 1}[method]
+        o = Context._opts(b, s, H, lam, seed, prec, recompute_every, 0, tol, check_every)
+        if panels is not None:  # primal (d, n), dual (n, d)
+            rows, cols = (int(v) for v in panels)
+            xf, ldv = CA_DENSE_F32_PANELS, 0
+        else:  # primal X: d x ld (n columns used), dual X^T: n x ld (d used)
+            rows, ldv = X.shape
+            xf = _xfmt(X)
+            used = n if m == 0 else d
+            cols = ldv if used is None else int(used)
+            ldv = ldv if ld is None else int(ld)
+        dd, nn = (rows, cols) if m == 0 else (cols, rows)
+        r = ca_request(m, xf, _ptr(X), dd, nn, ldv, _ptr(y), _ptr(x), _ptr(aux), o)
+        rid = ctypes.c_longlong()
+        st = self._lib.ca_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid))
+        if st != CA_OK:
+            raise CaError(st, "ca_server_submit")
+        self._keep[rid.value] = (X, y, x, aux)
+        return rid.value
+
+    def wait(self, rid: int) -> dict:
+        out = ca_result()
+        st = self._lib.ca_server_wait(self.handle, int(rid), ctypes.byref(out))
+        if st != CA_OK:
+            raise CaError(st, "ca_server_wait")
+        self._keep.pop(int(rid), None)
+        return {f: getattr(out, f) for f, _ in ca_result._fields_}
+
+    def drain(self):
+        st = self._lib.ca_server_drain(self.handle)
+        if st != CA_OK:
+            raise CaError(st, "ca_server_drain")
+
+    def stats(self) -> dict:
+        out = ca_server_stats()
+        st = self._lib.ca_server_get_stats(self.handle, ctypes.byref(out))
+        if st != CA_OK:
+            raise CaError(st, "ca_server_get_stats")
+        return {f: getattr(out, f) for f, _ in ca_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ca_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -497,6 +497,25 @@ size_t dense_work_bytes(ca_ctx* ctx, const ca_opts* o, long long K, int xfmt) {
 
 size_t panel_bytes(long long N, long long K) { return (size_t)((K + 31) / 32) * (size_t)N * 128; }
 
+// Arena bytes of a dense solve whose vectors are device-resident (host-resident
+// inputs add their staging on top): the Gram / solve work area, the split
+// copies of v and x, the sampled indices, rho (primal), the panel copy of X
+// when the solve repacks it, the scaled-FP16 row multipliers and the
+// stopping-test scratch.  method 0: primal (A = X, N = d, K = n); 1: dual
+// (A = X^T, N = n, K = d).
+size_t dense_base_need(ca_ctx* ctx, const ca_opts* o, int method, int xf, bool pre, long long d,
+                       long long n) {
+  const bool tc = (xf == CA_DENSE_F32) && tc_prec(o->prec);
+  const long long N = method == 0 ? d : n, K = method == 0 ? n : d;
+  size_t need = dense_work_bytes(ctx, o, K, xf) + align256((size_t)(K + 31) / 32 * 32 * 8) +
+                align256((size_t)N * 8) + align256((size_t)o->H * o->b * 4) + 8 * 256;
+  if (method == 0) need += align256((size_t)n * 8);  // rho
+  if (tc && !pre) need += align256(panel_bytes(N, K)) + 256;
+  if (tc && o->prec == CA_GRAM_FP16_SCALED) need += align256((size_t)N * 4) + 256;
+  if (o->check_every > 0) need += align256((size_t)N * 8) + 512;
+  return need;
+}
+
 void launch_pack(ca_ctx* ctx, const float* A, long long N, long long K, long long lda, float* out) {
   const long long units = N * ((K + 31) / 32);
   const long long blocks = std::min<long long>((units * 8 + 255) / 256, 16LL * ctx->num_sms);
@@ -626,22 +645,15 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   const bool x_host = !is_device_ptr(X), y_host = !is_device_ptr(y), w_host = !is_device_ptr(w);
   const bool z_host = z && !is_device_ptr(z);
   const size_t xbytes = pre ? panel_bytes(d, n) : (size_t)(d - 1) * ld * el + (size_t)n * el;
-  size_t need = dense_work_bytes(ctx, o, n, xf) + align256((size_t)n * 8) /* rho */ +
-                align256((size_t)(n + 31) / 32 * 32 * 8) /* rho split */ +
-                align256((size_t)d * 8) /* w split */ +
-                align256((size_t)o->H * o->b * 4) /* idx */;
+  size_t need = dense_base_need(ctx, o, 0, xf, pre, d, n);
   // FP32 X in pinned host memory: the panel repack reads it in place (one
   // pass over the host link instead of a copy followed by a repack)
   const void* x_mapped = (x_host && tc && !pre) ? mapped_host_ptr(X) : nullptr;
   if (x_host && !x_mapped) need += align256(xbytes) + 256;
-  if (tc && !pre) need += align256(panel_bytes(d, n)) + 256;
   const bool f16 = tc && o->prec == CA_GRAM_FP16_SCALED;
-  if (f16) need += align256((size_t)d * 4) + 256;
-  if (o->check_every > 0) need += align256((size_t)d * 8) + 512;
   if (y_host) need += align256((size_t)n * 8);
   if (w_host) need += align256((size_t)d * 8);
   if (z_host) need += align256((size_t)n * 8);
-  need += 8 * 256;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
   bool st;
@@ -735,10 +747,11 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   CA_TRY_CUDA(cudaSetDevice(ctx->device));
   const double ln = o->lam * (double)n;
   const bool y_host = !is_device_ptr(y), a_host = !is_device_ptr(alpha), w_host = !is_device_ptr(w);
-  size_t need = align256((size_t)o->H * o->b * 4) + 8 * 256;
-  if (y_host) need += align256((size_t)n * 8);
-  if (a_host) need += align256((size_t)n * 8);
-  if (w_host) need += align256((size_t)d * 8);
+  size_t need_host = 0;  // staging of host-resident vectors
+  if (y_host) need_host += align256((size_t)n * 8);
+  if (a_host) need_host += align256((size_t)n * 8);
+  if (w_host) need_host += align256((size_t)d * 8);
+  size_t need = align256((size_t)o->H * o->b * 4) + 8 * 256 + need_host;
 
   if (xfmt == CA_CSR_F32) {
     const ca_csr* csr = static_cast<const ca_csr*>(XT);
@@ -858,14 +871,10 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   const size_t el = xf == CA_DENSE_F64 ? 8 : 4;
   const bool x_host = !is_device_ptr(XT);
   const size_t xbytes = pre ? panel_bytes(n, d) : (size_t)(n - 1) * ld * el + (size_t)d * el;
-  need += dense_work_bytes(ctx, o, d, xf) + align256((size_t)(d + 31) / 32 * 32 * 8) +
-          align256((size_t)n * 8);
+  need = need_host + dense_base_need(ctx, o, 1, xf, pre, d, n);
   const void* x_mapped = (x_host && tc && !pre) ? mapped_host_ptr(XT) : nullptr;
   if (x_host && !x_mapped) need += align256(xbytes) + 256;
-  if (tc && !pre) need += align256(panel_bytes(n, d)) + 256;
   const bool f16 = tc && o->prec == CA_GRAM_FP16_SCALED;
-  if (f16) need += align256((size_t)n * 4) + 256;
-  if (o->check_every > 0) need += align256((size_t)n * 8) + 512;
   CA_TRY(ensure_arena(ctx, need));
   Carve cv{static_cast<char*>(ctx->arena)};
   bool st;
@@ -1014,6 +1023,31 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
   k_symmetrize<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(R, g.sbp, sb, G);
   CA_TRY_CUDA(cudaGetLastError());
   return finish(ctx);
+}
+
+int ca_solve_scratch_bytes(ca_ctx* ctx, int method, int xfmt, long long d, long long n,
+                           const ca_opts* o, size_t* bytes) {
+  t_cur_ctx = ctx;
+  if (!ctx || !bytes || (method != 0 && method != 1) || d < 1 || n < 1) return CA_ERR_ARG;
+  if (xfmt != CA_DENSE_F64 && xfmt != CA_DENSE_F32 && xfmt != CA_DENSE_F32_PANELS) return CA_ERR_ARG;
+  CA_TRY(check_opts(o, method == 0 ? d : n));
+  const bool pre = xfmt == CA_DENSE_F32_PANELS;
+  const int xf = pre ? (int)CA_DENSE_F32 : xfmt;
+  *bytes = dense_base_need(ctx, o, method, xf, pre, d, n);
+  return CA_OK;
+}
+
+int ca_bcd_release_scratch(ca_ctx* ctx) {
+  t_cur_ctx = ctx;
+  if (!ctx) return CA_ERR_ARG;
+  CA_TRY_CUDA(cudaSetDevice(ctx->device));
+  if (ctx->arena) {
+    CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    CA_TRY_CUDA(cudaFree(ctx->arena));
+    ctx->arena = nullptr;
+    ctx->arena_bytes = 0;
+  }
+  return CA_OK;
 }
 
 int ca_solve_info(const ca_ctx* ctx, ca_info* out) {

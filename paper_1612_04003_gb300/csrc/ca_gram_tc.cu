@@ -658,13 +658,12 @@ int launch_one(const float* A, long long lda, long long N, long long K, const in
                const float2* v2, int P, float* part, double* ppart, unsigned* err,
                const GramUpdate& u, cudaStream_t stream) {
   using C = TcCfg<SBP, THREE, UPD, BF, F16>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD, PANEL, BF, F16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-    if (e != cudaSuccess) return (int)e;
-    configured = true;
-  }
+  // once per instantiation (a function-local static is initialised once even
+  // when several threads launch concurrently)
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      k_gram_tc<SBP, THREE, UPD, PANEL, BF, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      C::kSmem);
+  if (configured != cudaSuccess) return (int)configured;
   const long long natoms = (K + 31) / 32;
   // launched as a programmatic dependent: its CTAs may start (and prefetch)
   // while the preceding grid in the stream finishes

@@ -1,0 +1,256 @@
+// Request scheduler of the serving loop (host only, no CUDA): a FIFO queue of
+// solve requests, a fixed set of workers (in the server each owns a CUDA
+// stream and a library context, so admitted requests run concurrently on the
+// device), and admission by device-memory footprint.
+//
+// Footprint model: worker w keeps a scratch arena of arena_w bytes that a
+// request needing `need` bytes grows to max(arena_w, need) (the library frees
+// the old arena before allocating the larger one).  The queue's head may
+// start on an idle worker w when
+//     sum_{v != w} arena_v + max(arena_w, need) <= budget,
+// on the idle worker for which that sum is smallest.  When it fits on no idle
+// worker, the largest arena of an idle worker is released and admission is
+// tried again; when no idle worker holds an arena, the head waits for a
+// request to finish.  A request needing more than the whole budget is
+// rejected at submission.  Strict FIFO: no request overtakes an earlier one.
+//
+// run(worker, id) executes request id on that worker and returns a status;
+// release(worker) frees an idle worker's arena.  Both are called without the
+// scheduler's lock held.
+#pragma once
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstddef>
+#include <cstdint>
+#include <deque>
+#include <functional>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace caserve {
+
+using Clock = std::chrono::steady_clock;
+
+struct JobState {
+  size_t need = 0;
+  int status = 0;
+  int worker = -1;
+  long long admitted = -1;  // position in the admission order
+  bool done = false;
+  Clock::time_point t_submit, t_start, t_end;
+};
+
+struct Stats {
+  long long submitted = 0, completed = 0, rejected = 0;
+  double p50_ms = 0, p99_ms = 0, mean_ms = 0, max_ms = 0;  // submission -> end
+  double wall_s = 0;            // first submission -> last end
+  size_t peak_footprint = 0;    // largest sum of arenas admitted
+  int peak_concurrency = 0;     // most requests running at once
+};
+
+class Scheduler {
+ public:
+  using RunFn = std::function<int(int worker, long long id)>;
+  using ReleaseFn = std::function<void(int worker)>;
+  static constexpr int kRejected = -6;  // status of a request larger than the budget
+
+  Scheduler(int workers, size_t budget, RunFn run, ReleaseFn release)
+      : budget_(budget), run_(std::move(run)), release_(std::move(release)), ws_(workers) {
+    for (int w = 0; w < workers; ++w) ws_[w].th = std::thread([this, w] { worker_loop(w); });
+    disp_ = std::thread([this] { dispatch_loop(); });
+  }
+
+  ~Scheduler() {
+    drain();
+    {
+      std::lock_guard<std::mutex> lk(m_);
+      stop_ = true;
+    }
+    cv_disp_.notify_all();
+    for (auto& w : ws_) w.cv.notify_all();
+    disp_.join();
+    for (auto& w : ws_) w.th.join();
+  }
+
+  Scheduler(const Scheduler&) = delete;
+  Scheduler& operator=(const Scheduler&) = delete;
+
+  // Queue a request needing `need` bytes of scratch; returns its id.
+  long long submit(size_t need) {
+    std::lock_guard<std::mutex> lk(m_);
+    const long long id = (long long)jobs_.size();
+    jobs_.emplace_back();
+    JobState& j = jobs_.back();
+    j.need = need;
+    j.t_submit = Clock::now();
+    if (first_ == Clock::time_point()) first_ = j.t_submit;
+    if (need > budget_) {
+      j.status = kRejected;
+      j.done = true;
+      j.t_start = j.t_end = j.t_submit;
+      ++rejected_;
+      cv_done_.notify_all();
+    } else {
+      queue_.push_back(id);
+      ++gen_;
+      cv_disp_.notify_one();
+    }
+    return id;
+  }
+
+  // Block until request id has ended; returns its state.
+  JobState wait(long long id) {
+    std::unique_lock<std::mutex> lk(m_);
+    cv_done_.wait(lk, [&] { return jobs_[(size_t)id].done; });
+    return jobs_[(size_t)id];
+  }
+
+  // Block until every submitted request has ended.
+  void drain() {
+    std::unique_lock<std::mutex> lk(m_);
+    cv_done_.wait(lk, [&] { return queue_.empty() && running_ == 0; });
+  }
+
+  Stats stats() {
+    std::lock_guard<std::mutex> lk(m_);
+    Stats s;
+    s.submitted = (long long)jobs_.size();
+    s.rejected = rejected_;
+    s.peak_footprint = peak_footprint_;
+    s.peak_concurrency = peak_running_;
+    std::vector<double> lat;
+    Clock::time_point last = first_;
+    for (const JobState& j : jobs_)
+      if (j.done && j.status != kRejected) {
+        lat.push_back(std::chrono::duration<double, std::milli>(j.t_end - j.t_submit).count());
+        last = std::max(last, j.t_end);
+      }
+    s.completed = (long long)lat.size();
+    if (!lat.empty()) {
+      std::sort(lat.begin(), lat.end());
+      auto rank = [&](double q) {  // nearest-rank percentile
+        size_t k = (size_t)std::ceil(q * (double)lat.size());
+        return lat[std::min(lat.size(), std::max<size_t>(k, 1)) - 1];
+      };
+      s.p50_ms = rank(0.50);
+      s.p99_ms = rank(0.99);
+      s.max_ms = lat.back();
+      double sum = 0;
+      for (double v : lat) sum += v;
+      s.mean_ms = sum / (double)lat.size();
+      s.wall_s = std::chrono::duration<double>(last - first_).count();
+    }
+    return s;
+  }
+
+  size_t arena_of(int w) {
+    std::lock_guard<std::mutex> lk(m_);
+    return ws_[w].arena;
+  }
+
+ private:
+  struct Worker {
+    size_t arena = 0;
+    long long job = -1;  // assigned request
+    bool busy = false;   // running, or being released
+    std::thread th;
+    std::condition_variable cv;
+  };
+
+  void dispatch_loop() {
+    std::unique_lock<std::mutex> lk(m_);
+    for (;;) {
+      const unsigned long long seen = gen_;
+      if (stop_ && queue_.empty()) return;
+      if (!queue_.empty()) {
+        JobState& j = jobs_[(size_t)queue_.front()];
+        size_t total = 0;
+        for (const Worker& w : ws_) total += w.arena;
+        int best = -1;
+        size_t best_total = 0;
+        for (int w = 0; w < (int)ws_.size(); ++w) {
+          if (ws_[w].busy) continue;
+          const size_t t = total - ws_[w].arena + std::max(ws_[w].arena, j.need);
+          if (t <= budget_ && (best < 0 || t < best_total)) {
+            best = w;
+            best_total = t;
+          }
+        }
+        if (best >= 0) {
+          const long long id = queue_.front();
+          queue_.pop_front();
+          Worker& w = ws_[best];
+          w.arena = std::max(w.arena, j.need);  // the arena the request grows it to
+          w.busy = true;
+          w.job = id;
+          j.worker = best;
+          j.admitted = admitted_++;
+          ++running_;
+          peak_running_ = std::max(peak_running_, running_);
+          peak_footprint_ = std::max(peak_footprint_, best_total);
+          w.cv.notify_one();
+          continue;
+        }
+        int victim = -1;  // the largest arena of an idle worker
+        for (int w = 0; w < (int)ws_.size(); ++w)
+          if (!ws_[w].busy && ws_[w].arena > 0 && (victim < 0 || ws_[w].arena > ws_[victim].arena))
+            victim = w;
+        if (victim >= 0) {
+          ws_[victim].busy = true;
+          lk.unlock();
+          release_(victim);
+          lk.lock();
+          ws_[victim].arena = 0;
+          ws_[victim].busy = false;
+          continue;
+        }
+      }
+      cv_disp_.wait(lk, [&] { return gen_ != seen || (stop_ && queue_.empty()); });
+    }
+  }
+
+  void worker_loop(int w) {
+    std::unique_lock<std::mutex> lk(m_);
+    for (;;) {
+      ws_[w].cv.wait(lk, [&] { return stop_ || ws_[w].job >= 0; });
+      if (ws_[w].job < 0) return;
+      const long long id = ws_[w].job;
+      jobs_[(size_t)id].t_start = Clock::now();
+      lk.unlock();
+      const int st = run_(w, id);
+      lk.lock();
+      JobState& j = jobs_[(size_t)id];
+      j.status = st;
+      j.t_end = Clock::now();
+      j.done = true;
+      ws_[w].job = -1;
+      ws_[w].busy = false;
+      --running_;
+      ++gen_;
+      cv_disp_.notify_one();
+      cv_done_.notify_all();
+    }
+  }
+
+  const size_t budget_;
+  RunFn run_;
+  ReleaseFn release_;
+  std::mutex m_;
+  std::condition_variable cv_disp_, cv_done_;
+  std::deque<JobState> jobs_;  // element references stay valid as it grows
+  std::deque<long long> queue_;
+  std::vector<Worker> ws_;
+  std::thread disp_;
+  bool stop_ = false;
+  unsigned long long gen_ = 0;  // bumped on every submission and completion
+  int running_ = 0, peak_running_ = 0;
+  long long rejected_ = 0, admitted_ = 0;
+  size_t peak_footprint_ = 0;
+  Clock::time_point first_{};
+};
+
+}  // namespace caserve

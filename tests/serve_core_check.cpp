@@ -1,0 +1,112 @@
+// CPU check of the serving scheduler (ca_serve_core.h) with a fake executor:
+// the executor mirrors the arena model (a worker's arena grows to a request's
+// need when it starts, a release sets it to zero) and checks, at every start,
+// that the arenas of all workers fit the budget; starts must follow the
+// submission order; oversized requests are rejected; every request ends.
+#include <atomic>
+#include <cstdio>
+#include <mutex>
+#include <random>
+#include <vector>
+
+#include "ca_serve_core.h"
+
+static int fails = 0;
+#define CHECK(c)                                             \
+  do {                                                       \
+    if (!(c)) {                                              \
+      std::printf("FAIL %s:%d %s\n", __FILE__, __LINE__, #c); \
+      ++fails;                                               \
+    }                                                        \
+  } while (0)
+
+struct Fake {
+  std::mutex m;
+  std::vector<size_t> arena;
+  std::vector<size_t> need;
+  std::vector<long long> starts;
+  size_t budget;
+  int running = 0, peak = 0;
+  bool over = false;
+  std::atomic<int> releases{0};
+  Fake(int workers, size_t b) : arena(workers, 0), budget(b) {}
+  int run(int w, long long id) {
+    {
+      std::lock_guard<std::mutex> lk(m);
+      arena[w] = std::max(arena[w], need[(size_t)id]);
+      size_t tot = 0;
+      for (size_t a : arena) tot += a;
+      if (tot > budget) over = true;
+      starts.push_back(id);
+      peak = std::max(peak, ++running);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200 + (id * 7919) % 1800));
+    std::lock_guard<std::mutex> lk(m);
+    --running;
+    return 0;
+  }
+  void release(int w) {
+    std::lock_guard<std::mutex> lk(m);
+    arena[w] = 0;
+    ++releases;
+  }
+};
+
+static void scenario(int workers, size_t budget, int njobs, size_t lo, size_t hi, unsigned seed) {
+  Fake f(workers, budget);
+  std::mt19937 rng(seed);
+  std::uniform_int_distribution<size_t> dist(lo, hi);
+  for (int i = 0; i < njobs; ++i) f.need.push_back(dist(rng));
+  std::vector<long long> ids, order;
+  {
+    caserve::Scheduler s(
+        workers, budget, [&](int w, long long id) { return f.run(w, id); },
+        [&](int w) { f.release(w); });
+    for (int i = 0; i < njobs; ++i) ids.push_back(s.submit(f.need[(size_t)i]));
+    for (int i = 0; i < njobs; ++i) {
+      caserve::JobState j = s.wait(ids[(size_t)i]);
+      CHECK(j.done);
+      if (f.need[(size_t)i] > budget) {
+        CHECK(j.status == caserve::Scheduler::kRejected && j.admitted < 0);
+      } else {
+        CHECK(j.status == 0 && j.worker >= 0 && j.worker < workers);
+        order.push_back(j.admitted);
+      }
+    }
+    s.drain();
+    caserve::Stats st = s.stats();
+    long long nrej = 0;
+    for (size_t v : f.need) nrej += v > budget;
+    CHECK(st.submitted == njobs && st.rejected == nrej && st.completed == njobs - nrej);
+    CHECK(st.p50_ms > 0 && st.p50_ms <= st.p99_ms && st.p99_ms <= st.max_ms);
+    CHECK(st.peak_footprint <= budget);
+    CHECK(st.peak_concurrency <= workers && st.peak_concurrency == f.peak);
+  }
+  CHECK(!f.over);
+  // admission follows the submission order (rejected requests never start)
+  for (size_t k = 0; k < order.size(); ++k) CHECK(order[k] == (long long)k);
+  CHECK(f.starts.size() == order.size());
+  std::printf("scenario workers=%d budget=%zu jobs=%d: peak concurrency %d, releases %d\n", workers,
+              budget, njobs, f.peak, f.releases.load());
+}
+
+int main() {
+  scenario(4, 100, 60, 5, 40, 1);    // several requests fit at once
+  scenario(4, 100, 40, 30, 120, 2);  // large requests: releases, rejections
+  scenario(1, 50, 20, 1, 50, 3);     // one worker: strictly one at a time
+  scenario(8, 1000, 200, 1, 100, 4); // wide
+  {  // a request that needs the whole budget after others grew their arenas
+    Fake f(3, 90);
+    f.need = {30, 30, 30, 90, 10};
+    caserve::Scheduler s(
+        3, 90, [&](int w, long long id) { return f.run(w, id); }, [&](int w) { f.release(w); });
+    std::vector<long long> ids;
+    for (size_t v : f.need) ids.push_back(s.submit(v));
+    for (size_t k = 0; k < ids.size(); ++k) CHECK(s.wait(ids[k]).admitted == (long long)k);
+    s.drain();
+    CHECK(!f.over);
+    CHECK(f.releases.load() >= 2);
+  }
+  if (fails == 0) std::printf("ALL OK\n");
+  return fails == 0 ? 0 : 1;
+}

@@ -41,6 +41,9 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.ca_sample_indices(None, 1, 0, 1, 1, 1, None) == ca.CA_ERR_ARG
     assert lib.ca_profile_enable(None, 1) == ca.CA_ERR_ARG
     assert lib.ca_solve_info(None, None) == ca.CA_ERR_ARG
+    assert lib.ca_server_submit(None, None, None) == ca.CA_ERR_ARG
+    assert lib.ca_server_get_stats(None, None) == ca.CA_ERR_ARG
+    lib.ca_server_destroy(None)  # no-op
     lib.ca_bcd_destroy(None)  # no-op
 
 
@@ -58,7 +61,7 @@ def _c_layout(tmp_path, struct, fields):
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     src = tmp_path / "layout.c"
     body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
-    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"ca_bcd.h\"\n"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"ca_serve.h\"\n"
                    f"int main(void) {{\n  printf(\"%zu\\n\", sizeof({struct}));\n{body}  return 0;\n}}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
@@ -66,7 +69,10 @@ def _c_layout(tmp_path, struct, fields):
     return [int(v) for v in out]
 
 
-@pytest.mark.parametrize("py,c", [(lambda: ca.ca_opts, "ca_opts"), (lambda: ca.ca_info, "ca_info")])
+@pytest.mark.parametrize("py,c", [(lambda: ca.ca_opts, "ca_opts"), (lambda: ca.ca_info, "ca_info"),
+                                  (lambda: ca.ca_request, "ca_request"),
+                                  (lambda: ca.ca_result, "ca_result"),
+                                  (lambda: ca.ca_server_stats, "ca_server_stats")])
 def test_struct_layout_matches_header(tmp_path, py, c):
     cls = py()
     names = [f[0] for f in cls._fields_]

@@ -1,0 +1,22 @@
+"""The serving scheduler's logic on the CPU: tests/serve_core_check.cpp
+drives paper_1612_04003_gb300/csrc/ca_serve_core.h with a fake executor
+(FIFO admission, the footprint bound at every start, releases, rejections,
+latency statistics)."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="no g++")
+def test_scheduler_core(tmp_path):
+    exe = tmp_path / "serve_core_check"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-pthread", "-I",
+                    os.path.join(ROOT, "paper_1612_04003_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "serve_core_check.cpp"), "-o", str(exe)],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "ALL OK" in r.stdout, r.stdout + r.stderr
