@@ -223,7 +223,9 @@ int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N,
  * library until the process exits).
  *   cuda_stream  the cudaStream_t to run on (NULL = legacy default stream),
  *                on the current device.
- *   Limits: sb <= 128 and K <= 262144 (beyond them: CA_ERR_UNSUPPORTED).
+ *   Limits: sb <= 128 and K <= 262144 (beyond them: CA_ERR_UNSUPPORTED);
+ *   prec CA_GRAM_FP16_SCALED needs per-row scales the fixed array has no
+ *   room for (CA_ERR_UNSUPPORTED).
  *   A, idx, v, G, p: as ca_gram_project, all device memory.
  * The first call on a device looks up the array's device address (keep that
  * first call outside any stream capture).  All calls share the array and it
