@@ -55,6 +55,17 @@ int run_request(ca_server* s, int w, long long id) {
   return st;
 }
 
+// Device (or managed) memory: the footprint admitted excludes host staging.
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 void fill_times(ca_result* out, const caserve::JobState& j) {
   using ms = std::chrono::duration<double, std::milli>;
   out->queue_ms = ms(j.t_start - j.t_submit).count();
@@ -104,6 +115,9 @@ int ca_server_submit(ca_server* s, const ca_request* r, long long* id) {
   if (!s || !r || !id || !r->X || !r->y || !r->x) return CA_ERR_ARG;
   if (r->method != 0 && r->method != 1) return CA_ERR_ARG;
   if (r->method == 1 && !r->aux) return CA_ERR_ARG;
+  for (const void* q : {r->X, static_cast<const void*>(r->y), static_cast<const void*>(r->x)})
+    if (!on_device(q)) return CA_ERR_ARG;
+  if (r->aux && !on_device(r->aux)) return CA_ERR_ARG;
   size_t need = 0;
   const int e = ca_solve_scratch_bytes(s->ctxs[0], r->method, r->xfmt, r->d, r->n, &r->opts, &need);
   if (e != CA_OK) return e;
