@@ -42,6 +42,14 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.ca_profile_enable(None, 1) == ca.CA_ERR_ARG
     assert lib.ca_solve_info(None, None) == ca.CA_ERR_ARG
     assert lib.ca_server_submit(None, None, None) == ca.CA_ERR_ARG
+    assert lib.ca_server_create(None, 0, 4, 1 << 20) == ca.CA_ERR_ARG
+    h = ctypes.c_void_p()
+    assert lib.ca_server_create(ctypes.byref(h), 0, 0, 1 << 20) == ca.CA_ERR_ARG  # no workers
+    assert lib.ca_server_create(ctypes.byref(h), 0, 4, 0) == ca.CA_ERR_ARG  # no budget
+    assert lib.ca_server_wait(None, 0, None) == ca.CA_ERR_ARG
+    assert lib.ca_server_drain(None) == ca.CA_ERR_ARG
+    assert lib.ca_solve_scratch_bytes(None, 0, 0, 1, 1, None, None) == ca.CA_ERR_ARG
+    assert lib.ca_bcd_release_scratch(None) == ca.CA_ERR_ARG
     assert lib.ca_server_get_stats(None, None) == ca.CA_ERR_ARG
     lib.ca_server_destroy(None)  # no-op
     lib.ca_bcd_destroy(None)  # no-op
