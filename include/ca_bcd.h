@@ -80,7 +80,7 @@ typedef enum {
   CA_GRAM_TF32 = 2,       /* FP32 X: TF32 tcgen05 products, FP32 accumulate     */
   CA_GRAM_BF16X3 = 3,     /* FP32 X: x = b0 + b1 in BF16, b0 b0^T + b0 b1^T +
                            * b1 b0^T on tcgen05 (kind::f16), FP32 accumulate;
-                           * each product within about 2^-16 |x| |y|          */
+                           * each product within 3 * 2^-16 |x| |y|           */
   CA_GRAM_FP16_SCALED = 4 /* FP32 X: each row of A times a power of two that
                            * brings its largest magnitude into [2^14, 2^15),
                            * rounded to FP16, one product on tcgen05

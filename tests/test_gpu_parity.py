@@ -5,10 +5,11 @@ Element-wise comparisons on the same seeded inputs.  Tolerances (relative
   * 1e-10 for FP64 X with the FP64 Gram;
   * 1e-5  for FP32 X with the 3xTF32 and the BF16x3 tensor-core Gram (FP32
     products in the projection / update, FP64 vectors and solves).  3xTF32
-    drops terms below ~2^-21 |x||y| per product; BF16x3 (x = b0 + b1 in
-    BF16) drops b1 c1 and the split remainders, at most 3 * 2^-18 |x||y|:
-    each Gram entry is within ~1e-5 sqrt(G_ii G_jj), and the iterates
-    (measured 2e-7 .. 4e-6 on these cases) stay inside the FP32 bound;
+    drops terms below ~2^-20 |x||y| per product; BF16x3 (x = b0 + b1 in
+    BF16, unit roundoff 2^-8) drops b1 c1 and the split remainders, at most
+    3 * 2^-16 |x||y| per product (random signs keep the Gram entries near
+    3e-6 sqrt(G_ii G_jj)), and the iterates (measured 2e-7 .. 4e-6 on these
+    cases) stay inside the FP32 bound;
   * TF32 Gram (inputs rounded to 11 significant bits) and the scaled FP16
     Gram (each row times a power of two, rounded to FP16's 11 significant
     bits; the scales come off exactly): each Gram entry is off
@@ -486,12 +487,12 @@ def gram_data():
 # Gram tolerances relative to sqrt(G_ii G_jj): FP64 rounding; 3xTF32: the
 # dropped lo*lo term (2^-22) plus FP32 accumulation of up to ~1000 same-sign
 # terms per split (1000 * 2^-24 ~ 6e-5 worst case, 2e-5 used); TF32: 2^-11
-# input rounding; BF16x3: the dropped b1 c1 and split remainders, 3 * 2^-18
-# ~ 1.1e-5 (Cauchy-Schwarz over the sum), plus the same FP32 accumulation
-# allowance: 4e-5; scaled FP16: each scaled element rounded to 11
+# input rounding; BF16x3: the dropped b1 c1 and split remainders, 3 * 2^-16
+# ~ 4.6e-5 (unit roundoff 2^-8; Cauchy-Schwarz over the sum), plus the same
+# FP32 accumulation allowance: 1e-4; scaled FP16: each scaled element rounded to 11
 # significant bits (2^-11 relative), a product within ~2^-10, as TF32: 3e-3.
 @pytest.mark.parametrize("prec,tolG,tolp", [("f64", 1e-13, 1e-13), ("3xtf32", 2e-5, 1e-6),
-                                            ("tf32", 3e-3, 1e-6), ("bf16x3", 4e-5, 1e-6),
+                                            ("tf32", 3e-3, 1e-6), ("bf16x3", 1e-4, 1e-6),
                                             ("fp16_scaled", 3e-3, 1e-6)])
 @pytest.mark.parametrize("sb", [1, 8, 32, 100, 128, 129, 136, 256])
 def test_gram_project_kernel(ctx, gram_data, prec, tolG, tolp, sb):
@@ -541,7 +542,7 @@ def test_gram_project_wide_magnitudes(ctx, prec):
     nrm = np.sqrt(np.diag(G_ref))
     Gerr = np.abs(G.cpu().numpy() - G_ref) / np.outer(nrm, nrm)
     assert np.isfinite(G.cpu().numpy()).all()
-    assert Gerr.max() < (3e-3 if prec == "fp16_scaled" else 4e-5), Gerr.max()
+    assert Gerr.max() < (3e-3 if prec == "fp16_scaled" else 1e-4), Gerr.max()
 
 
 def test_noalloc_refuses_scaled_fp16(ctx, gram_data):
