@@ -34,12 +34,17 @@ typedef struct {
   const double* y;   /* device, n labels */
   double* x;         /* device: primal w (d; w0 in, w_H out); dual alpha (n; in/out) */
   double* aux;       /* device: primal z = X^T w_H (n) or NULL; dual w (d, out) */
-  ca_opts opts;      /* as for the solve (stopping test included) */
+  ca_opts opts;      /* as for the solve (stopping test included); opts.s = 0:
+                      * the server picks s by measured cost: requests of one
+                      * shape class (method, xfmt, prec, b, binades of N and
+                      * K) try each s with s*b <= 256 once, then run the one
+                      * with the least measured time per block update        */
 } ca_request;
 
 typedef struct {
   int status;             /* CA_OK or the solve's error code                */
   int worker;             /* context that ran it (-1: rejected)             */
+  int s;                  /* unrolling depth it ran with                    */
   long long h_done;       /* block updates performed (ca_solve_info)        */
   double res0, res;       /* residual norms of the stopping test (or 0)     */
   double queue_ms;        /* submission -> start                            */

@@ -60,7 +60,8 @@ class ca_request(ctypes.Structure):
 
 
 class ca_result(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int), ("worker", ctypes.c_int), ("h_done", ctypes.c_longlong),
+    _fields_ = [("status", ctypes.c_int), ("worker", ctypes.c_int), ("s", ctypes.c_int),
+                ("h_done", ctypes.c_longlong),
                 ("res0", ctypes.c_double), ("res", ctypes.c_double), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
                 ("scratch_bytes", ctypes.c_size_t)]

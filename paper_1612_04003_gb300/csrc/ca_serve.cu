@@ -4,7 +4,9 @@
 // ca_bdcd_solve call on its worker's host thread, so requests admitted
 // together overlap on the device.  Its footprint is the scratch the solve
 // takes from the context's arena (ca_solve_scratch_bytes); admission keeps
-// the sum of the workers' arenas within the budget.
+// the sum of the workers' arenas within the budget.  Requests submitted with
+// opts.s = 0 get their unrolling depth from a measured-cost tuner shared by
+// requests of the same shape class.
 #include <cuda_runtime.h>
 
 #include <deque>
@@ -24,10 +26,17 @@ struct ca_server {
   std::mutex m;                   // guards reqs and results
   std::deque<ca_request> reqs;    // by id; element references stay valid
   std::deque<ca_result> results;  // by id
+  caserve::STuner tuner;           // s of requests submitted with opts.s = 0
   std::unique_ptr<caserve::Scheduler> sched;
 };
 
 namespace {
+
+caserve::STuner::Key tuner_key(const ca_request& r) {
+  const long long N = r.method == 0 ? r.d : r.n, K = r.method == 0 ? r.n : r.d;
+  return {r.method, r.xfmt, r.opts.prec, r.opts.b, caserve::STuner::binade(N),
+          caserve::STuner::binade(K)};
+}
 
 int run_request(ca_server* s, int w, long long id) {
   ca_request r;
@@ -40,15 +49,22 @@ int run_request(ca_server* s, int w, long long id) {
     return CA_ERR_CUDA;
   }
   ca_ctx* ctx = s->ctxs[(size_t)w];
+  const bool tuned = r.opts.s == 0;
+  const caserve::STuner::Key key = tuner_key(r);
+  if (tuned) r.opts.s = s->tuner.choose(key);
+  const auto t0 = caserve::Clock::now();
   const int st = r.method == 0
                      ? ca_bcd_solve(ctx, r.xfmt, r.X, r.d, r.n, r.ld, r.y, &r.opts, r.x, r.aux)
                      : ca_bdcd_solve(ctx, r.xfmt, r.X, r.d, r.n, r.ld, r.y, &r.opts, r.x, r.aux);
+  const double secs = std::chrono::duration<double>(caserve::Clock::now() - t0).count();
   ca_info info{};
   if (st == CA_OK) ca_solve_info(ctx, &info);
+  if (tuned && st == CA_OK) s->tuner.record(key, r.opts.s, secs, info.h_done);
   std::lock_guard<std::mutex> lk(s->m);
   ca_result& out = s->results[(size_t)id];
   out.status = st;
   out.worker = w;
+  out.s = r.opts.s;
   out.h_done = st == CA_OK ? info.h_done : 0;
   out.res0 = info.res0;
   out.res = info.res;
@@ -118,8 +134,12 @@ int ca_server_submit(ca_server* s, const ca_request* r, long long* id) {
   for (const void* q : {r->X, static_cast<const void*>(r->y), static_cast<const void*>(r->x)})
     if (!on_device(q)) return CA_ERR_ARG;
   if (r->aux && !on_device(r->aux)) return CA_ERR_ARG;
+  // s = 0: chosen at run time by measured cost; admit with the footprint of
+  // the largest candidate, which bounds every candidate's
+  ca_opts o = r->opts;
+  if (o.s == 0) o.s = s->tuner.largest(o.b);
   size_t need = 0;
-  const int e = ca_solve_scratch_bytes(s->ctxs[0], r->method, r->xfmt, r->d, r->n, &r->opts, &need);
+  const int e = ca_solve_scratch_bytes(s->ctxs[0], r->method, r->xfmt, r->d, r->n, &o, &need);
   if (e != CA_OK) return e;
   // the request's entries exist before the scheduler can start it (ids are
   // the submission order in both tables: submissions are serialised here)

@@ -27,7 +27,9 @@
 #include <cstdint>
 #include <deque>
 #include <functional>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <thread>
 #include <vector>
 
@@ -251,6 +253,93 @@ class Scheduler {
   long long rejected_ = 0, admitted_ = 0;
   size_t peak_footprint_ = 0;
   Clock::time_point first_{};
+};
+
+// Per-instance unrolling depth s by measured cost (the paper's b / s
+// trade-off: a larger s reads Y once for more block updates but lengthens
+// the dependent chain and the Gram tile).  Requests of one shape class share
+// a table of measured seconds per block update for every candidate s (powers
+// of two with s * b <= max_sb); a class first tries each candidate once, in
+// the order 8, 16, 4, 32, 2, 1, 64, ..., then runs the candidate with the
+// least mean cost so far (every run updates its running mean).
+class STuner {
+ public:
+  struct Key {
+    int method, xfmt, prec, b, lg_n, lg_k;  // lg_*: binade of N and K
+    bool operator<(const Key& o) const {
+      return std::tie(method, xfmt, prec, b, lg_n, lg_k) <
+             std::tie(o.method, o.xfmt, o.prec, o.b, o.lg_n, o.lg_k);
+    }
+  };
+
+  explicit STuner(int max_sb = 256) : max_sb_(max_sb) {}
+
+  static int binade(long long v) {
+    int e = 0;
+    while (v > 1) {
+      v >>= 1;
+      ++e;
+    }
+    return e;
+  }
+
+  // candidates of a block size b, in the order they are first tried
+  std::vector<int> candidates(int b) const {
+    std::vector<int> out;
+    for (int s : {8, 16, 4, 32, 2, 1, 64, 128, 256})
+      if (b >= 1 && (long long)s * b <= max_sb_) out.push_back(s);
+    if (out.empty()) out.push_back(1);
+    return out;
+  }
+
+  // the largest candidate (its scratch bounds every candidate's)
+  int largest(int b) const {
+    int m = 1;
+    for (int s : candidates(b)) m = std::max(m, s);
+    return m;
+  }
+
+  int choose(const Key& k) {
+    std::lock_guard<std::mutex> lk(m_);
+    auto& t = table_[k];
+    int best = -1;
+    double best_cost = 0;
+    for (int s : candidates(k.b)) {
+      const auto it = t.find(s);
+      if (it == t.end() || it->second.second == 0) return s;  // not measured yet
+      const double c = it->second.first / (double)it->second.second;
+      if (best < 0 || c < best_cost) {
+        best = s;
+        best_cost = c;
+      }
+    }
+    return best;
+  }
+
+  // a run of `updates` block updates at depth s took `seconds`
+  void record(const Key& k, int s, double seconds, long long updates) {
+    if (updates <= 0 || !(seconds >= 0)) return;
+    std::lock_guard<std::mutex> lk(m_);
+    auto& e = table_[k][s];
+    e.first += seconds / (double)updates;
+    e.second += 1;
+  }
+
+  // mean measured seconds per block update at depth s (-1: none yet)
+  double cost(const Key& k, int s) {
+    std::lock_guard<std::mutex> lk(m_);
+    const auto it = table_.find(k);
+    if (it == table_.end()) return -1;
+    const auto jt = it->second.find(s);
+    if (jt == it->second.end() || jt->second.second == 0) return -1;
+    return jt->second.first / (double)jt->second.second;
+  }
+
+ private:
+  const int max_sb_;
+  std::mutex m_;
+  // per class: s -> (sum of seconds per update, runs)
+  std::map<Key, std::map<int, std::pair<double, long long>>> table_;
 };
 
 }  // namespace caserve

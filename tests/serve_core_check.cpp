@@ -90,7 +90,46 @@ static void scenario(int workers, size_t budget, int njobs, size_t lo, size_t hi
               budget, njobs, f.peak, f.releases.load());
 }
 
+// The s tuner: each class explores its candidates once, then keeps to the
+// cheapest measured one; classes do not share measurements.
+static void tuner_checks() {
+  caserve::STuner t(256);
+  CHECK((t.candidates(8) == std::vector<int>{8, 16, 4, 32, 2, 1}));
+  CHECK((t.candidates(64) == std::vector<int>{4, 2, 1}));
+  CHECK(t.largest(8) == 32 && t.largest(300) == 1);
+  caserve::STuner::Key a{0, 1, 3, 8, 12, 18}, b{1, 1, 3, 8, 14, 11};
+  // seconds per update: a prefers s = 16, b prefers s = 4
+  auto cost_a = [](int s) { return 1.0 / s + 0.004 * s; };
+  auto cost_b = [](int s) { return 0.2 / s + 0.02 * s; };
+  std::vector<int> seen_a, seen_b;
+  for (int it = 0; it < 12; ++it) {
+    const int sa = t.choose(a), sb = t.choose(b);
+    seen_a.push_back(sa);
+    seen_b.push_back(sb);
+    t.record(a, sa, cost_a(sa) * 1000, 1000);
+    t.record(b, sb, cost_b(sb) * 500, 500);
+  }
+  CHECK((std::vector<int>(seen_a.begin(), seen_a.begin() + 6) == t.candidates(8)));
+  for (int it = 6; it < 12; ++it) CHECK(seen_a[(size_t)it] == 16 && seen_b[(size_t)it] == 4);
+  CHECK(t.cost(a, 16) > 0 && t.cost(a, 64) < 0);
+  // concurrent use
+  std::vector<std::thread> th;
+  for (int k = 0; k < 8; ++k)
+    th.emplace_back([&t, k] {
+      caserve::STuner::Key c{0, 1, 2, 4, k, 10};
+      for (int it = 0; it < 200; ++it) {
+        const int s = t.choose(c);
+        t.record(c, s, 1e-3 * (1.0 / s + 0.01 * s), 1);
+      }
+    });
+  for (auto& x : th) x.join();
+  caserve::STuner::Key c0{0, 1, 2, 4, 0, 10};
+  CHECK(t.choose(c0) == 8);  // argmin of 1/s + 0.01 s over 1, 2, 4, ..., 64
+  std::printf("tuner: class a -> %d, class b -> %d\n", seen_a.back(), seen_b.back());
+}
+
 int main() {
+  tuner_checks();
   scenario(4, 100, 60, 5, 40, 1);    // several requests fit at once
   scenario(4, 100, 40, 30, 120, 2);  // large requests: releases, rejections
   scenario(1, 50, 20, 1, 50, 3);     // one worker: strictly one at a time
