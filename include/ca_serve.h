@@ -67,7 +67,8 @@ typedef struct {
 int ca_server_create(ca_server** out, int device, int workers, size_t budget_bytes);
 
 /* Queue a copy of *r; returns at once with its id (0, 1, ...).  The arrays
- * it points to must be device memory and stay valid until the request ends.
+ * it points to must be memory of the server's device (or managed memory)
+ * and stay valid until the request ends.
  * Errors: CA_ERR_ARG (host pointers, or options the solve would refuse),
  * CA_ERR_UNSUPPORTED. */
 int ca_server_submit(ca_server* s, const ca_request* r, long long* id);

@@ -71,15 +71,17 @@ int run_request(ca_server* s, int w, long long id) {
   return st;
 }
 
-// Device (or managed) memory: the footprint admitted excludes host staging.
-bool on_device(const void* p) {
+// Memory of the server's device (or managed memory): the footprint admitted
+// excludes host staging, and the solves run on that device.
+bool on_device(const void* p, int device) {
   if (!p) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice && at.device == device) ||
+         at.type == cudaMemoryTypeManaged;
 }
 
 void fill_times(ca_result* out, const caserve::JobState& j) {
@@ -132,8 +134,8 @@ int ca_server_submit(ca_server* s, const ca_request* r, long long* id) {
   if (r->method != 0 && r->method != 1) return CA_ERR_ARG;
   if (r->method == 1 && !r->aux) return CA_ERR_ARG;
   for (const void* q : {r->X, static_cast<const void*>(r->y), static_cast<const void*>(r->x)})
-    if (!on_device(q)) return CA_ERR_ARG;
-  if (r->aux && !on_device(r->aux)) return CA_ERR_ARG;
+    if (!on_device(q, s->device)) return CA_ERR_ARG;
+  if (r->aux && !on_device(r->aux, s->device)) return CA_ERR_ARG;
   // s = 0: chosen at run time by measured cost; admit with the footprint of
   // the largest candidate, which bounds every candidate's
   ca_opts o = r->opts;
