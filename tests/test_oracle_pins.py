@@ -69,6 +69,23 @@ def test_sampler_first_draw_is_mapped_philox_word():
         assert idx[0] == (u * (N - b + 1)) >> 64
 
 
+def test_sampler_draws_use_philox_words_in_counter_order():
+    """Library pin of the counter layout (reading of the unspecified RNG): draw
+    m of block h is word m % 4 of the block for counter (h, m / 4, 0, 0) (the
+    256-bit integer h + (m / 4) 2^64) under key (seed, 0), taken here from
+    numpy's Philox.  With N = 2^31 - 1 the b draws do not collide, so Floyd's
+    rule keeps every one: idx[m] = floor(u_m (N - b + m + 1) / 2^64)."""
+    N, b = 2**31 - 1, 12
+    for seed, h in [(42, 1), (7, 777), (2**64 - 5, 2**40 + 3)]:
+        t = []
+        for m in range(b):
+            ctr = h + (m // 4) * 2**64
+            u = int(np.random.Philox(key=seed, counter=ctr - 1).random_raw(4)[m % 4])
+            t.append((u * (N - b + m + 1)) >> 64)
+        assert len(set(t)) == b  # no collision: Floyd's rule keeps each draw
+        assert oracle.sample_block(seed, h, b, N).tolist() == t
+
+
 @pytest.mark.parametrize("b,N", [(1, 1), (3, 3), (4, 64), (8, 4096), (64, 64), (37, 100)])
 def test_sampler_distinct_in_range(b, N):
     for h in range(50):
@@ -228,10 +245,15 @@ def test_bcd_block_minimisation_is_exact(tiny):
 
 
 def test_recompute_is_a_no_op(tiny):
+    """Rebuilding z = X^T w from its definition (Sec. 3.1) changes nothing in
+    exact arithmetic: Algorithms 1 and 2 with and without it agree."""
     X, y = tiny.X, tiny.y
     wa, _ = oracle.ca_bcd(X, y, LAM1, b=4, s=4, H=200, seed=42)
     wb, _ = oracle.ca_bcd(X, y, LAM1, b=4, s=4, H=200, seed=42, recompute_every=2)
     assert _rel(wb, wa) < 1e-12
+    wc, _ = oracle.bcd(X, y, LAM1, b=4, H=200, seed=42)
+    wd, _ = oracle.bcd(X, y, LAM1, b=4, H=200, seed=42, recompute_every=3)
+    assert _rel(wd, wc) < 1e-12
 
 
 def test_short_last_outer_step(tiny):
@@ -342,6 +364,20 @@ def test_bdcd_converges_and_duality(wide):
         gap = (oracle.primal_objective(X, y, lam, ww) + oracle.dual_objective(X, y, lam, aa)
                - y @ y / (2 * n))
         assert gap >= -1e-12
+
+
+def test_dual_recompute_is_a_no_op(wide):
+    """Rebuilding w = -X alpha/(lambda n) from its definition (eq. "3")
+    changes nothing in exact arithmetic: Algorithms 3 and 4 with and without
+    it agree, in alpha and in w."""
+    X, y, lam = wide.X, wide.y, 1e-2
+    for s in (1, 3):
+        a1, w1 = oracle.ca_bdcd(X, y, lam, b=6, s=s, H=120, seed=9)
+        a2, w2 = oracle.ca_bdcd(X, y, lam, b=6, s=s, H=120, seed=9, recompute_every=2)
+        assert _rel(a2, a1) < 1e-12 and _rel(w2, w1) < 1e-12
+    a3, w3 = oracle.bdcd(X, y, lam, b=6, H=120, seed=9)
+    a4, w4 = oracle.bdcd(X, y, lam, b=6, H=120, seed=9, recompute_every=5)
+    assert _rel(a4, a3) < 1e-12 and _rel(w4, w3) < 1e-12
 
 
 def test_dual_sparse_csr_equals_dense():

@@ -100,6 +100,12 @@ def test_dual_residual_csr_equals_dense(wide):
     r_dense = oracle.dual_residual(X, y, a, w)
     r_csr = oracle.dual_residual(oracle.CSR.from_dense(X), y, a, w)
     assert np.allclose(r_csr, r_dense, rtol=1e-13, atol=1e-13)
+    # a sparse CSR (columns of X^T skipped) against its dense expansion
+    sp = synth.sparse_dual(d=300, n=80, density=0.05, seed=3)
+    A = oracle.CSR(sp.rowptr, sp.col, sp.val.astype(np.float64), sp.d)
+    a, w = rng.standard_normal(sp.n), rng.standard_normal(sp.d)
+    r_dense = oracle.dual_residual(sp.dense_X(), sp.y, a, w)
+    assert np.allclose(oracle.dual_residual(A, sp.y, a, w), r_dense, rtol=1e-13, atol=1e-13)
 
 
 def test_primal_stopped_run(tiny):
