@@ -14,7 +14,9 @@ Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 equivalence, monotone objectives, duality identity, the sampler's generator
 against numpy's Philox, Floyd's algorithm by exhaustive enumeration; the
 residuals of the stopping test against finite differences of the objectives,
-their zeros at the optimum and on the block just solved).
+their zeros at the optimum and on the block just solved; the duality gaps
+against the closed forms ||r||^2/(2 lambda) and ||r||^2/(2n) of the two
+residuals and against the objective error to the closed-form optimum).
 """
 from __future__ import annotations
 
@@ -280,6 +282,78 @@ def dual_residual(X, y, alpha, w) -> np.ndarray:
     (X dense d x n or the CSR of X^T), whose rows at the sampled indices are
     the BDCD subproblem's right-hand side."""
     return -_xt_times(X, _f64(w)) + _f64(alpha) + _f64(y)
+
+
+def primal_duality_gap(X, y, lam, w) -> float:
+    """Duality gap of the primal point w (Sec. 2.2): f(w) + D(alpha) - ||y||^2/(2n)
+    at the dual point alpha = X^T w - y that the optimality conditions pair
+    with w (alpha* = X^T w* - y), from the definitions of f and D.  Weak
+    duality makes it >= 0 and >= f(w) - f(w*)."""
+    X, y, w = _f64(X), _f64(y), _f64(w)
+    n = X.shape[1]
+    return (primal_objective(X, y, lam, w) + dual_objective(X, y, lam, X.T @ w - y)
+            - float(y @ y) / (2 * n))
+
+
+def dual_duality_gap(X, y, lam, alpha) -> float:
+    """Duality gap of the dual point alpha: f(w) + D(alpha) - ||y||^2/(2n) at
+    w = -X alpha/(lambda n) (eq. "3"), from the definitions of f and D (X
+    dense d x n or the CSR of X^T).  It bounds both D(alpha) - D(alpha*) and
+    f(w) - f(w*)."""
+    A = _as_csr(X)
+    y, alpha = _f64(y), _f64(alpha)
+    w = np.zeros(A.d)
+    for i in range(A.n):  # w = -X alpha/(lambda n), column by column
+        a, b = A.rowptr[i], A.rowptr[i + 1]
+        w[A.col[a:b]] -= A.val[a:b] * alpha[i] / (lam * A.n)
+    Xd = np.zeros((A.d, A.n))
+    for i in range(A.n):
+        a, b = A.rowptr[i], A.rowptr[i + 1]
+        Xd[A.col[a:b], i] = A.val[a:b]
+    return (primal_objective(Xd, y, lam, w) + dual_objective(A, y, lam, alpha)
+            - float(y @ y) / (2 * A.n))
+
+
+def ca_bcd_certified(X, y, lam, b, s, H, seed, tol, check_every):
+    """Algorithm 2 with a certified stop: after every check_every outer steps
+    the duality gap g of w and the primal objective f(w); since
+    f(w*) >= f(w) - g, the relative objective error (f(w) - f(w*))/f(w*) is
+    at most g/(f(w) - g), and the run ends at the first check where that
+    bound is <= tol (tol = 0: never), or at H.  Returns (w, h_done,
+    [(f(w), g) after each check])."""
+    X, y = _f64(X), _f64(y)
+    w = np.zeros(X.shape[0])
+    h, trace = 0, []
+    while h < H:
+        m = min(check_every * s, H - h)
+        w, _ = ca_bcd(X, y, lam, b, s, m, seed, h0=h, w0=w)
+        h += m
+        f, g = primal_objective(X, y, lam, w), primal_duality_gap(X, y, lam, w)
+        trace.append((f, g))
+        if h < H and tol > 0 and g <= tol * (f - g):
+            break
+    return w, h, trace
+
+
+def ca_bdcd_certified(X, y, lam, b, s, H, seed, tol, check_every):
+    """Algorithm 4 with the certified stop of ca_bcd_certified, on the model
+    w = -X alpha/(lambda n) and the gap of alpha.  Returns (alpha, w, h_done,
+    [(f(w), g) after each check])."""
+    A = _as_csr(X)
+    y = _f64(y)
+    alpha = np.zeros(A.n)
+    w = np.zeros(A.d)
+    h, trace = 0, []
+    while h < H:
+        m = min(check_every * s, H - h)
+        alpha, w = ca_bdcd(A, y, lam, b, s, m, seed, h0=h, alpha0=alpha)
+        h += m
+        g = dual_duality_gap(A, y, lam, alpha)
+        f = g + float(y @ y) / (2 * A.n) - dual_objective(A, y, lam, alpha)
+        trace.append((f, g))
+        if h < H and tol > 0 and g <= tol * (f - g):
+            break
+    return alpha, w, h, trace
 
 
 def ca_bcd_stopped(X, y, lam, b, s, H, seed, tol, check_every):

@@ -143,10 +143,29 @@ MUTANTS = [
     ("dense_as_csr_transposed", PY, "return CSR(rowptr, col, X.T.reshape(-1), d)",
      "return CSR(rowptr, col, X.reshape(-1), d)", 0),
     ("stopped_absolute_tolerance", PY, "norms[-1] <= tol * r0", "norms[-1] <= tol", 0),
+    # (occurrences of the loop text: 0, 1 the certified runs, 2, 3 the stopped runs)
     ("stopped_check_every_update", PY, "m = min(check_every * s, H - h)",
+     "m = min(check_every, H - h)", 2),
+    ("stopped_dual_check_every_update", PY, "m = min(check_every * s, H - h)",
+     "m = min(check_every, H - h)", 3),
+    ("stopped_primal_restarts_sampler", PY, "seed, h0=h, w0=w)", "seed, h0=0, w0=w)", 1),
+    ("stopped_dual_drops_iterate", PY, "seed, h0=h, alpha0=alpha)", "seed, h0=h)", 1),
+    ("certified_check_every_update", PY, "m = min(check_every * s, H - h)",
      "m = min(check_every, H - h)", 0),
-    ("stopped_primal_restarts_sampler", PY, "seed, h0=h, w0=w)", "seed, h0=0, w0=w)", 0),
-    ("stopped_dual_drops_iterate", PY, "seed, h0=h, alpha0=alpha)", "seed, h0=h)", 0),
+    ("certified_primal_restarts_sampler", PY, "seed, h0=h, w0=w)", "seed, h0=0, w0=w)", 0),
+    ("certified_dual_drops_iterate", PY, "seed, h0=h, alpha0=alpha)", "seed, h0=h)", 0),
+    # duality gaps and the certified stop (Sec. 2.2 duality, Sec. 5.1.5)
+    ("gap_wrong_dual_point", PY, "dual_objective(X, y, lam, X.T @ w - y)",
+     "dual_objective(X, y, lam, X.T @ w + y)", 0),
+    ("primal_gap_label_norm_unhalved", PY, "- float(y @ y) / (2 * n))", "- float(y @ y) / n)", 0),
+    ("dual_gap_label_norm_unhalved", PY, "- float(y @ y) / (2 * A.n))", "- float(y @ y) / A.n)", 0),
+    ("dual_gap_model_sign", PY, "w[A.col[a:b]] -= A.val[a:b] * alpha[i] / (lam * A.n)",
+     "w[A.col[a:b]] += A.val[a:b] * alpha[i] / (lam * A.n)", 0),
+    ("certified_uncertified_bound", PY, "g <= tol * (f - g)", "g <= tol * f", 0),
+    ("certified_dual_uncertified_bound", PY, "g <= tol * (f - g)", "g <= tol * f", 1),
+    ("certified_dual_objective_drops_gap", PY,
+     "f = g + float(y @ y) / (2 * A.n) - dual_objective(A, y, lam, alpha)",
+     "f = float(y @ y) / (2 * A.n) - dual_objective(A, y, lam, alpha)", 0),
 ]
 
 
