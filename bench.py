@@ -370,7 +370,9 @@ def serve_study(args) -> int:
     FP32 X N(0,1), lambda log-uniform in [1e-6, 1e-1], half primal / half
     dual, b in {4, 8, 16}, s = min(16, 128 / b), H = min(2048, 4 N / b)
     block updates (4 sweeps of the sampled dimension), BF16x3 Gram, the
-    stopping test every 8 outer steps at ||r|| <= 1e-6 ||r_0||.  Reports
+    stopping test every 8 outer steps at ||r|| <= 1e-6 ||r_0|| (--serve-stop
+    residual) or at a certified relative objective error <= 1e-6 (--serve-stop
+    objective: duality gap <= 1e-6 (f(w) - gap)).  Reports
     latency percentiles, throughput and peak concurrency, and the same
     requests run one after another on one context.  One JSON line."""
     import math
@@ -402,7 +404,7 @@ def serve_study(args) -> int:
             xs, auxs = n, d
         reqs.append(dict(method=method, X=X, y=y, xs=xs, auxs=auxs,
                          kw=dict(b=b, s=s_, H=H, lam=lam, seed=7 + i, prec="bf16x3",
-                                 check_every=8, tol=1e-6)))
+                                 check_every=8, tol=1e-6, stop=args.serve_stop)))
     torch.cuda.synchronize()
 
     def fresh(r):
@@ -444,7 +446,9 @@ def serve_study(args) -> int:
     print(json.dumps({
         "study": "serve", "workload": "Poisson stream of %d dense ridge requests at %.0f/s "
         "(d 256-2048, n 4096-32768 log-uniform, half primal / half dual, BF16x3 Gram, "
-        "stopping at 1e-6 relative residual)" % (M, rate),
+        "stopping at %s)" % (M, rate, {"residual": "1e-6 relative residual",
+                                       "objective": "a certified 1e-6 relative objective error"}
+                          [args.serve_stop]),
         "workers": args.serve_workers, "budget_gb": args.serve_budget_gb,
         "completed": st["completed"], "ok": ok, "rejected": st["rejected"],
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
@@ -454,6 +458,9 @@ def serve_study(args) -> int:
         "peak_concurrency": st["peak_concurrency"],
         "peak_footprint_gb": st["peak_footprint"] / 2**30,
         "stopped_early": sum(1 for v, r in zip(res, reqs) if v["h_done"] < r["kw"]["H"]),
+        "certified_1e-6": (sum(1 for v in res if v["fval"] > v["gap"] and
+                               v["gap"] <= 1e-6 * (v["fval"] - v["gap"]))
+                           if args.serve_stop == "objective" else None),
         "sequential": {"wall_s": seq_s, "block_updates_per_s": h_seq / seq_s,
                        "how": "the same requests one after another on one context"},
         "arrival_span_s": float(arrivals[-1])}), flush=True)
@@ -476,6 +483,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=400.0, help="arrivals per second")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=int, default=32)
+    ap.add_argument("--serve-stop", default="residual", choices=["residual", "objective"],
+                    help="stopping rule of the served requests")
     ap.add_argument("--s", type=int, default=None, help="unrolling depth (default %d)" % S)
     ap.add_argument("--n", type=int, default=None,
                     help="samples (columns of X); smaller than the default only for profiler captures")

@@ -91,6 +91,14 @@ typedef enum {
                            * (CA_ERR_UNSUPPORTED).                           */
 } ca_prec;
 
+/* Stopping rule of the check every check_every outer steps (Sec. 5.1.5). */
+typedef enum {
+  CA_STOP_RESIDUAL = 0, /* end once ||r||_2 <= tol ||r_0||_2                  */
+  CA_STOP_OBJECTIVE = 1 /* end once gap <= tol (f(w) - gap): the relative
+                         * objective error (f(w) - f(w*))/f(w*) of the model
+                         * w is then certified <= tol (gap and f: ca_info)  */
+} ca_stop;
+
 /* Solve options. */
 typedef struct {
   int b;                /* block size b (primal) or b' (dual); 1 <= b <= N     */
@@ -108,9 +116,20 @@ typedef struct {
    * sampled indices are each block subproblem's right-hand side -- and the
    * solve ends once ||r||_2 <= tol ||r_0||_2 (tol = 0: never; the norms are
    * still reported).  r_0 is taken at the starting iterate; a check waits
-   * for the GPU.  ca_solve_info reports what happened.                     */
+   * for the GPU.  ca_solve_info reports what happened.
+   * The norm also gives the duality gap of Sec. 2.2's primal / dual pair in
+   * closed form: for the primal iterate w, at alpha = X^T w - y,
+   * gap = f(w) + D(alpha) - ||y||^2/(2n) = ||r||^2/(2 lambda); for the dual
+   * iterate alpha, at w = -X alpha/(lambda n), gap = ||r||^2/(2n).  Weak
+   * duality gives f(w) - f(w*) <= gap (and D(alpha) - D(alpha*) <= gap).
+   * With stop = CA_STOP_OBJECTIVE a check also forms f(w) from the
+   * maintained vectors (primal: lambda/2 ||w||^2 + ||y - X^T w||^2/(2n);
+   * dual: ||y||^2/(2n) - D(alpha) + gap; O(n + d) extra reads) and the
+   * solve ends once gap <= tol (f(w) - gap): since f(w*) >= f(w) - gap,
+   * the relative objective error is then certified <= tol.               */
   double tol;
   int check_every;
+  int stop;             /* ca_stop; CA_STOP_RESIDUAL unless set             */
 } ca_opts;
 
 /* What the last solve on a context did. */
@@ -122,6 +141,9 @@ typedef struct {
                          * at the end of the solve when it ran to H)          */
   double res0;          /* ||r_0||_2 (0 without checks)                        */
   double res;           /* ||r||_2 at the last check                           */
+  double gap;           /* duality gap at the last check (0 without checks)    */
+  double fval;          /* f(w) of the model at the last check
+                         * (CA_STOP_OBJECTIVE only; else 0)                    */
 } ca_info;
 
 /* Dual CSR input: CSR of X^T with n rows (samples) and d columns (features).

@@ -47,6 +47,8 @@ typedef struct {
   int s;                  /* unrolling depth it ran with                    */
   long long h_done;       /* block updates performed (ca_solve_info)        */
   double res0, res;       /* residual norms of the stopping test (or 0)     */
+  double gap, fval;       /* duality gap and f(w) at the last check
+                           * (ca_info; fval under CA_STOP_OBJECTIVE only)   */
   double queue_ms;        /* submission -> start                            */
   double run_ms;          /* start -> end                                   */
   double latency_ms;      /* submission -> end                              */

@@ -40,7 +40,7 @@ struct ca_ctx {
   unsigned* d_err = nullptr;     // device error word
   unsigned* d_ticket = nullptr;  // count of the reducing CTAs of the reduce/solve kernel
                                  // (d_err + 32; both cleared where a call starts)
-  unsigned* h_err = nullptr;     // pinned copy (64 bytes: error word; residual at +32)
+  unsigned* h_err = nullptr;     // pinned copy (128 bytes: error word; check sums at +32)
   Profile prof;
   ca_info info{};                // outcome of the last solve
   char last_error[256] = {0};    // text of the last failing CUDA call
@@ -169,6 +169,7 @@ int check_opts(const ca_opts* o, long long N) {
   if (!(o->lam > 0.0) || !std::isfinite(o->lam)) return CA_ERR_ARG;
   if (o->recompute_every < 0) return CA_ERR_ARG;
   if (o->check_every < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol)) return CA_ERR_ARG;
+  if (o->stop != CA_STOP_RESIDUAL && o->stop != CA_STOP_OBJECTIVE) return CA_ERR_ARG;
   if (o->prec < CA_GRAM_F64 || o->prec > CA_GRAM_FP16_SCALED) return CA_ERR_ARG;
   if (N > 2147483647LL) return CA_ERR_UNSUPPORTED;
   if (o->b > kMaxB) return CA_ERR_UNSUPPORTED;
@@ -193,29 +194,91 @@ struct DenseProblem {
   // recompute of v: v = c0 * y0 + c1 * sum_r A[r] x[r]
   const double* y0;
   double c0, c1;
-  // stopping test: N doubles of scratch (zero between uses) and one accumulator
+  int method = 0;           // 0: primal (A = X), 1: dual (A = X^T)
+  // stopping test: check_rows(o, N, K) doubles of scratch (zero between uses)
+  // and kCheckAcc accumulators
   double* rq = nullptr;
   double* racc = nullptr;
 };
 
-// ||r||_2 of the current iterate, r = cP A v - cI x - cY y (Sec. 5.1.5):
-// one pass over A, then a wait for the GPU.
-int full_residual(ca_ctx* ctx, const void* A, bool f64, bool panel, long long lda, long long N,
-                  long long K, const double* v, const float2* v2, const ca_csr_dev* csr,
-                  double* rq, double* racc, const double* x, const double* yv, double cP,
-                  double cI, double cY, double* out) {
-  CA_TRY_CUDA(cudaMemsetAsync(racc, 0, sizeof(double), ctx->stream));
+// Stopping test (Sec. 5.1.5).  A check forms ||r||_2 of the current
+// iterate, r = cP A v - cI x - cY y (one pass over A, then a wait for the
+// GPU), and the duality gap of Sec. 2.2 that it gives in closed form:
+// primal (method 0; x = w, v = rho = y - X^T w, n = K), at the dual point
+// alpha = X^T w - y, gap = ||r||^2/(2 lambda); dual (method 1; x = alpha,
+// v = w = -X alpha/(lambda n), n = N), gap = ||r||^2/(2n).  Under the
+// objective rule it also forms f(w) of the model from the maintained vectors:
+// primal lambda/2 ||w||^2 + ||rho||^2/(2n); dual ||y||^2/(2n) - D(alpha) +
+// gap with D(alpha) = lambda/2 ||w||^2 + ||alpha + y||^2/(2n).
+constexpr int kCheckAcc = 4;  // ||r||^2, then the sums of squares behind f(w)
+
+// Rows of the check's zero scratch: the residual's N row sums; the objective
+// rule also runs the sums of squares over the K entries of v through it.
+long long check_rows(const ca_opts* o, long long N, long long K) {
+  return o->stop == CA_STOP_OBJECTIVE ? std::max(N, K) : N;
+}
+
+struct CheckArgs {
+  int method;
+  bool objective;
+  double lam;
+  const void* A;  // dense A (nullptr with csr)
+  bool f64, panel;
+  long long lda, N, K;
+  const double* v;
+  const float2* v2;
+  const ca_csr_dev* csr;
+  double* rq;     // check_rows zeros
+  double* racc;   // kCheckAcc doubles
+  const double* x;
+  const double* yv;
+  double cP, cI, cY;
+};
+
+int full_check(ca_ctx* ctx, const CheckArgs& c, double* res, double* gap, double* fval) {
+  const int nacc = c.objective ? kCheckAcc : 1;
+  CA_TRY_CUDA(cudaMemsetAsync(c.racc, 0, nacc * sizeof(double), ctx->stream));
   prof_mark(ctx, PC_OTHER);
-  launch_residual(ctx->stream, ctx->num_sms, A, f64, panel, lda, N, K, v, v2, csr, rq, x, yv, cP,
-                  cI, cY, racc);
-  prof_mark(ctx, PC_OTHER);
+  launch_residual(ctx->stream, ctx->num_sms, c.A, c.f64, c.panel, c.lda, c.N, c.K, c.v, c.v2,
+                  c.csr, c.rq, c.x, c.yv, c.cP, c.cI, c.cY, c.racc);
   ctx->prof.kernel_launches += 2;
+  if (c.objective) {
+    launch_sumsq(ctx->stream, ctx->num_sms, c.rq, c.v, nullptr, c.K, 1.0, 0.0, c.racc + 1);
+    if (c.method == 0) {  // ||w||^2
+      launch_sumsq(ctx->stream, ctx->num_sms, c.rq, c.x, nullptr, c.N, 1.0, 0.0, c.racc + 2);
+      ctx->prof.kernel_launches += 2;
+    } else {              // ||alpha + y||^2, ||y||^2
+      launch_sumsq(ctx->stream, ctx->num_sms, c.rq, c.x, c.yv, c.N, 1.0, 1.0, c.racc + 2);
+      launch_sumsq(ctx->stream, ctx->num_sms, c.rq, c.yv, nullptr, c.N, 1.0, 0.0, c.racc + 3);
+      ctx->prof.kernel_launches += 3;
+    }
+  }
+  prof_mark(ctx, PC_OTHER);
   CA_TRY_CUDA(cudaGetLastError());
   double* h = reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->h_err) + 32);
-  CA_TRY_CUDA(cudaMemcpyAsync(h, racc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CA_TRY_CUDA(cudaMemcpyAsync(h, c.racc, nacc * sizeof(double), cudaMemcpyDeviceToHost,
+                              ctx->stream));
   CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-  *out = std::sqrt(*h);
+  const double r2 = h[0];
+  *res = std::sqrt(r2);
+  if (c.method == 0) {
+    *gap = r2 / (2.0 * c.lam);
+    if (c.objective) *fval = 0.5 * c.lam * h[2] + h[1] / (2.0 * (double)c.K);
+  } else {
+    *gap = r2 / (2.0 * (double)c.N);
+    if (c.objective) {
+      const double D = 0.5 * c.lam * h[1] + h[2] / (2.0 * (double)c.N);
+      *fval = h[3] / (2.0 * (double)c.N) - D + *gap;
+    }
+  }
   return CA_OK;
+}
+
+// The decision of a check after the start (tol = 0: never stop).
+bool check_says_stop(const ca_opts* o, const ca_info& in) {
+  if (!(o->tol > 0.0)) return false;
+  if (o->stop == CA_STOP_OBJECTIVE) return in.gap <= o->tol * (in.fval - in.gap);
+  return in.res <= o->tol * in.res0;
 }
 
 int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const double* y0,
@@ -395,10 +458,12 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   auto due = [&](long long k) { return o->recompute_every > 0 && (k + 1) % o->recompute_every == 0; };
   // stopping test (Sec. 5.1.5)
   const bool chk = o->check_every > 0;
-  ctx->info = ca_info{H, 0, 0.0, 0.0};
+  ctx->info = ca_info{H, 0, 0.0, 0.0, 0.0, 0.0};
+  const CheckArgs ck{pb.method, o->stop == CA_STOP_OBJECTIVE, o->lam, pb.A,
+                     pb.xfmt == CA_DENSE_F64, pb.panel, pb.lda, pb.N, K, pb.v, pb.v2, nullptr,
+                     pb.rq, pb.racc, pb.x, pb.yv, pb.cP, pb.cI, pb.cY};
   auto residual = [&](double* out) {
-    return full_residual(ctx, pb.A, pb.xfmt == CA_DENSE_F64, pb.panel, pb.lda, pb.N, K, pb.v,
-                         pb.v2, nullptr, pb.rq, pb.racc, pb.x, pb.yv, pb.cP, pb.cI, pb.cY, out);
+    return full_check(ctx, ck, out, &ctx->info.gap, &ctx->info.fval);
   };
   if (chk) {
     CA_TRY(residual(&ctx->info.res0));
@@ -459,7 +524,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
       if (due(k)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
       CA_TRY(residual(&ctx->info.res));
       ++ctx->info.checks;
-      if (o->tol > 0.0 && ctx->info.res <= o->tol * ctx->info.res0) {
+      if (check_says_stop(o, ctx->info)) {
         ctx->info.h_done = (k + 1) * (long long)s;
         return CA_OK;
       }
@@ -512,7 +577,7 @@ size_t dense_base_need(ca_ctx* ctx, const ca_opts* o, int method, int xf, bool p
   if (method == 0) need += align256((size_t)n * 8);  // rho
   if (tc && !pre) need += align256(panel_bytes(N, K)) + 256;
   if (tc && o->prec == CA_GRAM_FP16_SCALED) need += align256((size_t)N * 4) + 256;
-  if (o->check_every > 0) need += align256((size_t)N * 8) + 512;
+  if (o->check_every > 0) need += align256((size_t)check_rows(o, N, K) * 8) + 512;
   return need;
 }
 
@@ -573,7 +638,7 @@ int ca_bcd_init(ca_ctx** out, int device, void* cuda_stream, size_t scratch_byte
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   ctx->scratch_max = scratch_bytes_max;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess || cudaMallocHost(&ctx->h_err, 64) != cudaSuccess) {
+  if (cudaMalloc(&ctx->d_err, 256) != cudaSuccess || cudaMallocHost(&ctx->h_err, 128) != cudaSuccess) {
     cudaGetLastError();
     ca_bcd_destroy(ctx);
     return CA_ERR_CUDA;
@@ -685,12 +750,13 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   float2* rho2 = cv.take<float2>((size_t)(n + 31) / 32 * 32);
   float2* w2s = cv.take<float2>((size_t)d);
   int* idx = cv.take<int>((size_t)o->H * o->b);
-  double* rq = nullptr;  // stopping test: N doubles (zero between uses) and an accumulator
+  double* rq = nullptr;  // stopping test: zero scratch and the accumulators
   double* racc = nullptr;
   if (o->check_every > 0) {
-    rq = cv.take<double>((size_t)d);
-    racc = cv.take<double>(1);
-    CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)d * 8, ctx->stream));
+    const long long rows = check_rows(o, d, n);
+    rq = cv.take<double>((size_t)rows);
+    racc = cv.take<double>(kCheckAcc);
+    CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)rows * 8, ctx->stream));
   }
   char* work = static_cast<char*>(ctx->arena) + align256(cv.off);  // after every carve above
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
@@ -699,6 +765,7 @@ int ca_bcd_solve(ca_ctx* ctx, int xfmt, const void* X, long long d, long long n,
   pb.xfmt = xf;
   pb.A = Xd;
   pb.panel = panel;
+  pb.method = 0;
   pb.N = d;
   pb.K = n;
   pb.lda = ld;
@@ -770,7 +837,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     // row pairs of the transposed Rs)
     const size_t sbp = (size_t)(sbm + 31) / 32 * 32;
     need += 2 * align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
-    if (o->check_every > 0) need += align256((size_t)n * 8) + 512;
+    if (o->check_every > 0) need += align256((size_t)check_rows(o, n, d) * 8) + 512;
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
     bool st;
@@ -790,14 +857,16 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* rq = nullptr;
     double* racc = nullptr;
     if (o->check_every > 0) {  // stopping test scratch (zero between uses)
-      rq = cv.take<double>((size_t)n);
-      racc = cv.take<double>(1);
-      CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)n * 8, ctx->stream));
+      const long long rows = check_rows(o, n, d);
+      rq = cv.take<double>((size_t)rows);
+      racc = cv.take<double>(kCheckAcc);
+      CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)rows * 8, ctx->stream));
     }
     const ca_csr_dev cdev{rp, col, val};
+    const CheckArgs ck{1, o->stop == CA_STOP_OBJECTIVE, o->lam, nullptr, false, false, 0, n, d,
+                       wd, nullptr, &cdev, rq, racc, ad, yd, 1.0, 1.0, 1.0};
     auto residual = [&](double* out) {  // X^T w - alpha - y (Sec. 5.1.5)
-      return full_residual(ctx, nullptr, false, false, 0, n, d, wd, nullptr, &cdev, rq, racc, ad,
-                           yd, 1.0, 1.0, 1.0, out);
+      return full_check(ctx, ck, out, &ctx->info.gap, &ctx->info.fval);
     };
     auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
       k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
@@ -811,7 +880,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     CA_TRY_CUDA(cudaGetLastError());
     const int b = o->b, s = o->s;
     const long long n_outer = (o->H + s - 1) / s;
-    ctx->info = ca_info{o->H, 0, 0.0, 0.0};
+    ctx->info = ca_info{o->H, 0, 0.0, 0.0, 0.0, 0.0};
     if (o->check_every > 0) {
       CA_TRY(residual(&ctx->info.res0));
       ctx->info.res = ctx->info.res0;
@@ -846,7 +915,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       if (o->check_every > 0 && ((k + 1) % o->check_every == 0 || k + 1 == n_outer)) {
         CA_TRY(residual(&ctx->info.res));
         ++ctx->info.checks;
-        if (k + 1 < n_outer && o->tol > 0.0 && ctx->info.res <= o->tol * ctx->info.res0) {
+        if (k + 1 < n_outer && check_says_stop(o, ctx->info)) {
           ctx->info.h_done = (k + 1) * (long long)s;
           break;
         }
@@ -905,12 +974,13 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   float2* w2 = cv.take<float2>((size_t)(d + 31) / 32 * 32);
   float2* a2s = cv.take<float2>((size_t)n);
   int* idx = cv.take<int>((size_t)o->H * o->b);
-  double* rq = nullptr;  // stopping test: N doubles (zero between uses) and an accumulator
+  double* rq = nullptr;  // stopping test: zero scratch and the accumulators
   double* racc = nullptr;
   if (o->check_every > 0) {
-    rq = cv.take<double>((size_t)n);
-    racc = cv.take<double>(1);
-    CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)n * 8, ctx->stream));
+    const long long rows = check_rows(o, n, d);
+    rq = cv.take<double>((size_t)rows);
+    racc = cv.take<double>(kCheckAcc);
+    CA_TRY_CUDA(cudaMemsetAsync(rq, 0, (size_t)rows * 8, ctx->stream));
   }
   char* work = static_cast<char*>(ctx->arena) + align256(cv.off);  // after every carve above
   CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
@@ -918,6 +988,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
   pb.xfmt = xf;
   pb.A = Xd;
   pb.panel = panel;
+  pb.method = 1;
   pb.N = n;
   pb.K = d;
   pb.lda = ld;

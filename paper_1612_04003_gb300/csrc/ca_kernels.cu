@@ -1419,6 +1419,12 @@ void launch_residual(cudaStream_t st, int num_sms, const void* A, bool f64, bool
   k_residual_norm<<<(unsigned)rg, 256, 0, st>>>(q, x, y, N, cP, cI, cY, out);
 }
 
+void launch_sumsq(cudaStream_t st, int num_sms, double* q, const double* x, const double* y,
+                  long long len, double cx, double cy, double* out) {
+  const long long rg = std::max(1LL, std::min<long long>((len + 255) / 256, 2LL * num_sms));
+  k_residual_norm<<<(unsigned)rg, 256, 0, st>>>(q, x, y, len, 0.0, -cx, -cy, out);
+}
+
 // Scaled FP16 Gram: for each row r of the N x K FP32 matrix A (row-major,
 // leading dimension lda, or 32-column panels), the power of two
 // rscale[r] = 2^(15 - e), where max_k |A[r][k]| = m 2^e with m in [0.5, 1):

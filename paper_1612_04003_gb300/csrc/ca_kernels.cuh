@@ -91,6 +91,11 @@ void launch_residual(cudaStream_t st, int num_sms, const void* A, bool f64, bool
                      long long lda, long long N, long long K, const double* v, const float2* v2,
                      const ca_csr_dev* csr, double* q, const double* x, const double* y,
                      double cP, double cI, double cY, double* out);
+// *out += sum_{r < len} (cx x[r] + cy y[r])^2 (y may be null), by the
+// residual's reduction kernel with cP = 0; q must hold len zeros (they are
+// written back as zeros).
+void launch_sumsq(cudaStream_t st, int num_sms, double* q, const double* x, const double* y,
+                  long long len, double cx, double cy, double* out);
 
 // Scaled FP16 Gram: per-row power-of-two multipliers of A (k_row_scale).
 void launch_row_scale(cudaStream_t st, const float* A, long long lda, long long N, long long K,

@@ -68,6 +68,8 @@ int run_request(ca_server* s, int w, long long id) {
   out.h_done = st == CA_OK ? info.h_done : 0;
   out.res0 = info.res0;
   out.res = info.res;
+  out.gap = info.gap;
+  out.fval = info.fval;
   return st;
 }
 
