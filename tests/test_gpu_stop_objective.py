@@ -128,7 +128,11 @@ def test_primal_certified_relative_objective_error(ctx, mid, prec):
     f = oracle.primal_objective(X64, y, lam, wg)
     r = oracle.primal_residual(X64, y, lam, wg)
     assert abs(info["fval"] - f) <= 1e-8 * f
-    assert abs(info["gap"] - r @ r / (2 * lam)) <= 1e-3 * (r @ r / (2 * lam)) + 1e-15 * f
+    g_own = r @ r / (2 * lam)
+    # FP32 X: the residual pass sums FP32 partials of x v; its gap is within
+    # 1e-2 g + 1e-10 f (derived by emulation in test_split_precision_cpu.py)
+    rtol, atol = (1e-6, 1e-14) if prec == "f64" else (1e-2, 1e-10)
+    assert abs(info["gap"] - g_own) <= rtol * g_own + atol * f
     assert (f - fstar) / fstar <= tol
     # the same solve stopped one check earlier: its bound was above tol
     w = torch.zeros(512, dtype=torch.float64, device="cuda")
