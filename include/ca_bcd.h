@@ -210,6 +210,22 @@ int ca_sample_indices(ca_ctx* ctx, unsigned long long seed, long long h0, long l
  * returned CA_OK).  Errors: CA_ERR_ARG. */
 int ca_solve_info(const ca_ctx* ctx, ca_info* out);
 
+/* One check of the stopping test, as recorded by ca_solve_trace. */
+typedef struct {
+  long long h;          /* block updates of this solve done at the check (0:
+                         * the start)                                         */
+  double res;           /* ||r||_2                                            */
+  double gap;           /* duality gap                                        */
+  double fval;          /* f(w) of the model (CA_STOP_OBJECTIVE only; else 0) */
+} ca_check;
+
+/* Every check of the last solve on ctx, the one at the start first (the
+ * trajectory behind Sec. 5.1.5's stopping test): copies the first
+ * min(max, *count) of them to out (out may be NULL when max = 0) and their
+ * number to *count.  A solve with check_every = 0 records none.  Errors:
+ * CA_ERR_ARG. */
+int ca_solve_trace(const ca_ctx* ctx, ca_check* out, int max, int* count);
+
 /* Device scratch (bytes) a dense solve takes from ctx's arena when X, y and
  * the iterates are device memory: method 0 = ca_bcd_solve (X d x n), 1 =
  * ca_bdcd_solve (X^T n x d); xfmt CA_DENSE_F64, CA_DENSE_F32 or

@@ -56,6 +56,11 @@ class ca_info(ctypes.Structure):
                 ("res", ctypes.c_double), ("gap", ctypes.c_double), ("fval", ctypes.c_double)]
 
 
+class ca_check(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_longlong), ("res", ctypes.c_double), ("gap", ctypes.c_double),
+                ("fval", ctypes.c_double)]
+
+
 class ca_request(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("xfmt", ctypes.c_int), ("X", ctypes.c_void_p),
                 ("d", ctypes.c_longlong), ("n", ctypes.c_longlong), ("ld", ctypes.c_longlong),
@@ -260,6 +265,20 @@ class Context:
         bound = info.gap / (info.fval - info.gap) if info.fval > info.gap else None
         return {"h_done": info.h_done, "checks": info.checks, "res0": info.res0, "res": info.res,
                 "gap": info.gap, "fval": info.fval, "bound": bound}
+
+    def solve_trace(self) -> list:
+        """Every check of the last solve, the start first: dicts with the
+        block updates done (h), ||r||, the duality gap and f(w) (objective
+        rule only, else 0)."""
+        cnt = ctypes.c_int()
+        st = self._lib.ca_solve_trace(self.handle, None, 0, ctypes.byref(cnt))
+        if st != CA_OK:
+            raise CaError(st, "ca_solve_trace")
+        buf = (ca_check * max(cnt.value, 1))()
+        st = self._lib.ca_solve_trace(self.handle, buf, cnt.value, ctypes.byref(cnt))
+        if st != CA_OK:
+            raise CaError(st, "ca_solve_trace")
+        return [{f: getattr(buf[i], f) for f, _ in ca_check._fields_} for i in range(cnt.value)]
 
     def ca_bcd_solve(self, X, y, w, z=None, *, b, s=1, H, lam, seed=42, prec="tf32",
                      recompute_every=0, h0=0, n=None, ld=None, panels=None, tol=0.0,

@@ -43,6 +43,7 @@ struct ca_ctx {
   unsigned* h_err = nullptr;     // pinned copy (128 bytes: error word; check sums at +32)
   Profile prof;
   ca_info info{};                // outcome of the last solve
+  std::vector<ca_check> trace;   // its checks of the stopping test
   char last_error[256] = {0};    // text of the last failing CUDA call
 };
 
@@ -235,7 +236,8 @@ struct CheckArgs {
   double cP, cI, cY;
 };
 
-int full_check(ca_ctx* ctx, const CheckArgs& c, double* res, double* gap, double* fval) {
+int full_check(ca_ctx* ctx, const CheckArgs& c, long long h_at, double* res, double* gap,
+               double* fval) {
   const int nacc = c.objective ? kCheckAcc : 1;
   CA_TRY_CUDA(cudaMemsetAsync(c.racc, 0, nacc * sizeof(double), ctx->stream));
   prof_mark(ctx, PC_OTHER);
@@ -271,6 +273,7 @@ int full_check(ca_ctx* ctx, const CheckArgs& c, double* res, double* gap, double
       *fval = h[3] / (2.0 * (double)c.N) - D + *gap;
     }
   }
+  ctx->trace.push_back(ca_check{h_at, *res, *gap, c.objective ? *fval : 0.0});
   return CA_OK;
 }
 
@@ -459,14 +462,15 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   // stopping test (Sec. 5.1.5)
   const bool chk = o->check_every > 0;
   ctx->info = ca_info{H, 0, 0.0, 0.0, 0.0, 0.0};
+  ctx->trace.clear();
   const CheckArgs ck{pb.method, o->stop == CA_STOP_OBJECTIVE, o->lam, pb.A,
                      pb.xfmt == CA_DENSE_F64, pb.panel, pb.lda, pb.N, K, pb.v, pb.v2, nullptr,
                      pb.rq, pb.racc, pb.x, pb.yv, pb.cP, pb.cI, pb.cY};
-  auto residual = [&](double* out) {
-    return full_check(ctx, ck, out, &ctx->info.gap, &ctx->info.fval);
+  auto residual = [&](double* out, long long h_at) {
+    return full_check(ctx, ck, h_at, out, &ctx->info.gap, &ctx->info.fval);
   };
   if (chk) {
-    CA_TRY(residual(&ctx->info.res0));
+    CA_TRY(residual(&ctx->info.res0, 0));
     ctx->info.res = ctx->info.res0;
   }
   bool pending = false;  // an update (prev_*) not yet applied
@@ -522,7 +526,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
       // the deferred update of this step first: the residual needs v current
       CA_TRY(update_alone());
       if (due(k)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
-      CA_TRY(residual(&ctx->info.res));
+      CA_TRY(residual(&ctx->info.res, (k + 1) * (long long)s));
       ++ctx->info.checks;
       if (check_says_stop(o, ctx->info)) {
         ctx->info.h_done = (k + 1) * (long long)s;
@@ -535,7 +539,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     if (due(n_outer - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
   }
   if (chk) {
-    CA_TRY(residual(&ctx->info.res));
+    CA_TRY(residual(&ctx->info.res, H));
     ++ctx->info.checks;
   }
   return CA_OK;
@@ -865,8 +869,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     const ca_csr_dev cdev{rp, col, val};
     const CheckArgs ck{1, o->stop == CA_STOP_OBJECTIVE, o->lam, nullptr, false, false, 0, n, d,
                        wd, nullptr, &cdev, rq, racc, ad, yd, 1.0, 1.0, 1.0};
-    auto residual = [&](double* out) {  // X^T w - alpha - y (Sec. 5.1.5)
-      return full_check(ctx, ck, out, &ctx->info.gap, &ctx->info.fval);
+    auto residual = [&](double* out, long long h_at) {  // X^T w - alpha - y (Sec. 5.1.5)
+      return full_check(ctx, ck, h_at, out, &ctx->info.gap, &ctx->info.fval);
     };
     auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
       k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
@@ -881,8 +885,9 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     const int b = o->b, s = o->s;
     const long long n_outer = (o->H + s - 1) / s;
     ctx->info = ca_info{o->H, 0, 0.0, 0.0, 0.0, 0.0};
+    ctx->trace.clear();
     if (o->check_every > 0) {
-      CA_TRY(residual(&ctx->info.res0));
+      CA_TRY(residual(&ctx->info.res0, 0));
       ctx->info.res = ctx->info.res0;
     }
     for (long long k = 0; k < n_outer; ++k) {
@@ -913,7 +918,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       CA_TRY_CUDA(cudaGetLastError());
       if (o->recompute_every > 0 && (k + 1) % o->recompute_every == 0) recompute();
       if (o->check_every > 0 && ((k + 1) % o->check_every == 0 || k + 1 == n_outer)) {
-        CA_TRY(residual(&ctx->info.res));
+        CA_TRY(residual(&ctx->info.res, std::min<long long>((k + 1) * (long long)s, o->H)));
         ++ctx->info.checks;
         if (k + 1 < n_outer && check_says_stop(o, ctx->info)) {
           ctx->info.h_done = (k + 1) * (long long)s;
@@ -1124,6 +1129,14 @@ int ca_bcd_release_scratch(ca_ctx* ctx) {
 int ca_solve_info(const ca_ctx* ctx, ca_info* out) {
   if (!ctx || !out) return CA_ERR_ARG;
   *out = ctx->info;
+  return CA_OK;
+}
+
+int ca_solve_trace(const ca_ctx* ctx, ca_check* out, int max, int* count) {
+  if (!ctx || !count || max < 0 || (max > 0 && !out)) return CA_ERR_ARG;
+  const int n = (int)ctx->trace.size();
+  for (int i = 0; i < std::min(n, max); ++i) out[i] = ctx->trace[(size_t)i];
+  *count = n;
   return CA_OK;
 }
 

@@ -41,6 +41,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.ca_sample_indices(None, 1, 0, 1, 1, 1, None) == ca.CA_ERR_ARG
     assert lib.ca_profile_enable(None, 1) == ca.CA_ERR_ARG
     assert lib.ca_solve_info(None, None) == ca.CA_ERR_ARG
+    assert lib.ca_solve_trace(None, None, 0, None) == ca.CA_ERR_ARG
     assert lib.ca_server_submit(None, None, None) == ca.CA_ERR_ARG
     assert lib.ca_server_create(None, 0, 4, 1 << 20) == ca.CA_ERR_ARG
     h = ctypes.c_void_p()
@@ -78,6 +79,7 @@ def _c_layout(tmp_path, struct, fields):
 
 
 @pytest.mark.parametrize("py,c", [(lambda: ca.ca_opts, "ca_opts"), (lambda: ca.ca_info, "ca_info"),
+                                  (lambda: ca.ca_check, "ca_check"),
                                   (lambda: ca.ca_request, "ca_request"),
                                   (lambda: ca.ca_result, "ca_result"),
                                   (lambda: ca.ca_server_stats, "ca_server_stats")])

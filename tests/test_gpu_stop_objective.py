@@ -217,3 +217,60 @@ def test_served_certified_request_equals_alone(ctx, tiny):
     assert abs(res["gap"] - alone["gap"]) <= 1e-9 * alone["gap"]
     assert abs(res["fval"] - alone["fval"]) <= 1e-12 * alone["fval"]
     assert _rel(_np(w2), _np(w)) < 1e-12
+
+
+def test_trace_primal_objective_non_increasing(ctx, tiny):
+    """Sec. 3.1: each BCD step minimises f exactly over its block, so f never
+    increases; the per-check trace (every outer step here) gives f(w_h) and
+    the gap, each against the oracle's iterate of the same length."""
+    X, y, lam = tiny.X, tiny.y, 1e-3
+    kw = dict(b=4, s=4, H=200, seed=42)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(_dev(X), _dev(y), w, lam=lam, prec="f64", check_every=1, stop="objective",
+                     **kw)
+    info, tr = ctx.solve_info(), ctx.solve_trace()
+    assert len(tr) == info["checks"] + 1 == 51
+    assert [c["h"] for c in tr] == list(range(0, 201, 4))
+    assert tr[0]["res"] == info["res0"] and tr[-1]["res"] == info["res"]
+    assert tr[-1]["gap"] == info["gap"] and tr[-1]["fval"] == info["fval"]
+    fs = [c["fval"] for c in tr]
+    assert all(b <= a * (1 + 1e-13) for a, b in zip(fs, fs[1:]))
+    for c in tr[::10]:
+        wh, _ = oracle.ca_bcd(X, y, lam, H=c["h"], **{k: v for k, v in kw.items() if k != "H"}) \
+            if c["h"] else (np.zeros(64), None)
+        f = oracle.primal_objective(X, y, lam, wh)
+        r = oracle.primal_residual(X, y, lam, wh)
+        assert abs(c["fval"] - f) <= 1e-10 * f
+        assert abs(c["gap"] - r @ r / (2 * lam)) <= 1e-6 * (r @ r / (2 * lam)) + 1e-14 * f
+
+
+def test_trace_dual_objective_non_increasing(ctx, wide):
+    """Sec. 3.2: BDCD minimises D exactly over its block, so D never
+    increases (the primal objective of w(alpha) need not decrease).  From
+    the trace, D = ||y||^2/(2n) + gap - f(w)."""
+    X, y, lam = wide.X, wide.y, 1e-2
+    d, n = X.shape
+    a = torch.zeros(n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(d, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve(_dev(X.T), _dev(y), a, w, lam=lam, prec="f64", b=6, s=3, H=150, seed=9,
+                      check_every=1, stop="objective")
+    tr = ctx.solve_trace()
+    assert len(tr) == 51
+    scale = y @ y / (2 * n)
+    D = [scale + c["gap"] - c["fval"] for c in tr]
+    assert all(b <= a + 1e-13 * scale for a, b in zip(D, D[1:]))
+    assert abs(D[-1] - oracle.dual_objective(X, y, lam, _np(a))) <= 1e-10 * scale
+
+
+def test_trace_residual_rule_records_norms(ctx, tiny):
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w, b=4, s=4, H=200, lam=1e-3, seed=42, prec="f64", check_every=5)
+    info, tr = ctx.solve_info(), ctx.solve_trace()
+    assert len(tr) == info["checks"] + 1 == 11
+    assert [c["h"] for c in tr] == list(range(0, 201, 20))
+    assert all(c["fval"] == 0.0 for c in tr)
+    assert all(abs(c["gap"] - c["res"] ** 2 / 2e-3) <= 1e-12 * c["gap"] for c in tr)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    ctx.ca_bcd_solve(X, y, w, b=4, s=4, H=200, lam=1e-3, seed=42, prec="f64")
+    assert ctx.solve_trace() == []
