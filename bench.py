@@ -349,8 +349,13 @@ def precision_study(args) -> int:
             t = _device_time(stream, lambda: ctx.ca_bcd_solve(X, y, w.zero_(), prec=prec, **kw), 2)
             rel_w = float((w - w_ref).norm() / w_ref.norm())
             f = objective(w)
+            # the same solve with one check at its end: the certified relative
+            # objective error of w_H (duality gap)
+            wc = torch.zeros(d, dtype=torch.float64, device="cuda")
+            ctx.ca_bcd_solve(X, y, wc, prec=prec, check_every=H // s_, stop="objective", **kw)
             rows.append({"cond": cond, "gram": prec, "rel_err_w_vs_fp64": rel_w,
                          "rel_objective_diff": abs(f - f_ref) / abs(f_ref),
+                         "certified_rel_obj_err": ctx.solve_info()["bound"],
                          "block_updates_per_s": H / (t * 1e-3)})
         rows.append({"cond": cond, "gram": "f64 (FP64 X, reference)", "rel_err_w_vs_fp64": 0.0,
                      "rel_objective_diff": 0.0, "block_updates_per_s": H / (t64 * 1e-3)})
@@ -360,6 +365,86 @@ def precision_study(args) -> int:
                       "lambda 1e-6, b=16, s=16, H=8192, recompute every 8 outer steps",
                       "rows": rows, "gram_conditioning": gram_cond}), flush=True)
     ctx.close()
+    return 0
+
+
+def _trajectory(tr, f_star, keep=48):
+    """Rows of a check trace: relative residual, certified and true relative
+    objective error (f* known to within its own certificate; None: f* not
+    certified, no true error); at most keep rows, evenly spaced, the first
+    and last included."""
+    r0 = tr[0]["res"] if tr and tr[0]["res"] > 0 else 1.0
+    idx = sorted(set(int(round(i * (len(tr) - 1) / max(keep - 1, 1))) for i in range(keep)))
+    rows = []
+    for i in idx:
+        c = tr[i]
+        f, g = c["fval"], c["gap"]
+        rows.append({"h": c["h"], "rel_residual": c["res"] / r0,
+                     "certified_rel_obj_err": (g / (f - g)) if f > g else None,
+                     "true_rel_obj_err": (f - f_star) / f_star if f_star else None})
+    return rows
+
+
+def stopping_study(args) -> int:
+    """--stopping-study: the stopping test along a solve (Sec. 5.1.5; the
+    analogue of the paper's stopping-criterion figure).  At every check: the
+    relative residual ||r||/||r_0||, the certified relative objective error
+    gap/(f - gap) (duality gap) and the true relative objective error
+    (f - f*)/f*, with f* from the same solve continued to a certified 1e-13
+    (f* taken as f - gap/2 there; reported only when that run certified
+    1e-9 or better).  Dense primal CA-BCD on
+    the benchmark's X 4096 x 262144 FP32 (BF16x3 Gram, b = 8, s = 16,
+    lambda 1e-4, a check every 4 outer steps) and sparse dual CA-BDCD on the
+    CSR of X^T 16384 x 131072 (b = 8, s = 8, lambda 1e-5, FP64, f of the model
+    w(alpha)).  One JSON line."""
+    import numpy as np
+    import torch
+    import paper_1612_04003_gb300 as ca
+    import synth
+    ca.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = ca.Context(0, stream=stream.cuda_stream)
+    out = {}
+    X, y, _ = synth.dense_primal_torch(D, N_SAMPLES, cond=COND, seed=1, device="cuda")
+    Xp = torch.empty(((N_SAMPLES + 31) // 32) * D * 32, dtype=torch.float32, device="cuda")
+    ctx.ca_pack_panels(X, Xp)
+    del X
+    w = torch.zeros(D, dtype=torch.float64, device="cuda")
+    kw = dict(b=B, s=S, lam=LAM, seed=42, prec=PREC, panels=(D, N_SAMPLES), stop="objective")
+    ctx.ca_bcd_solve(Xp, y, w, H=1 << 18, tol=1e-13, check_every=64, **kw)
+    fin = ctx.solve_info()
+    # f* to within gap/2; unusable unless certified tightly
+    f_star = fin["fval"] - fin["gap"] / 2 if (fin["bound"] or 1.0) <= 1e-9 else None
+    w.zero_()
+    h_run = max(S, min(1 << 18, fin["h_done"]))
+    ctx.ca_bcd_solve(Xp, y, w, H=h_run, tol=0.0, check_every=4, **kw)
+    out["primal"] = {"workload": "dense primal CA-BCD, X 4096 x 262144 FP32 (cond 1e3), "
+                                 "lambda 1e-4, b=8, s=16, BF16x3 Gram, a check every 4 outer steps",
+                     "f_star": f_star, "f_star_certified_rel": fin["bound"],
+                     "h_to_certify_1e-13": fin["h_done"],
+                     "rows": _trajectory(ctx.solve_trace(), f_star)}
+    del Xp, y
+    sp = synth.sparse_dual()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    csr = (dev(sp.rowptr), dev(sp.col), dev(sp.val))
+    ys = dev(sp.y)
+    a = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
+    wd = torch.zeros(sp.d, dtype=torch.float64, device="cuda")
+    kw = dict(b=8, s=8, lam=1e-5, seed=42, prec="f64", d=sp.d, stop="objective")
+    ctx.ca_bdcd_solve(csr, ys, a, wd, H=1 << 17, tol=1e-13, check_every=16, **kw)
+    fin = ctx.solve_info()
+    f_star = fin["fval"] - fin["gap"] / 2 if (fin["bound"] or 1.0) <= 1e-9 else None
+    a.zero_()
+    h_run = max(8, min(1 << 17, fin["h_done"]))
+    ctx.ca_bdcd_solve(csr, ys, a, wd, H=h_run, tol=0.0, check_every=4, **kw)
+    out["dual"] = {"workload": "sparse dual CA-BDCD, CSR of X^T 16384 x 131072 (0.5%, Pareto "
+                               "nnz per feature), lambda 1e-5, b=8, s=8, a check every 4 outer steps",
+                   "f_star": f_star, "f_star_certified_rel": fin["bound"],
+                   "h_to_certify_1e-13": fin["h_done"],
+                   "rows": _trajectory(ctx.solve_trace(), f_star)}
+    ctx.close()
+    print(json.dumps({"study": "stopping", **out}), flush=True)
     return 0
 
 
@@ -485,6 +570,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=int, default=32)
     ap.add_argument("--serve-stop", default="residual", choices=["residual", "objective"],
                     help="stopping rule of the served requests")
+    ap.add_argument("--stopping-study", action="store_true",
+                    help="relative residual, certified and true objective error along a solve")
     ap.add_argument("--s", type=int, default=None, help="unrolling depth (default %d)" % S)
     ap.add_argument("--n", type=int, default=None,
                     help="samples (columns of X); smaller than the default only for profiler captures")
@@ -501,6 +588,8 @@ def main():
         return precision_study(args)
     if args.serve:
         return serve_study(args)
+    if args.stopping_study:
+        return stopping_study(args)
     s_run = args.s or S
     n_run = args.n or N_SAMPLES
     h_run = args.h or H

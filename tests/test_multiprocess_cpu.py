@@ -63,3 +63,22 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--gpus", "2", "--steps", "1", "--warmup", "3"],
                        capture_output=True, text=True, timeout=120, env=env, cwd=ROOT)
     assert r.returncode == 0 and r.stdout.strip() == "", r.stdout + r.stderr
+
+
+def test_stopping_study_rows():
+    """bench.py's stopping-study rows from a check trace: relative residual,
+    the certified bound gap/(f - gap) (None while f <= gap) and the true
+    relative error against f*; at most `keep` rows, first and last kept."""
+    sys.path.insert(0, ROOT)
+    import bench
+    tr = [{"h": 16 * i, "res": 2.0 ** -i, "gap": 4.0 ** -i, "fval": 1.0 + 2.0 ** -i}
+          for i in range(100)]
+    tr[0]["gap"] = 5.0  # gap above f: no certificate yet
+    rows = bench._trajectory(tr, 1.0, keep=10)
+    assert len(rows) == 10 and rows[0]["h"] == 0 and rows[-1]["h"] == 16 * 99
+    assert rows[0]["rel_residual"] == 1.0 and rows[0]["certified_rel_obj_err"] is None
+    r = rows[5]
+    i = r["h"] // 16
+    assert abs(r["certified_rel_obj_err"] - 4.0 ** -i / (1.0 + 2.0 ** -i - 4.0 ** -i)) < 1e-15
+    assert abs(r["true_rel_obj_err"] - 2.0 ** -i) < 1e-15
+    assert all(x["true_rel_obj_err"] is None for x in bench._trajectory(tr, None, keep=5))
