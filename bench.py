@@ -415,7 +415,8 @@ def stopping_study(args) -> int:
     ctx.ca_bcd_solve(Xp, y, w, H=1 << 18, tol=1e-13, check_every=64, **kw)
     fin = ctx.solve_info()
     # f* to within gap/2; unusable unless certified tightly
-    f_star = fin["fval"] - fin["gap"] / 2 if (fin["bound"] or 1.0) <= 1e-9 else None
+    certified = fin["bound"] is not None and fin["bound"] <= 1e-9
+    f_star = fin["fval"] - fin["gap"] / 2 if certified else None
     w.zero_()
     h_run = max(S, min(1 << 18, fin["h_done"]))
     ctx.ca_bcd_solve(Xp, y, w, H=h_run, tol=0.0, check_every=4, **kw)
@@ -434,7 +435,8 @@ def stopping_study(args) -> int:
     kw = dict(b=8, s=8, lam=1e-5, seed=42, prec="f64", d=sp.d, stop="objective")
     ctx.ca_bdcd_solve(csr, ys, a, wd, H=1 << 17, tol=1e-13, check_every=16, **kw)
     fin = ctx.solve_info()
-    f_star = fin["fval"] - fin["gap"] / 2 if (fin["bound"] or 1.0) <= 1e-9 else None
+    certified = fin["bound"] is not None and fin["bound"] <= 1e-9
+    f_star = fin["fval"] - fin["gap"] / 2 if certified else None
     a.zero_()
     h_run = max(8, min(1 << 17, fin["h_done"]))
     ctx.ca_bdcd_solve(csr, ys, a, wd, H=h_run, tol=0.0, check_every=4, **kw)
