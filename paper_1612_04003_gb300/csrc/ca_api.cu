@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "ca_bcd.h"
+#include "ca_check.h"
 #include "ca_kernels.cuh"
 
 namespace {
@@ -261,18 +262,7 @@ int full_check(ca_ctx* ctx, const CheckArgs& c, long long h_at, double* res, dou
   CA_TRY_CUDA(cudaMemcpyAsync(h, c.racc, nacc * sizeof(double), cudaMemcpyDeviceToHost,
                               ctx->stream));
   CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-  const double r2 = h[0];
-  *res = std::sqrt(r2);
-  if (c.method == 0) {
-    *gap = r2 / (2.0 * c.lam);
-    if (c.objective) *fval = 0.5 * c.lam * h[2] + h[1] / (2.0 * (double)c.K);
-  } else {
-    *gap = r2 / (2.0 * (double)c.N);
-    if (c.objective) {
-      const double D = 0.5 * c.lam * h[1] + h[2] / (2.0 * (double)c.N);
-      *fval = h[3] / (2.0 * (double)c.N) - D + *gap;
-    }
-  }
+  check_values(c.method, c.objective, c.lam, c.N, c.K, h, res, gap, fval);
   ctx->trace.push_back(ca_check{h_at, *res, *gap, c.objective ? *fval : 0.0});
   return CA_OK;
 }

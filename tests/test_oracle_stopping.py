@@ -242,3 +242,4 @@ def test_dual_certified_run(wide):
     assert h2 == 15 * (j + 1)
     fstar = oracle.primal_objective(X, y, lam, oracle.closed_form(X, y, lam))
     assert (oracle.primal_objective(X, y, lam, w2) - fstar) / fstar <= tol
+
