@@ -26,7 +26,7 @@ FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + 
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(INCLUDE, "ca_bcd.h"))
+    files += [os.path.join(INCLUDE, h) for h in ("ca_bcd.h", "ca_serve.h")]
     return files
 
 
