@@ -274,3 +274,27 @@ def test_trace_residual_rule_records_norms(ctx, tiny):
     w = torch.zeros(64, dtype=torch.float64, device="cuda")
     ctx.ca_bcd_solve(X, y, w, b=4, s=4, H=200, lam=1e-3, seed=42, prec="f64")
     assert ctx.solve_trace() == []
+
+
+def test_served_s_by_measured_cost(ctx, tiny):
+    """Serving: requests submitted with s = 0 get their unrolling depth from
+    measured cost -- each candidate s (s*b <= 256, in the order 8, 16, 4, 32,
+    2, 1, 64) once per shape class, then the cheapest so far; every result
+    equals the same solve made alone with the s it reports."""
+    import paper_1612_04003_gb300 as ca
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    kw = dict(b=4, H=96, lam=1e-3, seed=42, prec="f64")
+    srv = ca.Server(0, workers=1, budget_bytes=1 << 30)
+    outs = []
+    for _ in range(9):  # one after another: each choice sees the earlier costs
+        w = torch.zeros(64, dtype=torch.float64, device="cuda")
+        outs.append((srv.wait(srv.submit("primal", X, y, w, None, s=0, **kw)), w))
+    srv.close()
+    cands = [8, 16, 4, 32, 2, 1, 64]
+    assert [r["s"] for r, _ in outs[:7]] == cands
+    assert all(r["s"] in cands for r, _ in outs[7:])
+    for r, w in outs:
+        assert r["status"] == ca.CA_OK and r["h_done"] == 96
+        w_alone = torch.zeros(64, dtype=torch.float64, device="cuda")
+        ctx.ca_bcd_solve(X, y, w_alone, s=r["s"], **kw)
+        assert _rel(_np(w), _np(w_alone)) < 1e-12
