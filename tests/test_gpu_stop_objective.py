@@ -10,6 +10,9 @@ Checked here: gap and f(w) against the oracle at the GPU's own iterate; the
 update count of the stop against the oracle's certified run (tolerance
 chosen between two clearly separated checks); the certificate against the
 closed-form optimum; the stop at the first check under the tolerance.
+Also the per-check trace (f non-increasing under BCD, D under BDCD) and,
+for the serving loop, a certified request and requests whose unrolling
+depth s the server picks by measured cost.
 """
 import numpy as np
 import pytest
