@@ -407,7 +407,9 @@ class Server:
                ld=None, panels=None) -> int:
         """method "primal" (X d x ld, x = w, aux = z or None) or "dual"
         (X = X^T n x ld, x = alpha, aux = w); panels=(rows, cols) for
-        pre-packed FP32 panels."""
+        pre-packed FP32 panels.  s = 0: the server picks s by measured cost
+        (the result's "s"); stop="objective": end at a certified relative
+        objective error tol (the result's "gap" and "fval")."""
         m = {"primal": 0, "dual": 1}[method]
         o = Context._opts(b, s, H, lam, seed, prec, recompute_every, 0, tol, check_every, stop)
         if panels is not None:  # primal (d, n), dual (n, d)
