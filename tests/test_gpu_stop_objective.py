@@ -301,3 +301,13 @@ def test_served_s_by_measured_cost(ctx, tiny):
         w_alone = torch.zeros(64, dtype=torch.float64, device="cuda")
         ctx.ca_bcd_solve(X, y, w_alone, s=r["s"], **kw)
         assert _rel(_np(w), _np(w_alone)) < 1e-12
+
+
+def test_unknown_stopping_rule_is_refused(ctx, tiny):
+    import paper_1612_04003_gb300 as ca
+    X, y = _dev(tiny.X), _dev(tiny.y)
+    w = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(ca.CaError) as e:
+        ctx.ca_bcd_solve(X, y, w, b=4, s=4, H=40, lam=1e-3, prec="f64", check_every=2, stop=2)
+    assert e.value.status == ca.CA_ERR_ARG
+    assert float(w.abs().max()) == 0.0
