@@ -12,7 +12,8 @@ chosen between two clearly separated checks); the certificate against the
 closed-form optimum; the stop at the first check under the tolerance.
 Also the per-check trace (f non-increasing under BCD, D under BDCD) and,
 for the serving loop, a certified request and requests whose unrolling
-depth s the server picks by measured cost.
+depth s the server picks by measured cost.  Collected after the parity and
+serving suites.
 """
 import numpy as np
 import pytest
