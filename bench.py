@@ -2,9 +2,9 @@
 
 Workload (the dense primal FP32 configuration): X 4096 x 262144 FP32 with
 geometrically scaled rows (condition 1e3), y = X^T w_true + 1% noise,
-lambda = 1e-4, b = 8, s = 16, H = 4096 block updates, FP32-faithful Gram on
-the tensor cores (3xTF32 split products, FP32 accumulation), FP64-accurate
-solves.  One step = one full solve (sampling, H/s outer steps of
+lambda = 1e-4, b = 8, s = 16, H = 4096 block updates, BF16x3 split-product
+Gram on the tensor cores (FP32 accumulation), double-float (~2^-44) b x b
+solves and vector updates, FP64 vectors.  One step = one full solve (sampling, H/s outer steps of
 gather+Gram+projection, inner solves, deferred update, and the final
 z = X^T w_H pass) with X resident in HBM.  X (4 GiB) is larger than L2.
 X is resident in the library's 32-column panel layout (packed once, as a
@@ -42,16 +42,17 @@ D, N_SAMPLES, COND, LAM, B, S, H = 4096, 262144, 1e3, 1e-4, 8, 16, 4096
 # accumulate (meets the FP32 path's 1e-5 iterate tolerance; the fastest mode
 # that does)
 PREC = "bf16x3"
-DTYPE = {"bf16x3": "bf16x3 (bf16 split products, fp32 accumulate; fp64 solves)",
-         "fp16_scaled": "fp16 (per-row power-of-two scaling, fp32 accumulate; fp64 solves)",
-         "3xtf32": "3xtf32 (fp32-faithful split products; fp64 solves)",
-         "tf32": "tf32 (fp32 accumulate; fp64 solves)"}
+_DF = "double-float (~2^-44) b x b solves and vector updates, fp64 vectors"
+DTYPE = {"bf16x3": f"bf16x3 Gram (bf16 split products, fp32 accumulate); {_DF}",
+         "fp16_scaled": f"fp16 Gram (per-row power-of-two scaling, fp32 accumulate); {_DF}",
+         "3xtf32": f"3xtf32 Gram (fp32-faithful split products); {_DF}",
+         "tf32": f"tf32 Gram (fp32 accumulate); {_DF}"}
 
 
 def workload_config(d=D, n=N_SAMPLES, b=B, s=S, h=H, prec=PREC):
     return {
         "workload": f"dense primal CA-BCD, FP32 X {d}x{n} (cond 1e3 geometric rows), "
-                    f"lambda 1e-4, b={b}, s={s}, H={h}, {prec} tcgen05 Gram, FP64 solves",
+                    f"lambda 1e-4, b={b}, s={s}, H={h}, {prec} tcgen05 Gram, double-float solves",
         "d": d, "n": n, "b": b, "s": s, "H": h, "lambda": LAM, "gram": prec,
         "l2": "inputs larger than L2 (X is 4 GiB, L2 129 MB); no flush needed",
         "step": "one full solve of H block updates incl. sampling and final z = X^T w_H",
@@ -162,7 +163,8 @@ def barrier(world: int):
         dist.barrier()
 
 
-def time_solves(ctx, X, y, w, z, steps, stream, b=B, s=S, h=H, prec=PREC, panels=None):
+def time_solves(ctx, X, y, w, z, steps, stream, b=B, s=S, h=H, prec=PREC, panels=None,
+                solve="df"):
     """Device time (ms) of `steps` back-to-back solves, CUDA events on the
     library's stream.  panels=(d, n): X holds the 32-column panel layout."""
     import torch
@@ -172,10 +174,38 @@ def time_solves(ctx, X, y, w, z, steps, stream, b=B, s=S, h=H, prec=PREC, panels
     e0.record(stream)
     for _ in range(steps):
         w.zero_()
-        ctx.ca_bcd_solve(X, y, w, z, b=b, s=s, H=h, lam=LAM, seed=42, prec=prec, panels=panels)
+        ctx.ca_bcd_solve(X, y, w, z, b=b, s=s, H=h, lam=LAM, seed=42, prec=prec, panels=panels,
+                         solve=solve)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+def certified_race(ctx, XP, y, pan, tol=1e-6, h_cap=1 << 17):
+    """The headline solve in each Gram mode, run until its certified relative
+    objective error (the duality gap bound gap / (f(w) - gap), a check every
+    16 outer steps) is <= tol: wall time of the call (the checks wait for the
+    GPU), block updates done, and the bound reached (h_cap block updates at
+    most)."""
+    import torch
+    rows = []
+    for prec_ in ("3xtf32", "bf16x3", "fp16_scaled", "tf32"):
+        w_ = torch.zeros(D, dtype=torch.float64, device="cuda")
+        kw = dict(b=B, s=S, H=h_cap, lam=LAM, seed=42, prec=prec_, panels=pan, tol=tol,
+                  check_every=16, stop="objective")
+        ctx.ca_bcd_solve(XP, y, w_, **kw)  # warm
+        w_.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.ca_bcd_solve(XP, y, w_, **kw)
+        dt = time.perf_counter() - t0
+        info = ctx.solve_info()
+        rows.append({"gram": prec_, "seconds_to_stop": dt, "h_done": info["h_done"],
+                     "block_updates_per_s": info["h_done"] / dt,
+                     "certified_rel_obj_err": info["bound"],
+                     "certified": info["bound"] is not None and info["bound"] <= tol})
+    return {"tol": tol, "how": "same solve per Gram mode, stop once gap <= tol (f(w) - gap); "
+                               "wall time of the call", "rows": rows}
 
 
 def cpu_baseline(X_host_f32, y_host, budget_s: float = 30.0):
@@ -707,6 +737,19 @@ def main():
                 sweep.append({"gram": prec_, "b": b_, "s": s_, "ms_per_step": t,
                               "block_updates_per_s": h_run / (t * 1e-3)})
 
+    # the b x b solves in FP64 (block Cholesky, CA_SOLVE_F64) against the
+    # double-float default, same K solves
+    solve_f64 = None
+    race = None
+    if not args.no_sweep:
+        time_solves(ctx, XP, y, w, z, 1, stream, s=s_run, h=h_run, panels=pan, solve="f64")
+        t64 = time_solves(ctx, XP, y, w, z, 4, stream, s=s_run, h=h_run, panels=pan,
+                          solve="f64") / 4
+        solve_f64 = {"ms_per_step": t64, "block_updates_per_s": h_run / (t64 * 1e-3),
+                     "how": "same solve with opts.solve = CA_SOLVE_F64 (FP64 Cholesky of each "
+                            "diagonal block, FP64 block forward substitution, one CTA)"}
+        race = certified_race(ctx, XP, y, pan)
+
     # the same roofline for the other Gram modes, same K solves
     roof_other = {}
     secondary = []
@@ -740,6 +783,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(), "sweep": sweep,
+            "solve_fp64": solve_f64, "time_to_certified_1e-6": race,
             **{f"roofline_{p}_gram": r for p, r in roof_other.items()},
             "other_workloads": secondary,
             "input_layout": "X resident on the device in the library's 32-column panel layout "

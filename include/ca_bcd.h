@@ -72,8 +72,16 @@ typedef enum {
                            * tcgen05 Gram modes only                          */
 } ca_xfmt;
 
-/* Arithmetic of the Gram matrix (step a3).  The projection, the solves and
- * all vectors are FP64-accurate in every mode. */
+/* Arithmetic of the Gram matrix (step a3).  The vectors at the boundary
+ * (y, w, alpha, z) are FP64 in every mode; on FP64 X every vector pass is
+ * FP64.  On FP32 X: the projection (a3) and the deferred update (a5) form
+ * FP32 products of X with the FP32 (hi, lo) split of the FP64 vector, summed
+ * in FP32 and compensated FP32 pairs, the update applied in double-float
+ * (two FP32 values, ~2^-44 relative) to the maintained vector; the
+ * recomputation (a6), the final z and the stopping test's residual form
+ * exact products (FMA error terms) summed in double-float, and a check of
+ * the stopping test first rebuilds the maintained vector that way.  The
+ * b x b solves (a4) run in double-float by default or in FP64 (ca_solve). */
 typedef enum {
   CA_GRAM_F64 = 0,        /* FP64 on CUDA cores (any dense X)                   */
   CA_GRAM_FP32_EXACT = 1, /* FP32 X: 3xTF32 split products on tcgen05, FP32 acc. */
@@ -90,6 +98,18 @@ typedef enum {
                            * X.  Not in ca_gram_project_noalloc
                            * (CA_ERR_UNSUPPORTED).                           */
 } ca_prec;
+
+/* Arithmetic of the s unrolled b x b solves (step a4). */
+typedef enum {
+  CA_SOLVE_DF = 0,  /* b <= 32 and s*b <= 256: the diagonal blocks Gamma_j
+                     * inverted up front (Gauss-Jordan sweep) and the
+                     * dependent chain, both in double-float (pairs of FP32,
+                     * ~2^-44 relative: GB300's FP64 pipe is ~1/64 of its
+                     * FP32 pipe); larger b or s*b: as CA_SOLVE_F64          */
+  CA_SOLVE_F64 = 1  /* FP64 throughout: a Cholesky factorisation of each
+                     * Gamma_j in turn and the block forward substitution of
+                     * eq. "recur", as Algorithm 2 / 4 write it (one CTA)     */
+} ca_solve;
 
 /* Stopping rule of the check every check_every outer steps (Sec. 5.1.5). */
 typedef enum {
@@ -126,10 +146,18 @@ typedef struct {
    * maintained vectors (primal: lambda/2 ||w||^2 + ||y - X^T w||^2/(2n);
    * dual: ||y||^2/(2n) - D(alpha) + gap; O(n + d) extra reads) and the
    * solve ends once gap <= tol (f(w) - gap): since f(w*) >= f(w) - gap,
-   * the relative objective error is then certified <= tol.               */
+   * the relative objective error is then certified <= tol.  The
+   * certificate is as exact as the computed gap and f(w): on FP64 X to
+   * FP64 rounding; on FP32 X each check rebuilds the maintained vector from
+   * its definition and forms the residual with exact products summed in
+   * double-float, so gap and f(w) carry errors of order 2^-44 of the sums
+   * of |terms| behind them, far below any tol >= 1e-9 (the bounds are
+   * derived by emulation and tested in the test suite's precision checks).
+   * On FP32 X a check costs two passes over X.                          */
   double tol;
   int check_every;
   int stop;             /* ca_stop; CA_STOP_RESIDUAL unless set             */
+  int solve;            /* ca_solve; CA_SOLVE_DF unless set                  */
 } ca_opts;
 
 /* What the last solve on a context did. */
@@ -144,6 +172,9 @@ typedef struct {
   double gap;           /* duality gap at the last check (0 without checks)    */
   double fval;          /* f(w) of the model at the last check
                          * (CA_STOP_OBJECTIVE only; else 0)                    */
+  double bound;         /* certified relative objective error at the last
+                         * check, gap / (fval - gap) (CA_STOP_OBJECTIVE with
+                         * fval > gap; else -1)                                */
 } ca_info;
 
 /* Dual CSR input: CSR of X^T with n rows (samples) and d columns (features).
@@ -173,8 +204,9 @@ int ca_bcd_init(ca_ctx** ctx, int device, void* cuda_stream, size_t scratch_byte
  *         reads only the panels.  Host X: pageable memory is copied to the
  *         device first; page-locked (pinned) memory is read in place by the
  *         repack.  CA_DENSE_F32_PANELS: X is already in that
- *         layout (ceil(n/32) * d * 32 floats; ld is ignored); TF32 / 3xTF32
- *         only.
+ *         layout (ceil(n/32) * d * 32 floats; ld is ignored); any of the
+ *         tcgen05 Gram modes (TF32, 3xTF32, BF16x3, scaled FP16), not
+ *         CA_GRAM_F64.
  *   y     n labels (FP64).
  *   w     d (FP64): w0 on entry, w_H on return.
  *   z     NULL, or n (FP64): receives X^T w_H computed by a final full pass.
@@ -250,9 +282,11 @@ int ca_bcd_release_scratch(ca_ctx* ctx);
 int ca_gram_project(ca_ctx* ctx, int xfmt, int prec, const void* A, long long N, long long K,
                     long long ld, const int* idx, int sb, const double* v, double* G, double* p);
 
-/* Steps a2+a3 exactly as ca_gram_project computes them, for callers that must
- * not allocate device memory (the paper has no counterpart: this is an
- * interface convenience).  Such callers include code running while a host
+/* Steps a2+a3 as ca_gram_project computes them (the same kernels; the split-K
+ * partials are summed in a different order, so the results agree to
+ * rounding: within 1e-12 relative on FP64 A, and within the Gram mode's
+ * product bound on FP32 A), for callers that must not allocate device memory
+ * (the paper has no counterpart: this is an interface convenience).  Such callers include code running while a host
  * framework owns every device allocation through its own pool, code on a
  * latency-critical path where an allocation's implicit synchronisation is not
  * acceptable, and code that may only enqueue work on a stream it was given.

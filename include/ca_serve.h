@@ -49,6 +49,8 @@ typedef struct {
   double res0, res;       /* residual norms of the stopping test (or 0)     */
   double gap, fval;       /* duality gap and f(w) at the last check
                            * (ca_info; fval under CA_STOP_OBJECTIVE only)   */
+  double bound;           /* certified relative objective error there
+                           * (ca_info.bound; -1 when none)                  */
   double queue_ms;        /* submission -> start                            */
   double run_ms;          /* start -> end                                   */
   double latency_ms;      /* submission -> end                              */

@@ -40,6 +40,10 @@ CA_STOP_RESIDUAL = 0
 CA_STOP_OBJECTIVE = 1
 STOP = {"residual": CA_STOP_RESIDUAL, "objective": CA_STOP_OBJECTIVE}
 
+CA_SOLVE_DF = 0
+CA_SOLVE_F64 = 1
+SOLVE = {"df": CA_SOLVE_DF, "f64": CA_SOLVE_F64}
+
 PREC = {"f64": CA_GRAM_F64, "fp32_exact": CA_GRAM_FP32_EXACT, "3xtf32": CA_GRAM_FP32_EXACT,
         "tf32": CA_GRAM_TF32, "bf16x3": CA_GRAM_BF16X3, "fp16_scaled": CA_GRAM_FP16_SCALED}
 
@@ -48,12 +52,14 @@ class ca_opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("s", ctypes.c_int), ("H", ctypes.c_longlong),
                 ("lam", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("prec", ctypes.c_int),
                 ("recompute_every", ctypes.c_int), ("h0", ctypes.c_longlong),
-                ("tol", ctypes.c_double), ("check_every", ctypes.c_int), ("stop", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("check_every", ctypes.c_int), ("stop", ctypes.c_int),
+                ("solve", ctypes.c_int)]
 
 
 class ca_info(ctypes.Structure):
     _fields_ = [("h_done", ctypes.c_longlong), ("checks", ctypes.c_int), ("res0", ctypes.c_double),
-                ("res", ctypes.c_double), ("gap", ctypes.c_double), ("fval", ctypes.c_double)]
+                ("res", ctypes.c_double), ("gap", ctypes.c_double), ("fval", ctypes.c_double),
+                ("bound", ctypes.c_double)]
 
 
 class ca_check(ctypes.Structure):
@@ -72,7 +78,8 @@ class ca_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("worker", ctypes.c_int), ("s", ctypes.c_int),
                 ("h_done", ctypes.c_longlong),
                 ("res0", ctypes.c_double), ("res", ctypes.c_double), ("gap", ctypes.c_double),
-                ("fval", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("fval", ctypes.c_double), ("bound", ctypes.c_double),
+                ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
                 ("scratch_bytes", ctypes.c_size_t)]
 
@@ -246,25 +253,26 @@ class Context:
 
     @staticmethod
     def _opts(b, s, H, lam, seed, prec, recompute_every, h0, tol=0.0, check_every=0,
-              stop="residual"):
+              stop="residual", solve="df"):
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         st = STOP[stop] if isinstance(stop, str) else int(stop)
+        sv = SOLVE[solve] if isinstance(solve, str) else int(solve)
         return ca_opts(int(b), int(s), int(H), float(lam), int(seed), p, int(recompute_every),
-                       int(h0), float(tol), int(check_every), st)
+                       int(h0), float(tol), int(check_every), st, sv)
 
     def solve_info(self) -> dict:
         """Outcome of the last solve: block updates done (h_done), number of
         full-residual checks, ||r_0|| and ||r|| at the last check, the duality
         gap there, f(w) of the model there (objective rule only, else 0) and
-        the certified relative objective error gap / (f(w) - gap) (None
-        unless f(w) > gap)."""
+        the certified relative objective error gap / (f(w) - gap) the
+        library formed (None unless the objective rule ran and f(w) > gap)."""
         info = ca_info()
         st = self._lib.ca_solve_info(self.handle, ctypes.byref(info))
         if st != CA_OK:
             raise CaError(st, "ca_solve_info")
-        bound = info.gap / (info.fval - info.gap) if info.fval > info.gap else None
         return {"h_done": info.h_done, "checks": info.checks, "res0": info.res0, "res": info.res,
-                "gap": info.gap, "fval": info.fval, "bound": bound}
+                "gap": info.gap, "fval": info.fval,
+                "bound": info.bound if info.bound >= 0.0 else None}
 
     def solve_trace(self) -> list:
         """Every check of the last solve, the start first: dicts with the
@@ -282,7 +290,7 @@ class Context:
 
     def ca_bcd_solve(self, X, y, w, z=None, *, b, s=1, H, lam, seed=42, prec="tf32",
                      recompute_every=0, h0=0, n=None, ld=None, panels=None, tol=0.0,
-                     check_every=0, stop="residual"):
+                     check_every=0, stop="residual", solve="df"):
         """Primal CA-BCD: w (in: w0, out: w_H) and optionally z = X^T w_H.
         X is d x ld (ld = X.shape[1]); n (default ld) columns are used.
         panels=(d, n): X holds the 32-column panels of a d x n matrix
@@ -290,7 +298,8 @@ class Context:
         for a in (y, w) + ((z,) if z is not None else ()):
             if not _dtype_is_f64(a):
                 raise TypeError("y, w, z must be float64")
-        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0, tol, check_every, stop)
+        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0, tol, check_every, stop,
+                       solve)
         if panels is not None:
             d, n = (int(v) for v in panels)
             xf, ld = CA_DENSE_F32_PANELS, 0
@@ -307,14 +316,15 @@ class Context:
 
     def ca_bdcd_solve(self, XT, y, alpha, w, *, b, s=1, H, lam, seed=42, prec="tf32",
                       recompute_every=0, h0=0, d=None, ld=None, panels=None, tol=0.0,
-                      check_every=0, stop="residual"):
+                      check_every=0, stop="residual", solve="df"):
         """Dual CA-BDCD.  XT is X^T (n x d, dense), a (rowptr, col, val) CSR
         triple of X^T (then d must be given), or with panels=(n, d) the
         32-column panels of X^T (ca_pack_panels)."""
         for a in (y, alpha, w):
             if not _dtype_is_f64(a):
                 raise TypeError("y, alpha, w must be float64")
-        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0, tol, check_every, stop)
+        o = self._opts(b, s, H, lam, seed, prec, recompute_every, h0, tol, check_every, stop,
+                       solve)
         if panels is not None:
             n, dd = (int(v) for v in panels)
             st = self._lib.ca_bdcd_solve(self.handle, CA_DENSE_F32_PANELS, _ptr(XT), dd, n, 0,
@@ -403,15 +413,16 @@ class Server:
         self._keep = {}
 
     def submit(self, method, X, y, x, aux=None, *, b, s=1, H, lam, seed=42, prec="tf32",
-               recompute_every=0, tol=0.0, check_every=0, stop="residual", d=None, n=None,
-               ld=None, panels=None) -> int:
+               recompute_every=0, tol=0.0, check_every=0, stop="residual", solve="df", d=None,
+               n=None, ld=None, panels=None) -> int:
         """method "primal" (X d x ld, x = w, aux = z or None) or "dual"
         (X = X^T n x ld, x = alpha, aux = w); panels=(rows, cols) for
         pre-packed FP32 panels.  s = 0: the server picks s by measured cost
         (the result's "s"); stop="objective": end at a certified relative
         objective error tol (the result's "gap" and "fval")."""
         m = {"primal": 0, "dual": 1}[method]
-        o = Context._opts(b, s, H, lam, seed, prec, recompute_every, 0, tol, check_every, stop)
+        o = Context._opts(b, s, H, lam, seed, prec, recompute_every, 0, tol, check_every, stop,
+                          solve)
         if panels is not None:  # primal (d, n), dual (n, d)
             rows, cols = (int(v) for v in panels)
             xf, ldv = CA_DENSE_F32_PANELS, 0

@@ -172,6 +172,7 @@ int check_opts(const ca_opts* o, long long N) {
   if (o->recompute_every < 0) return CA_ERR_ARG;
   if (o->check_every < 0 || !(o->tol >= 0.0) || !std::isfinite(o->tol)) return CA_ERR_ARG;
   if (o->stop != CA_STOP_RESIDUAL && o->stop != CA_STOP_OBJECTIVE) return CA_ERR_ARG;
+  if (o->solve != CA_SOLVE_DF && o->solve != CA_SOLVE_F64) return CA_ERR_ARG;
   if (o->prec < CA_GRAM_F64 || o->prec > CA_GRAM_FP16_SCALED) return CA_ERR_ARG;
   if (N > 2147483647LL) return CA_ERR_UNSUPPORTED;
   if (o->b > kMaxB) return CA_ERR_UNSUPPORTED;
@@ -263,15 +264,14 @@ int full_check(ca_ctx* ctx, const CheckArgs& c, long long h_at, double* res, dou
                               ctx->stream));
   CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
   check_values(c.method, c.objective, c.lam, c.N, c.K, h, res, gap, fval);
+  ctx->info.bound = c.objective ? certified_bound(*fval, *gap) : -1.0;
   ctx->trace.push_back(ca_check{h_at, *res, *gap, c.objective ? *fval : 0.0});
   return CA_OK;
 }
 
 // The decision of a check after the start (tol = 0: never stop).
 bool check_says_stop(const ca_opts* o, const ca_info& in) {
-  if (!(o->tol > 0.0)) return false;
-  if (o->stop == CA_STOP_OBJECTIVE) return in.gap <= o->tol * (in.fval - in.gap);
-  return in.res <= o->tol * in.res0;
+  return check_stops(o->stop == CA_STOP_OBJECTIVE, o->tol, in.res0, in.res, in.gap, in.fval);
 }
 
 int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const double* y0,
@@ -340,12 +340,16 @@ GramPlan gram_plan(ca_ctx* ctx, int xfmt, int prec, int sbm, long long K) {
 }
 
 // a2+a3: split-K partials of Y Y^T and Y v for the sampled rows idx[0..sb).
+// early: the preceding kernel in the stream is the reduce + chain launch,
+// which writes nothing the Gram prologue reads (see GramUpdate::early).
 int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long long lda, long long N,
                 long long K, const int* idx, int sb, const double* v, const float2* v2, void* part,
-                double* ppart, bool panel = false, const float* rscale = nullptr) {
+                double* ppart, bool panel = false, const float* rscale = nullptr,
+                bool early = false) {
   if (g.tc) {
     GramUpdate none{};
     none.rscale = rscale;
+    none.early = early;
     const int e = launch_gram_tc(static_cast<const float*>(A), lda, N, K, idx, sb, v2, g.P, g.sbp,
                                  static_cast<float*>(part), ppart, ctx->d_err, g.three, ctx->stream,
                                  &none, panel);
@@ -356,7 +360,11 @@ int launch_gram(ca_ctx* ctx, const GramPlan& g, int xfmt, const void* A, long lo
   return cuda_status(cudaGetLastError());
 }
 
-bool fast_solve(int b, int sb) { return b <= CA_FAST_B && sb <= CA_FAST_SB; }
+// The double-float fast form of a4 (inverted diagonal blocks + chain), unless
+// the FP64 solve is asked for.
+bool fast_solve(int b, int sb, bool f64solve = false) {
+  return !f64solve && b <= CA_FAST_B && sb <= CA_FAST_SB;
+}
 
 size_t chain_smem(int b, int sb) {
   if (b <= 16) {  // lookahead chain: ring | Gamma^{-1} | rhs0 | Delta | hand-over | indices
@@ -369,8 +377,8 @@ size_t chain_smem(int b, int sb) {
 // a4: the chain (fast form, from Rs, p and the inverted diagonal blocks
 // Ginv) or the general block forward substitution (from R, p).
 void launch_solve(ca_ctx* ctx, const double* R, const float2* Rs, const double* pvec,
-                  const float2* Ginv, const SolveArgs& sa) {
-  if (fast_solve(sa.b, sa.sb)) {
+                  const float2* Ginv, const SolveArgs& sa, bool f64solve) {
+  if (fast_solve(sa.b, sa.sb, f64solve)) {
     launch_chain(sa.b, chain_smem(sa.b, sa.sb), ctx->stream, Rs, pvec, Ginv, sa, ctx->d_err);
   } else {
     k_solve<<<1, 256, (size_t)(sa.sb + sa.b * sa.b + sa.b) * sizeof(double), ctx->stream>>>(
@@ -378,12 +386,18 @@ void launch_solve(ca_ctx* ctx, const double* R, const float2* Rs, const double* 
   }
 }
 
+// Whether launch_reduce_solve runs a4 as the single reduce + chain launch.
+bool uses_reduce_chain(const GramPlan& g, const SolveArgs& sa, bool f64solve) {
+  return g.tc && sa.s_cur > 0 && fast_solve(sa.b, sa.sb, f64solve) && sa.b <= 16;
+}
+
 // a4 entry: reduce the partials to R, p and invert the diagonal blocks (in
 // the reduce launch for b <= 16, by k_factor otherwise), then (s_cur > 0) the
 // inner solves.
 int launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const double* ppart,
-                        double* R, float2* Rs, double* pvec, float2* Ginv, const SolveArgs& sa) {
-  const bool fast = sa.s_cur > 0 && fast_solve(sa.b, sa.sb);
+                        double* R, float2* Rs, double* pvec, float2* Ginv, const SolveArgs& sa,
+                        bool f64solve = false) {
+  const bool fast = sa.s_cur > 0 && fast_solve(sa.b, sa.sb, f64solve);
   const long long entries = (long long)sa.sb * (sa.sb + 1) / 2 + sa.sb;
   const long long passes = (entries + 31) / 32;
   const int G = (int)std::max(1LL, std::min<long long>(passes, 8LL * ctx->num_sms));
@@ -413,7 +427,7 @@ int launch_reduce_solve(ca_ctx* ctx, const GramPlan& g, const void* part, const 
   prof_mark(ctx, PC_SOLVE);
   if (sa.s_cur > 0) {
     prof_mark(ctx, PC_CHAIN);
-    launch_solve(ctx, R, Rs, pvec, Ginv, sa);
+    launch_solve(ctx, R, Rs, pvec, Ginv, sa, f64solve);
     prof_mark(ctx, PC_CHAIN);
     ctx->prof.kernel_launches += 1;
   }
@@ -428,8 +442,10 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   const int sbm = (int)(std::min<long long>(s, H) * b);
   Carve cv{work};
   (void)work_bytes;
+  const bool f64solve = o->solve == CA_SOLVE_F64;
   GramPlan g = gram_plan(ctx, pb.xfmt, o->prec, sbm, K);
-  if (g.tc && pb.panel && g.sbp <= 128 && b <= 16 && fast_solve(b, sbm) && ctx->num_sms > 1) {
+  if (g.tc && pb.panel && g.sbp <= 128 && b <= 16 && fast_solve(b, sbm, f64solve) &&
+      ctx->num_sms > 1) {
     // the chain of step k runs on one SM (last CTA of the reduce launch) while
     // the Gram CTAs of step k+1 prepare: leave that SM to it, so that no Gram
     // CTA starts only after the chain
@@ -451,7 +467,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   auto due = [&](long long k) { return o->recompute_every > 0 && (k + 1) % o->recompute_every == 0; };
   // stopping test (Sec. 5.1.5)
   const bool chk = o->check_every > 0;
-  ctx->info = ca_info{H, 0, 0.0, 0.0, 0.0, 0.0};
+  ctx->info = ca_info{H, 0, 0.0, 0.0, 0.0, 0.0, -1.0};
   ctx->trace.clear();
   const CheckArgs ck{pb.method, o->stop == CA_STOP_OBJECTIVE, o->lam, pb.A,
                      pb.xfmt == CA_DENSE_F64, pb.panel, pb.lda, pb.N, K, pb.v, pb.v2, nullptr,
@@ -459,11 +475,18 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   auto residual = [&](double* out, long long h_at) {
     return full_check(ctx, ck, h_at, out, &ctx->info.gap, &ctx->info.fval);
   };
-  if (chk) {
+  // FP32 X: the deferred updates round their products to FP32, so v drifts
+  // from its definition by ~2^-24 of each step's increment; a check first
+  // rebuilds v from the definition (a6 with exact products summed in
+  // double-float) so that the residual, the gap and f(w) it reports are
+  // those of the current iterate.  (FP64 X: the updates are FP64.)
+  const bool rebuild_at_check = pb.xfmt == CA_DENSE_F32;
+  if (chk) {  // (v was just formed from its definition)
     CA_TRY(residual(&ctx->info.res0, 0));
     ctx->info.res = ctx->info.res0;
   }
   bool pending = false;  // an update (prev_*) not yet applied
+  bool after_rc = false;  // the last kernel in the stream is the reduce + chain launch
   const int* prev_idx = nullptr;
   int prev_sb = 0;
   const double* prev_delta = nullptr;
@@ -476,6 +499,7 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     prof_mark(ctx, PC_UPDATE);
     ctx->prof.kernel_launches += 1;
     pending = false;
+    after_rc = false;
     return cuda_status(cudaGetLastError());
   };
 
@@ -486,11 +510,11 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     const int* idx = idx_all + (size_t)s * k * b;
     double* delta = delta2[k & 1];
     if (pending && (!fuse || due(k - 1))) {
-      CA_TRY(update_alone());                                   // a5 of step k-1
+      CA_TRY(update_alone());                                   // a5 of step k-1 (clears after_rc)
       if (due(k - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));  // a6
     }
     // a2 + a3 (and a5 of step k-1 when fused)
-    GramUpdate gu{prev_idx, pending ? prev_sb : 0, prev_delta, pb.cU, pb.v2, pb.rscale};
+    GramUpdate gu{prev_idx, pending ? prev_sb : 0, prev_delta, pb.cU, pb.v2, pb.rscale, after_rc};
     prof_mark(ctx, PC_GRAM);
     if (pending) {
       const int e = launch_gram_tc(static_cast<const float*>(pb.A), pb.lda, pb.N, K, idx, sb, pb.v2,
@@ -500,14 +524,15 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
       pending = false;
     } else {
       CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart,
-                         pb.panel, pb.rscale));
+                         pb.panel, pb.rscale, after_rc));
     }
     prof_mark(ctx, PC_GRAM);
     ctx->prof.kernel_launches += 1;
     // a4 (reduce of the split-K partials, then the s unrolled solves)
     SolveArgs sa{idx, pb.N, b, sk, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, delta};
-    CA_TRY(launch_reduce_solve(ctx, g, part, ppart, R, Rs, pvec, Ginv, sa));
+    CA_TRY(launch_reduce_solve(ctx, g, part, ppart, R, Rs, pvec, Ginv, sa, f64solve));
     CA_TRY_CUDA(cudaGetLastError());
+    after_rc = uses_reduce_chain(g, sa, f64solve);
     pending = true;
     prev_idx = idx;
     prev_sb = sb;
@@ -515,7 +540,8 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
     if (chk && (k + 1) % o->check_every == 0 && k + 1 < n_outer) {
       // the deferred update of this step first: the residual needs v current
       CA_TRY(update_alone());
-      if (due(k)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
+      after_rc = false;  // (also after a recompute and the check's kernels)
+      if (due(k) || rebuild_at_check) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
       CA_TRY(residual(&ctx->info.res, (k + 1) * (long long)s));
       ++ctx->info.checks;
       if (check_says_stop(o, ctx->info)) {
@@ -524,11 +550,16 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
       }
     }
   }
+  bool fresh = false;  // v just rebuilt from its definition
   if (pending) {
     CA_TRY(update_alone());
-    if (due(n_outer - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
+    if (due(n_outer - 1)) {
+      CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
+      fresh = true;
+    }
   }
   if (chk) {
+    if (rebuild_at_check && !fresh) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));
     CA_TRY(residual(&ctx->info.res, H));
     ++ctx->info.checks;
   }
@@ -874,7 +905,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     CA_TRY_CUDA(cudaGetLastError());
     const int b = o->b, s = o->s;
     const long long n_outer = (o->H + s - 1) / s;
-    ctx->info = ca_info{o->H, 0, 0.0, 0.0, 0.0, 0.0};
+    ctx->info = ca_info{o->H, 0, 0.0, 0.0, 0.0, 0.0, -1.0};
     ctx->trace.clear();
     if (o->check_every > 0) {
       CA_TRY(residual(&ctx->info.res0, 0));
@@ -893,13 +924,14 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       prof_mark(ctx, PC_GRAM);
       SolveArgs sa{ik, n, b, sk, sb, (int)sbp, 1.0 / ln, 1.0, 1.0, 1.0, ad, yd, delta};
       prof_mark(ctx, PC_SOLVE);
-      if (fast_solve(b, sb)) {
+      const bool f64solve = o->solve == CA_SOLVE_F64;
+      if (fast_solve(b, sb, f64solve)) {
         k_scale_split<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(
             R, (int)sbp, sb, b, 1.0 / ln, Rs);
         launch_factor(ctx->stream, R, sa, Ginv, ctx->d_err);
         ctx->prof.kernel_launches += 2;
       }
-      launch_solve(ctx, R, Rs, pvec, Ginv, sa);
+      launch_solve(ctx, R, Rs, pvec, Ginv, sa, f64solve);
       prof_mark(ctx, PC_SOLVE);
       k_scatter_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb,
                                                                         delta, -1.0 / ln, wd,

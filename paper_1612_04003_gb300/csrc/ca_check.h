@@ -29,3 +29,20 @@ inline void check_values(int method, bool objective, double lam, long long N, lo
     }
   }
 }
+
+// Certified relative objective error of a check under the objective rule:
+// f(w*) >= f(w) - gap gives (f(w) - f(w*))/f(w*) <= gap / (f(w) - gap) when
+// f(w) > gap; -1 when no bound follows.
+inline double certified_bound(double fval, double gap) {
+  return fval > gap ? gap / (fval - gap) : -1.0;
+}
+
+// Whether a check ends the solve: the objective rule stops once
+// gap <= tol (f(w) - gap), the residual rule once ||r|| <= tol ||r_0||
+// (tol = 0: never).
+inline bool check_stops(int objective, double tol, double res0, double res, double gap,
+                        double fval) {
+  if (!(tol > 0.0)) return false;
+  if (objective) return gap <= tol * (fval - gap);
+  return res <= tol * res0;
+}

@@ -209,6 +209,24 @@ __device__ __forceinline__ float2 df_rcp(float2 d) {
   return make_float2(h, lo - (h - r));
 }
 
+// (hi, lo) += x * (dh + dl) for an FP32 x and a double-float (dh, dl): the
+// product x dh is split exactly into p + e (e by a fused multiply-add), p is
+// accumulated by TwoSum and the small terms e and x dl go to lo (the
+// compensated dot product of Ogita, Rump and Oishi, 2005).  The sum carries
+// ~2^-44 of sum |x (dh + dl)|, against 2^-24 when products are rounded.
+__device__ __forceinline__ void df_dot_acc(float x, float dh, float dl, float& hi, float& lo) {
+  const float p = x * dh;
+  const float e = fmaf(x, dl, fmaf(x, dh, -p));
+  float s, t;
+  two_sum(hi, p, s, t);
+  hi = s;
+  lo += t + e;
+}
+
+__device__ __forceinline__ float2 df_shfl_xor(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
 // (shi, slo) += a * b, with a and b double-float values
 __device__ __forceinline__ void df_fma_acc(float2 a, float2 b, float& shi, float& slo) {
   const float p = a.x * b.x;

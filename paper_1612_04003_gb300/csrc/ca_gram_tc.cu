@@ -29,11 +29,14 @@
 // ring never waits on the tensor cores.
 // With a fused update (s*b <= 128) each stage also brings in the previous
 // outer step's rows: the loader warps apply that step's deferred update
-// (v -= cU Yprev^T Delta, in double-float on the FP32-pair copy of v) to the
-// stage's 32 columns, write it back, and project the current rows on the
-// updated values: the update pass and the next Gram pass share one launch
-// and one sweep over the K range.
+// (v -= cU Yprev^T Delta: FP32 products of the FP32 rows with the (hi, lo)
+// FP32 split of Delta, summed in FP32, the result applied in double-float to
+// the FP32-pair copy of v) to the stage's 32 columns, write it back, and
+// project the current rows on the updated values: the update pass and the
+// next Gram pass share one launch and one sweep over the K range.
 // Every wait is bounded (CA_WAIT_LIMIT_NS) and raises CA_DEV_ERR_TIMEOUT.
+#include <atomic>
+
 #include "ca_kernels.cuh"
 
 namespace {
@@ -214,6 +217,9 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x, P = gridDim.x;
+  // the prologue below reads A, the sampled indices, v2 and the row scales:
+  // before the preceding grid has finished only when it writes none of them
+  if (!u.early) pdl_wait();
   const long long a_begin = natoms * c / P, a_end = natoms * (c + 1) / P;
   const int T = (int)(a_end - a_begin);
 
@@ -343,9 +349,9 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       if (t < T) issue(t, t);
       cp_async_commit();
     }
-    // Everything above reads only X, the sampled indices and v2, which the
-    // preceding grid (the previous outer step's solve) does not write; Delta
-    // and the partial buffers wait for it.
+    // Everything above reads only X, the sampled indices, v2 and the row
+    // scales; with u.early the preceding grid (the previous outer step's
+    // solve) writes none of them.  Delta and the partial buffers wait for it.
     pdl_wait();
     pdl_trigger();
     if constexpr (UPD) {
@@ -368,10 +374,14 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       }
       if constexpr (UPD) {
         // deferred update of the previous outer step on this stage's 32
-        // columns, v_new = v_old - cU * sum_r Yprev[r][k] Delta_r, in
-        // double-float: per-thread sums over its rows, a shuffle over the 4
-        // row groups of the warp, one shared-memory exchange between warps
-        // (every warp then forms v_new for all 32 columns itself)
+        // columns, v_new = v_old - cU * sum_r Yprev[r][k] Delta_r: FP32
+        // products and sums (per-thread sums over its rows, a shuffle over
+        // the 4 row groups of the warp, one shared-memory exchange between
+        // warps; every warp then forms v_new for all 32 columns itself), the
+        // subtraction in double-float.  Exact products summed in double-float
+        // cost ~35% more time in this pass; the stopping test instead
+        // rebuilds v from its definition with exact products before each
+        // check (the FP32 roundings then never reach a certificate).
         float up[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
@@ -658,12 +668,19 @@ int launch_one(const float* A, long long lda, long long N, long long K, const in
                const float2* v2, int P, float* part, double* ppart, unsigned* err,
                const GramUpdate& u, cudaStream_t stream) {
   using C = TcCfg<SBP, THREE, UPD, BF, F16>;
-  // once per instantiation (a function-local static is initialised once even
-  // when several threads launch concurrently)
-  static const cudaError_t configured = cudaFuncSetAttribute(
-      k_gram_tc<SBP, THREE, UPD, PANEL, BF, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      C::kSmem);
-  if (configured != cudaSuccess) return (int)configured;
+  // the shared-memory limit is a per-device setting: raised once per device
+  // and instantiation (a bit per device; setting it twice is harmless)
+  static std::atomic<unsigned long long> configured{0ull};
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return (int)ce;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (!bit || !(configured.load(std::memory_order_acquire) & bit)) {
+    ce = cudaFuncSetAttribute(k_gram_tc<SBP, THREE, UPD, PANEL, BF, F16>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (ce != cudaSuccess) return (int)ce;
+    configured.fetch_or(bit, std::memory_order_release);
+  }
   const long long natoms = (K + 31) / 32;
   // launched as a programmatic dependent: its CTAs may start (and prefetch)
   // while the preceding grid in the stream finishes
@@ -692,7 +709,10 @@ int launch_gram_tc(const float* A, long long lda, long long N, long long K, cons
                    int three_pass, cudaStream_t stream, const GramUpdate* upd, bool panel) {
   // three_pass: 0 = TF32, 1 = 3xTF32, 2 = BF16x3, 3 = scaled FP16 (needs upd->rscale)
   GramUpdate none{};
-  if (upd) none.rscale = upd->rscale;
+  if (upd) {
+    none.rscale = upd->rscale;
+    none.early = upd->early;
+  }
   if (three_pass == 3 && !none.rscale) return (int)cudaErrorInvalidValue;
 #define CA_TC_CASE(S, U, PN, UU)                                                              \
   if (sbp == S) {                                                                            \

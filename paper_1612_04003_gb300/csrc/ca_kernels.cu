@@ -902,7 +902,10 @@ k_solve(const double* __restrict__ R, const double* __restrict__ pvec, SolveArgs
 // a5: deferred update  v[k] -= cU * sum_r Y[r][k] Delta_r  (primal: rho -= Y^T
 // Delta, i.e. z += Y^T Delta; dual: w -= Y Delta alpha/(lambda n)).
 // FP64 X: FP64 FMAs.  FP32 X: Delta split into two FP32 halves, FP32 products
-// and sums over the rows, one FP64 subtraction per element.
+// and sums over the rows (compensated across the row groups), the update
+// applied in double-float to the FP32-pair copy of v.  (The stopping test
+// rebuilds v with exact products before each check, so these FP32 roundings
+// never reach its gap or f(w).)
 // ---------------------------------------------------------------------------
 // CTA = 4 row groups x 64 threads; thread t of group g handles the 4
 // consecutive k at (64 blockIdx + t) * 4 and the rows r = g (mod 4); group 0
@@ -1013,8 +1016,9 @@ template __global__ void k_update_dense<float, true>(const float*, long long, lo
 // (primal: rho = y - X^T w, or z = X^T w; dual: w = -X alpha/(lambda n)).
 // Grid (K-blocks, row splits); row splits add into v with FP64 atomics after
 // split 0 wrote the c0 * y0 term.  FP32 A: x split in two FP32 halves,
-// FP32 sums over 32 rows, then FP64.  PANEL (FP32 only): A stored as
-// 32-column panels [K/32][N][32] (zero-padded).
+// exact products summed in double-float over the split's rows, then FP64.
+// PANEL (FP32 only): A stored as 32-column panels [K/32][N][32]
+// (zero-padded).
 // ---------------------------------------------------------------------------
 template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
@@ -1036,32 +1040,25 @@ k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long
         if (e < nk) acc[e] = fma((double)row[e], xr, acc[e]);
     }
   } else {
-    // x split in FP32 halves (x2); FP32 partial sums over 32 rows folded into
-    // compensated FP32 pairs
+    // x split in FP32 halves (x2); exact products, double-float sums
     const bool vec = PANEL || ((nk == 4) && ((lda & 3) == 0) &&
                                ((reinterpret_cast<uintptr_t>(A) & 15) == 0));
     const long long pbase = (k >> 5) * N * 32 + (k & 31);
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    for (long long rb = r0; rb < r1; rb += 32) {
-      float part[4] = {0.f, 0.f, 0.f, 0.f};
-      const long long re = min(r1, rb + 32);
 #pragma unroll 8
-      for (long long r = rb; r < re; ++r) {
-        const float2 xs = __ldg(x2 + r);
-        const float* row = reinterpret_cast<const float*>(A) + (PANEL ? pbase + r * 32 : r * lda + k);
-        float q[4];
-        if (vec) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(row));
-          q[0] = t.x; q[1] = t.y; q[2] = t.z; q[3] = t.w;
-        } else {
+    for (long long r = r0; r < r1; ++r) {
+      const float2 xs = __ldg(x2 + r);
+      const float* row = reinterpret_cast<const float*>(A) + (PANEL ? pbase + r * 32 : r * lda + k);
+      float q[4];
+      if (vec) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(row));
+        q[0] = t.x; q[1] = t.y; q[2] = t.z; q[3] = t.w;
+      } else {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) q[e] = (e < nk) ? row[e] : 0.f;
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) part[e] = fmaf(q[e], xs.x, fmaf(q[e], xs.y, part[e]));
+        for (int e = 0; e < 4; ++e) q[e] = (e < nk) ? row[e] : 0.f;
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) comp_add(hi[e], lo[e], part[e]);
+      for (int e = 0; e < 4; ++e) df_dot_acc(q[e], xs.x, xs.y, hi[e], lo[e]);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[e] = (double)hi[e] + (double)lo[e];
@@ -1288,8 +1285,8 @@ int launch_reduce_chain(int grid, size_t smem, cudaStream_t st, const float* par
 // q[r] += sum_k A[r][k] v[k] over the 32-column chunks [a0, a1) of this CTA's
 // split (blockIdx.y); 8 warps x 8 rows per CTA, lane c takes column 32 a + c
 // (a coalesced 128-byte row segment per load, panels or row-major).  FP32 A:
-// products with the (hi, lo) FP32 split of v, FP32 sums folded every 8 chunks
-// into a compensated pair (v2 zero-padded to a multiple of 32); FP64 A: FP64.
+// exact products with the (hi, lo) FP32 split of v (FMA error terms) summed
+// in double-float (v2 zero-padded to a multiple of 32); FP64 A: FP64.
 // v and v2 change between calls (the solves update them): read through L2
 // (ld.global.cg), never the non-coherent read-only path; A is constant.
 // q starts at zero (k_residual_norm clears it after use).
@@ -1319,9 +1316,9 @@ k_rowdot_dense(const T* __restrict__ A, long long lda, long long N, long long K,
       if (lane == 0 && r0 + j < N) atomicAdd(q + r0 + j, t);
     }
   } else {
-    float pacc[8], hi[8], lo[8];
+    float hi[8], lo[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) pacc[j] = hi[j] = lo[j] = 0.f;
+    for (int j = 0; j < 8; ++j) hi[j] = lo[j] = 0.f;
     for (long long a = a0; a < a1; ++a) {
       const float2 vk = __ldcg(v2 + a * 32 + lane);
       const long long k = a * 32 + lane;
@@ -1333,19 +1330,11 @@ k_rowdot_dense(const T* __restrict__ A, long long lda, long long N, long long K,
           if constexpr (PANEL) x = __ldg(reinterpret_cast<const float*>(A) + (a * N + r) * 32 + lane);
           else if (k < K) x = __ldg(reinterpret_cast<const float*>(A) + r * lda + k);
         }
-        pacc[j] = fmaf(x, vk.x, fmaf(x, vk.y, pacc[j]));
-      }
-      if (((a - a0) & 7) == 7) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          comp_add(hi[j], lo[j], pacc[j]);
-          pacc[j] = 0.f;
-        }
+        df_dot_acc(x, vk.x, vk.y, hi[j], lo[j]);
       }
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      comp_add(hi[j], lo[j], pacc[j]);
       float2 t = df_norm(hi[j], lo[j]);
       for (int o = 16; o; o >>= 1)
         t = df_add(t, make_float2(__shfl_xor_sync(0xffffffffu, t.x, o),

@@ -76,6 +76,11 @@ struct GramUpdate {
   double cU;            // v -= cU * Yprev^T Delta
   float2* v2;           // K entries as FP32 (hi, lo) pairs: read, updated in place
   const float* rscale;  // scaled FP16 Gram: power-of-two multiplier of each row of A
+  // true only when the preceding grid in the stream writes none of A, the
+  // sampled indices, v2 or rscale (the reduce + chain launch of the solves):
+  // the CTAs then read them and start their loads before waiting for that
+  // grid; otherwise they wait first
+  bool early;
 };
 
 // Stopping criterion: *out += ||cP A v - cI x - cY y||^2 over the N rows of

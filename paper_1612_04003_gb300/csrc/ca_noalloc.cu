@@ -109,10 +109,12 @@ extern "C" int ca_gram_project_noalloc(void* cuda_stream, int xfmt, int prec, co
   const long long natoms = (K + 31) / 32;
   int P, sbp;
   if (tc) {
-    sbp = 128;
+    // tile height: the smallest of 32, 64, 128 rows that holds sb
+    sbp = sb <= 32 ? 32 : (sb <= 64 ? 64 : 128);
     P = (int)std::min<long long>(kSplits, natoms);
     const long long Kp = natoms * 32;
     k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, stream>>>(v, K, Kp, v2);
+    // (k_split writes v2: the Gram launch waits for it before its first load)
     if (launch_gram_tc(static_cast<const float*>(A), ld, N, K, idx, sb, v2, P, sbp,
                        static_cast<float*>(part), ppart, err, prec == CA_GRAM_FP32_EXACT ? 1 : (prec == CA_GRAM_BF16X3 ? 2 : 0),
                        stream) != 0)

@@ -70,6 +70,7 @@ int run_request(ca_server* s, int w, long long id) {
   out.res = info.res;
   out.gap = info.gap;
   out.fval = info.fval;
+  out.bound = st == CA_OK ? info.bound : -1.0;
   return st;
 }
 

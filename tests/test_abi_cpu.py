@@ -33,7 +33,7 @@ def test_status_strings(lib):
 
 
 def test_null_arguments_rejected_without_gpu(lib):
-    o = ca.ca_opts(4, 4, 200, 1e-3, 42, ca.CA_GRAM_F64, 0, 0, 0.0, 0)
+    o = ca.ca_opts(4, 4, 200, 1e-3, 42, ca.CA_GRAM_F64, 0, 0, 0.0, 0, 0, 0)
     assert lib.ca_bcd_solve(None, 0, None, 64, 1024, 1024, None, ctypes.byref(o), None, None) == \
         ca.CA_ERR_ARG
     assert lib.ca_bdcd_solve(None, 0, None, 64, 1024, 64, None, ctypes.byref(o), None, None) == \

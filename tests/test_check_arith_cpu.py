@@ -62,7 +62,39 @@ def test_host_check_arithmetic_against_the_oracle(tmp_path, tiny, wide):
                          text=True, check=True).stdout.split("\n")
     assert len([o for o in out if o.strip()]) == len(want)
     for line, (res, gap, f, scale) in zip(out, want):
-        r_, g_, f_ = (float(v) for v in line.split())
+        r_, g_, f_, b_, stop = line.split()
+        r_, g_, f_, b_ = float(r_), float(g_), float(f_), float(b_)
         assert abs(r_ - res) <= 1e-14 * res + 1e-300
         assert abs(g_ - gap) <= 1e-9 * gap + 1e-14 * scale
         assert abs(f_ - f) <= 1e-12 * f + 1e-14 * scale
+        # the certified bound gap / (f - gap) and the objective rule's stop
+        if f_ > g_:
+            assert abs(b_ - g_ / (f_ - g_)) <= 1e-15 * b_ + 1e-300
+        else:  # far from the optimum the gap can exceed f: no bound
+            assert b_ == -1.0
+        assert stop == ("1" if g_ <= 1e-6 * (f_ - g_) else "0")
+
+
+def test_certified_bound_edge_cases(tmp_path):
+    """No bound when f(w) <= gap (-1); the residual rule and tol = 0 never
+    stop on the objective; the stop at the boundary gap = tol (f - gap)."""
+    import os
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "edge.cpp"
+    src.write_text('#include <cstdio>\n#include "ca_check.h"\nint main() {\n'
+                   '  std::printf("%g %g\\n", certified_bound(1.0, 1.0), certified_bound(0.5, 1.0));\n'
+                   '  std::printf("%d %d %d\\n", (int)check_stops(1, 0.0, 1, 1, 0.0, 1.0),\n'
+                   '              (int)check_stops(1, 0.5, 1, 1, 1.0, 3.0),\n'
+                   '              (int)check_stops(1, 0.5, 1, 1, 1.0 + 1e-12, 3.0));\n'
+                   '  std::printf("%d %d\\n", (int)check_stops(0, 0.5, 2.0, 1.0, 9.0, 1.0),\n'
+                   '              (int)check_stops(0, 0.5, 2.0, 1.1, 0.0, 1.0));\n'
+                   '  return 0;\n}\n')
+    exe = tmp_path / "edge"
+    subprocess.run(["g++", "-std=c++17", "-I", os.path.join(root, "paper_1612_04003_gb300", "csrc"),
+                    str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out == ["-1", "-1", "0", "1", "0", "1", "0"]

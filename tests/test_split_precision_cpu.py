@@ -109,52 +109,158 @@ def test_3xtf32_product_bound():
     assert np.all(np.abs(prod - exact) <= (2.0 ** -22 + 2 * 2.0 ** -21) * 1.01 * np.abs(exact))
 
 
-def test_fp32_residual_pass_precision_at_a_certified_stop():
-    """The tolerance of the GPU gap at a certified stop (FP32 X): the
-    residual pass multiplies FP32 X by the FP32 (hi, lo) pair of the FP64
-    vector with FP32 fused multiply-adds, 8 atoms per lane into an FP32
-    partial, partials summed compensated.  Its error is a fixed fraction of
-    sum |x_k v_k|, so relative to r it grows as r shrinks.  Emulated on a
-    dense 512 x 1024 problem (cond 1e3 rows) along a BCD run: the gap's
-    relative error stays below 1e-3 while the certified bound is above 1e-8,
-    and everywhere within 1e-2 of the gap plus 1e-10 of f (the cross term
-    2 r.dr grows relative to r as r shrinks; at convergence the gap it gives
-    levels off near 1.2e-13 f): certificates on FP32 X are sound down to
-    ~1e-10."""
+# --- double-float arithmetic of the FP32-X vector passes, emulated exactly ---
+# numpy float32 operations round once each, as the GPU's FP32 pipe does;
+# a fused multiply-add a*b + c is emulated in FP64, where a*b (48 bits) and
+# the sums formed below are exact, then rounded once to FP32.
+_F = np.float32
+
+
+def _fmaf(a, b, c):
+    return (np.asarray(a, np.float64) * np.asarray(b, np.float64)
+            + np.asarray(c, np.float64)).astype(_F)
+
+
+def _two_sum(a, b):
+    s = (a + b).astype(_F)
+    bb = (s - a).astype(_F)
+    return s, ((a - (s - bb)).astype(_F) + (b - bb).astype(_F)).astype(_F)
+
+
+def _dot_acc(x, dh, dl, hi, lo):
+    """(hi, lo) += x (dh + dl): exact product split, TwoSum accumulation."""
+    p = (x * dh).astype(_F)
+    e = _fmaf(x, dl, _fmaf(x, dh, -p))
+    hi, t = _two_sum(hi, p)
+    return hi, (lo + (t + e).astype(_F)).astype(_F)
+
+
+def _df_norm(hi, lo):
+    h = (hi + lo).astype(_F)
+    return h, (lo - (h - hi).astype(_F)).astype(_F)
+
+
+def _df_add(a, b):
+    s, e = _two_sum(a[0], b[0])
+    e = (e + (a[1] + b[1]).astype(_F)).astype(_F)
+    h = (s + e).astype(_F)
+    return h, (e - (h - s).astype(_F)).astype(_F)
+
+
+def _df_mul(a, b):
+    p = (a[0] * b[0]).astype(_F)
+    e = (_fmaf(a[0], b[0], -p) + _fmaf(a[0], b[1], (a[1] * b[0]).astype(_F))).astype(_F)
+    h = (p + e).astype(_F)
+    return h, (e - (h - p).astype(_F)).astype(_F)
+
+
+def _split(x):
+    h = np.asarray(x, np.float64).astype(_F)
+    return h, (np.asarray(x, np.float64) - h).astype(_F)
+
+
+def _device_like_fp32_update(v, Y, delta):
+    """One deferred update rho -= Y^T Delta as the Gram pass applies it: FP32
+    products of the rows with the (hi, lo) split of Delta, FP32 sums, the
+    result subtracted in double-float from the FP32-pair state."""
+    acc = np.zeros(Y.shape[1], _F)
+    dh, dl = _split(delta)
+    for r in range(Y.shape[0]):
+        acc = _fmaf(Y[r], dh[r], _fmaf(Y[r], dl[r], acc))
+    return _df_add(v, (-acc, np.zeros_like(acc)))
+
+
+def _device_like_rebuild(X32, y, w):
+    """rho = y - X^T w as the recomputation forms it before a check: exact
+    products of the FP32 rows with the (hi, lo) split of w summed in
+    double-float over the rows, then y - (hi + lo) in FP64."""
+    hi, lo = np.zeros(X32.shape[1], _F), np.zeros(X32.shape[1], _F)
+    wh, wl = _split(w)
+    for r in range(X32.shape[0]):
+        hi, lo = _dot_acc(X32[r], wh[r], wl[r], hi, lo)
+    return y - (hi.astype(np.float64) + lo.astype(np.float64))
+
+
+def _device_like_rowdot(X32, v):
+    """q = X v over the rows of FP32 X as the residual pass forms it: lane c
+    of a warp takes columns 32 a + c with exact products summed in
+    double-float, then a tree over the 32 lanes, then FP64."""
+    d, n = X32.shape
+    vh, vl = v
+    A = X32.reshape(d, n // 32, 32)
+    hi, lo = np.zeros((d, 32), _F), np.zeros((d, 32), _F)
+    for a in range(n // 32):
+        hi, lo = _dot_acc(A[:, a, :], vh.reshape(-1, 32)[a], vl.reshape(-1, 32)[a], hi, lo)
+    t = _df_norm(hi, lo)
+    o = 16
+    while o:
+        t = _df_add(t, (np.roll(t[0], -o, axis=1), np.roll(t[1], -o, axis=1)))
+        o >>= 1
+    return t[0][:, 0].astype(np.float64) + t[1][:, 0].astype(np.float64)
+
+
+def test_df_dot_is_exact_to_double_float():
+    """The compensated dot product carries ~2^-44 of sum |x y|, far below the
+    2^-24 of FP32-rounded products (here: a sum with heavy cancellation)."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((64, 4096)).astype(_F)
+    w = rng.standard_normal(64)
+    exact = w @ x.astype(np.float64)
+    hi, lo = np.zeros(4096, _F), np.zeros(4096, _F)
+    dh, dl = _split(w)
+    for r in range(64):
+        hi, lo = _dot_acc(x[r], dh[r], dl[r], hi, lo)
+    got = hi.astype(np.float64) + lo.astype(np.float64)
+    scale = np.abs(w) @ np.abs(x.astype(np.float64))
+    assert np.max(np.abs(got - exact) / scale) < 2.0 ** -40
+    naive = np.zeros(4096, _F)
+    for r in range(64):  # fmaf(x, dh, fmaf(x, dl, acc)): FP32-rounded products
+        naive = _fmaf(x[r], dh[r], _fmaf(x[r], dl[r], naive))
+    assert np.max(np.abs(naive - exact) / scale) > 2.0 ** -30
+
+
+def test_rebuilt_rho_and_residual_precision_at_a_certified_stop():
+    """The tolerances of f(w) and of the gap at a certified stop on FP32 X.
+    Between checks the Gram pass maintains rho = y - X^T w with FP32-rounded
+    products (each step's increment off by ~2^-24 of its terms, compounding:
+    emulated here, f(w) from that rho drifts to ~1e-8 f, as a GPU run showed,
+    3.7e-8).  A check therefore first rebuilds rho from its definition with
+    exact products summed in double-float, then forms
+    f(w) = lambda/2 ||w||^2 + ||rho||^2/(2n) and the gap from the residual
+    pass (1/n) X rho - lambda w (exact products, double-float sums).
+    Emulated along a CA-BCD run (b = 8, s = 8) on a dense 128 x 1024 problem
+    (cond 1e3 rows, lambda 1e-4) at the iterates of the FP64 oracle: f(w)
+    within 1e-12 f and the gap within 1e-6 gap + 1e-13 f of the exact values
+    at every check.  The GPU tests use 1e-10 f for f(w) and 1e-4 gap +
+    1e-12 f for the gap."""
     import oracle
     import synth
     m = synth.dense_primal(d=128, n=1024, cond=1e3, seed=2)
-    X32 = np.ascontiguousarray(m.X[:, :1024]).astype(np.float32)
+    X32 = np.ascontiguousarray(m.X[:, :1024]).astype(_F)
     X64, y, lam = X32.astype(np.float64), m.y[:1024], 1e-4
     d, n = X64.shape
-
-    def device_like_r(w):
-        rho = y - X64.T @ w
-        hi = rho.astype(np.float32)
-        lo = (rho - hi).astype(np.float32)
-        A = X32.reshape(d, n // 32, 32).astype(np.float64)
-        pacc = np.zeros((d, 32), dtype=np.float32)
-        tot = np.zeros((d, 32))
-        for a in range(n // 32):  # fmaf(x, hi, fmaf(x, lo, pacc)), one rounding each
-            t = (A[:, a, :] * lo.reshape(-1, 32)[a] + pacc).astype(np.float32)
-            pacc = (A[:, a, :] * hi.reshape(-1, 32)[a] + t).astype(np.float32)
-            if a % 8 == 7:
-                tot += pacc
-                pacc[:] = 0
-        tot += pacc
-        return tot.sum(axis=1) / n - lam * w
-
+    b, s = 8, 8
     w = np.zeros(d)
-    h, seen = 0, 0
-    while h < 2048:
-        w, _ = oracle.ca_bcd(X64, y, lam, 8, 8, 64, 7, h0=h, w0=w)
-        h += 64
+    drift = _split(y)  # the maintained rho, never rebuilt
+    h, worst_f, worst_drift, seen = 0, 0.0, 0.0, 0
+    while h < 1024:  # one outer step (s block updates) at a time
+        w_new, _ = oracle.ca_bcd(X64, y, lam, b, s, s, 7, h0=h, w0=w)
+        idx = np.unique(oracle.sample_blocks(7, h, s, b, d).ravel())
+        drift = _device_like_fp32_update(drift, X32[idx], (w_new - w)[idx])
+        w, h = w_new, h + s
+        f = oracle.primal_objective(X64, y, lam, w)
+        rho = _device_like_rebuild(X32, y, w)
+        f_dev = 0.5 * lam * (w @ w) + rho @ rho / (2 * n)
+        worst_f = max(worst_f, abs(f_dev - f) / f)
+        d64 = drift[0].astype(np.float64) + drift[1].astype(np.float64)
+        worst_drift = max(worst_drift, abs(0.5 * lam * (w @ w) + d64 @ d64 / (2 * n) - f) / f)
         r = oracle.primal_residual(X64, y, lam, w)
-        f, g = oracle.primal_objective(X64, y, lam, w), r @ r / (2 * lam)
-        rd = device_like_r(w)
-        gd = rd @ rd / (2 * lam)
-        if f > g and g / (f - g) > 1e-8:
-            assert abs(gd - g) <= 1e-3 * g
-            seen += 1
-        assert abs(gd - g) <= 1e-2 * g + 1e-10 * f
-    assert seen >= 3
+        g = r @ r / (2 * lam)
+        r_dev = _device_like_rowdot(X32, _split(rho)) / n - lam * w
+        g_dev = r_dev @ r_dev / (2 * lam)
+        assert abs(g_dev - g) <= 1e-6 * g + 1e-13 * f
+        seen += f > g and g / (f - g) < 1e-6
+    print(f"f rel err: rebuilt {worst_f:.3e}, maintained {worst_drift:.3e}")
+    assert worst_f <= 1e-12
+    assert worst_drift > 100 * worst_f  # why the check rebuilds rho
+    assert seen >= 1  # the run reaches certified bounds below 1e-6

@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 # ~1000 same-sign terms per split, 1000 * 2^-24 ~ 6e-5 worst case), relative to sqrt(G_ii G_jj) and
 # ||y_i|| ||v||; the two entry points sum the split-K partials in a different
 # order, so FP32-accumulated modes differ at rounding level
-TOL = {"f64": (1e-13, 1e-13), "3xtf32": (2e-5, 1e-6), "tf32": (3e-3, 1e-6)}
+TOL = {"f64": (1e-13, 1e-13), "3xtf32": (2e-5, 1e-6), "bf16x3": (2e-5, 1e-6),
+       "tf32": (3e-3, 1e-6)}
 
 
 @pytest.fixture(scope="module")
@@ -32,7 +33,7 @@ def setup():
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "3xtf32", "tf32"])
+@pytest.mark.parametrize("prec", ["f64", "3xtf32", "bf16x3", "tf32"])
 def test_noalloc_matches_regular_entry_point(setup, prec):
     ca, ctx = setup
     rng = np.random.default_rng(23)
@@ -40,7 +41,8 @@ def test_noalloc_matches_regular_entry_point(setup, prec):
     A = torch.as_tensor((rng.standard_normal((N, K))).astype(np.float32)).cuda()
     v = torch.as_tensor(rng.standard_normal(K)).cuda()
     tolG, tolp = TOL[prec]
-    for call, sb in enumerate((100, 37)):  # two calls in a row, different sizes
+    # calls in a row, different sizes (tile heights 128, 64 and 32)
+    for call, sb in enumerate((100, 37, 20)):
         idx = torch.as_tensor(rng.integers(0, N, size=sb).astype(np.int32)).cuda()
         G0 = torch.zeros((sb, sb), dtype=torch.float64, device="cuda")
         p0 = torch.zeros(sb, dtype=torch.float64, device="cuda")
