@@ -68,10 +68,13 @@ struct TcCfg {
   static constexpr int kNSfit = (kBudget - kMS * kMmaSlotBytes) / kRawBytes;
   static constexpr int kNS = kNSfit < 16 ? kNSfit : 16;         // load-ring depth
   static constexpr int kMmaRing = kMS * kMmaSlotBytes;
-  // SBP <= 128 with the 3-product split keeps two accumulators: D = hi hi^T
-  // and T = hi lo^T (lo hi^T = T^T is added in the epilogue)
-  static constexpr bool kSym = (SBP <= 128) && THREE && !F16;
-  static constexpr int kTmemCols = (SBP == 256) ? 512 : (kSym ? 256 : 128);
+  // one FP32 accumulator per 128-row tile; the split modes add their three
+  // products (hi hi^T, hi lo^T, lo hi^T) into it (a second accumulator for
+  // hi lo^T, transposed through shared memory in the epilogue, measured
+  // 1.3 us slower per launch)
+  // (SBP 256: rows 128..255 against up to 256 columns at column 128; the
+  // allocation is a power of two)
+  static constexpr int kTmemCols = (SBP == 256) ? 512 : 128;
   // the M = 128 MMA reads 128 rows of its A tile; with SBP < 128 the rows past
   // the tile are whatever follows in shared memory (their accumulator rows
   // are never stored).  The MMA ring is followed by the load ring; the last
@@ -87,7 +90,6 @@ struct TcCfg {
   static constexpr int kSmem = kZeroBytes + 1024 + 512;
   static_assert(THREE || kNS >= 4, "plain TF32 refills one stage late: needs >= 4 slots");
   static_assert(kNS >= 2, "load ring too shallow");
-  static_assert(!kSym || kMmaRing + kNS * kRawBytes >= 128 * 129 * 4, "no room for the T tile");
   static_assert(kSmem <= 232448, "shared memory");
 };
 
@@ -552,30 +554,6 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
       if constexpr (F16) return v * s_rinv[row] * s_rinv[col];
       else return v;
     };
-    if constexpr (C::kSym) {
-      // G = D + T + T^T: T goes through the (now idle) stage buffers as a
-      // 128 x 129 FP32 array, read back transposed without bank conflicts
-      float* Ts = reinterpret_cast<float*>(smem);
-      for (int cc = 32 * cpar; cc < n1; cc += 64) {
-        uint32_t r[32];
-        tmem_ld32(tbase + 128u + (uint32_t)cc, r);
-#pragma unroll
-        for (int q = 0; q < 32; ++q) Ts[trow * 129 + cc + q] = __uint_as_float(r[q]);
-      }
-      asm volatile("bar.sync 1, %0;" ::"n"(kLoaderThreads) : "memory");
-      for (int cc = 32 * cpar; cc < n1; cc += 64) {
-        uint32_t r[32];
-        tmem_ld32(tbase + (uint32_t)cc, r);
-        if (cc <= trow && trow < SBP) {  // rows past a short tile hold garbage
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int col = cc + q;
-            Pc[(long long)col * SBP + trow] =
-                __uint_as_float(r[q]) + Ts[trow * 129 + col] + Ts[col * 129 + trow];
-          }
-        }
-      }
-    } else
     for (int cc = 32 * cpar; cc < n1; cc += 64) {  // rows 0..127, columns 0..n1-1
       uint32_t r[32];
       tmem_ld32(tbase + (uint32_t)cc, r);
@@ -628,10 +606,7 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         const uint32_t acc = (t > 0 || kk > 0) ? 1u : 0u;
         const uint64_t h0 = desc(hb + kk * 32);
         mma(tmem, h0, h0, id1, acc);
-        if constexpr (C::kSym) {
-          const uint64_t l0 = desc(lb + kk * 32);
-          mma(tmem + 128u, h0, l0, id1, acc);  // T = hi lo^T
-        } else if constexpr (THREE && !F16) {
+        if constexpr (THREE && !F16) {
           const uint64_t l0 = desc(lb + kk * 32);
           mma(tmem, h0, l0, id1, 1u);
           mma(tmem, l0, h0, id1, 1u);
