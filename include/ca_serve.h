@@ -77,6 +77,16 @@ int ca_server_create(ca_server** out, int device, int workers, size_t budget_byt
  * CA_ERR_UNSUPPORTED. */
 int ca_server_submit(ca_server* s, const ca_request* r, long long* id);
 
+/* Batching: from now on the scheduler may start the queue's head together
+ * with up to max_group - 1 requests queued right behind it that a batched
+ * solve accepts (ca_batch_solve: FP32 X, the head's tcgen05 Gram mode,
+ * b <= 16, s*b <= 128 or s = 0), as one ca_batch_solve on one worker, when
+ * the group's scratch (the sum of each member's ca_batch_scratch_bytes
+ * alone) fits the budget.  The group's requests share the Gram, reduction
+ * and chain launches of each round and end together.  max_group = 1: every
+ * request runs alone (the default).  Errors: CA_ERR_ARG. */
+int ca_server_set_batching(ca_server* s, int max_group);
+
 /* Block until request id has ended; its outcome in *out.  Errors:
  * CA_ERR_ARG (unknown id). */
 int ca_server_wait(ca_server* s, long long id, ca_result* out);
@@ -90,6 +100,48 @@ int ca_server_get_stats(ca_server* s, ca_server_stats* out);
 
 /* Drain, then free the contexts and streams.  NULL is a no-op. */
 void ca_server_destroy(ca_server* s);
+
+/* Batched solves: `count` dense problems of uneven sizes solved together on
+ * ctx (its stream, its scratch arena).  Each round runs one outer step of
+ * every unfinished problem in three shared launches: one Gram pass whose
+ * CTAs split the concatenation of all problems' 32-column atoms into
+ * stretches of equal HBM cost (steps a2+a3, with each problem's deferred
+ * update a5 fused in), one reduction of every problem's split-K partials
+ * with the inversion of its diagonal blocks, and one chain CTA per problem
+ * (the s unrolled solves of eq. "recur" / its dual analogue, step a4).
+ * Problems are independent: each computes what ca_bcd_solve / ca_bdcd_solve
+ * computes alone, up to the order of the FP32 Gram sums (the split-K
+ * partition of its atoms differs).
+ *   reqs[i]  method 0 (primal: x = w, aux = z or NULL) or 1 (dual: x =
+ *            alpha, aux = w, required); xfmt CA_DENSE_F32 (row-major, ld a
+ *            multiple of 4, repacked into panels in ctx's scratch) or
+ *            CA_DENSE_F32_PANELS; every array device memory.  opts: one
+ *            tcgen05 Gram mode for all problems; b <= 16; s*b <= 128, or
+ *            s = 0: the depth is chosen by measured cost (a warm-up round,
+ *            then one timed round each at s*b = 128, 64, 32 rows per outer
+ *            step, then the cheapest per block update; changing s between
+ *            outer steps keeps the s = 1 iterates in exact arithmetic);
+ *            recompute_every and the stopping test (check_every, tol, stop)
+ *            as for the solves (a check rebuilds the problem's maintained
+ *            vector, forms its residual and waits for the GPU; a problem
+ *            that meets its rule leaves the rounds); solve CA_SOLVE_DF
+ *            (else CA_ERR_UNSUPPORTED).
+ *   flags    CA_BATCH_GRAPH: rounds that differ only in pointers (a segment,
+ *            up to 64 rounds) are captured into one CUDA graph and launched
+ *            as one (needs a non-NULL stream on ctx; ignored while
+ *            profiling).
+ *   out      count results: status, s (the depth of the last step), h_done,
+ *            and the stopping test's res0, res, gap, fval and bound.
+ * Returns after the work finished.  Errors: CA_ERR_ARG, CA_ERR_UNSUPPORTED,
+ * CA_ERR_OOM, CA_ERR_CUDA, and the device errors of the solves (then no
+ * result is valid). */
+#define CA_BATCH_GRAPH 1
+int ca_batch_solve(ca_ctx* ctx, int count, const ca_request* reqs, int flags, ca_result* out);
+
+/* Device scratch (bytes) ca_batch_solve takes from ctx's arena for these
+ * requests (with the same checks of the requests).  Errors: as
+ * ca_batch_solve's argument checks. */
+int ca_batch_scratch_bytes(ca_ctx* ctx, int count, const ca_request* reqs, size_t* bytes);
 
 #ifdef __cplusplus
 }

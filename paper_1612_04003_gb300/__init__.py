@@ -40,6 +40,8 @@ CA_STOP_RESIDUAL = 0
 CA_STOP_OBJECTIVE = 1
 STOP = {"residual": CA_STOP_RESIDUAL, "objective": CA_STOP_OBJECTIVE}
 
+CA_BATCH_GRAPH = 1
+
 CA_SOLVE_DF = 0
 CA_SOLVE_F64 = 1
 SOLVE = {"df": CA_SOLVE_DF, "f64": CA_SOLVE_F64}
@@ -164,6 +166,14 @@ def load():
     lib.ca_pack_panels.restype = i32
     lib.ca_selftest_wait_timeout.argtypes = [vp, i64]
     lib.ca_selftest_wait_timeout.restype = i32
+    lib.ca_batch_solve.argtypes = [vp, i32, ctypes.POINTER(ca_request), i32,
+                                   ctypes.POINTER(ca_result)]
+    lib.ca_batch_solve.restype = i32
+    lib.ca_batch_scratch_bytes.argtypes = [vp, i32, ctypes.POINTER(ca_request),
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    lib.ca_batch_scratch_bytes.restype = i32
+    lib.ca_server_set_batching.argtypes = [vp, i32]
+    lib.ca_server_set_batching.restype = i32
     _lib = lib
     return lib
 
@@ -373,6 +383,46 @@ class Context:
             raise CaError(st, "ca_pack_panels", self.last_error())
         return out
 
+    def ca_batch_solve(self, problems, *, graph=True):
+        """ca_batch_solve: the problems solved together in shared launches.
+        problems: dicts with method ("primal" / "dual"), X (FP32 device
+        array: primal X d x ld, dual X^T n x ld), y, x (w or alpha: in x0,
+        out x_H), aux (primal z or None, dual w), optional panels=(rows,
+        cols) for pre-packed panels, n / d (columns used, default ld), and
+        the solve keywords b, s (0: by measured cost), H, lam, seed, prec,
+        recompute_every, h0, tol, check_every, stop.  Returns one result
+        dict per problem (the certified bound is None when not formed)."""
+        reqs = (ca_request * len(problems))()
+        keep = []
+        for i, p in enumerate(problems):
+            m = {"primal": 0, "dual": 1}[p["method"]]
+            o = self._opts(p["b"], p.get("s", 0), p["H"], p["lam"], p.get("seed", 42),
+                           p.get("prec", "bf16x3"), p.get("recompute_every", 0), p.get("h0", 0),
+                           p.get("tol", 0.0), p.get("check_every", 0), p.get("stop", "residual"))
+            X = p["X"]
+            if p.get("panels") is not None:
+                rows, cols = (int(v) for v in p["panels"])
+                xf, ldv = CA_DENSE_F32_PANELS, 0
+            else:
+                rows, ldv = X.shape
+                xf = _xfmt(X)
+                used = p.get("n") if m == 0 else p.get("d")
+                cols = ldv if used is None else int(used)
+            dd, nn = (rows, cols) if m == 0 else (cols, rows)
+            reqs[i] = ca_request(m, xf, _ptr(X), dd, nn, ldv, _ptr(p["y"]), _ptr(p["x"]),
+                                 _ptr(p.get("aux")), o)
+            keep.append(p)
+        outs = (ca_result * len(problems))()
+        st = self._lib.ca_batch_solve(self.handle, len(problems), reqs,
+                                      CA_BATCH_GRAPH if graph else 0, outs)
+        if st != CA_OK:
+            raise CaError(st, "ca_batch_solve", self.last_error())
+        res = [{f: getattr(outs[i], f) for f, _ in ca_result._fields_}
+               for i in range(len(problems))]
+        for r in res:
+            r["bound"] = r["bound"] if r["bound"] >= 0.0 else None
+        return res
+
     def ca_selftest_wait_timeout(self, limit_ns: int) -> int:
         return int(self._lib.ca_selftest_wait_timeout(self.handle, int(limit_ns)))
 
@@ -403,7 +453,8 @@ class Server:
     submit() returns at once with an id; wait(id) blocks until that request
     ended.  The arrays of a request stay referenced here until it ended."""
 
-    def __init__(self, device: int = 0, workers: int = 4, budget_bytes: int = 8 << 30):
+    def __init__(self, device: int = 0, workers: int = 4, budget_bytes: int = 8 << 30,
+                 batch: int = 1):
         self._lib = load()
         h = ctypes.c_void_p()
         st = self._lib.ca_server_create(ctypes.byref(h), device, int(workers), int(budget_bytes))
@@ -411,6 +462,10 @@ class Server:
             raise CaError(st, "ca_server_create")
         self.handle = h
         self._keep = {}
+        if batch > 1:  # groups of up to `batch` requests share launches
+            st = self._lib.ca_server_set_batching(self.handle, int(batch))
+            if st != CA_OK:
+                raise CaError(st, "ca_server_set_batching")
 
     def submit(self, method, X, y, x, aux=None, *, b, s=1, H, lam, seed=42, prec="tf32",
                recompute_every=0, tol=0.0, check_every=0, stop="residual", solve="df", d=None,

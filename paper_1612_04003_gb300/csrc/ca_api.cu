@@ -9,60 +9,10 @@
 
 #include "ca_bcd.h"
 #include "ca_check.h"
+#include "ca_internal.h"
 #include "ca_kernels.cuh"
 
-namespace {
-
-constexpr int kMaxB = 128;          // b x b block held in shared memory by the solve
-constexpr int kMaxSB = 1024;        // s*b right-hand sides held in shared memory
-constexpr int kSolveSmemMax = 220 * 1024;
-
-// Kernel classes timed by the profiling hooks.
-enum { PC_GRAM = 0, PC_SOLVE = 1, PC_UPDATE = 2, PC_OTHER = 3, PC_CHAIN = 4, PC_N = 5 };
-
-struct Profile {
-  bool on = false;
-  std::vector<cudaEvent_t> pool;  // events, created once and reused
-  std::vector<int> cls;           // class of pool[i] for the marks of this call: start / stop pairs
-  double ms[PC_N] = {0, 0, 0, 0, 0};
-  long long launches[PC_N] = {0, 0, 0, 0, 0};
-  long long kernel_launches = 0;
-};
-
-}  // namespace
-
-struct ca_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  size_t scratch_max = 0;
-  int num_sms = 0;
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  unsigned* d_err = nullptr;     // device error word
-  unsigned* d_ticket = nullptr;  // count of the reducing CTAs of the reduce/solve kernel
-                                 // (d_err + 32; both cleared where a call starts)
-  unsigned* h_err = nullptr;     // pinned copy (128 bytes: error word; check sums at +32)
-  Profile prof;
-  ca_info info{};                // outcome of the last solve
-  std::vector<ca_check> trace;   // its checks of the stopping test
-  char last_error[256] = {0};    // text of the last failing CUDA call
-};
-
-namespace {
-
-struct Carve {
-  char* base;
-  size_t off = 0;
-  template <typename T>
-  T* take(size_t count) {
-    off = (off + 255) & ~size_t(255);
-    T* p = reinterpret_cast<T*>(base + off);
-    off += count * sizeof(T);
-    return p;
-  }
-};
-
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+namespace caint {
 
 thread_local ca_ctx* t_cur_ctx = nullptr;  // context of the running entry point
 
@@ -73,20 +23,9 @@ int cuda_fail(cudaError_t e, int line) {
   return CA_ERR_CUDA;
 }
 
-#define cuda_status(expr) cuda_status_at((expr), __LINE__)
 int cuda_status_at(cudaError_t e, int line) { return e == cudaSuccess ? CA_OK : cuda_fail(e, line); }
 
-#define CA_TRY_CUDA(call)                              \
-  do {                                                 \
-    cudaError_t e_ = (call);                           \
-    if (e_ != cudaSuccess) return cuda_fail(e_, __LINE__); \
-  } while (0)
 
-#define CA_TRY(call)        \
-  do {                      \
-    int s_ = (call);        \
-    if (s_ != CA_OK) return s_; \
-  } while (0)
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -181,28 +120,6 @@ int check_opts(const ca_opts* o, long long N) {
   return CA_OK;
 }
 
-// The dense outer-step loop shared by both methods.
-struct DenseProblem {
-  int xfmt;                 // CA_DENSE_F64 / CA_DENSE_F32
-  const void* A;            // N x K row-major, leading dim lda (device), or panels
-  bool panel = false;       // FP32 A stored as 32-column panels [K/32][N][32]
-  long long N, K, lda;
-  double* v;                // K: projection vector (rho or w), device
-  float2* v2;               // its (hi, lo) FP32 split, zero-padded to a multiple of 32
-  const float* rscale = nullptr;  // scaled FP16 Gram: per-row multipliers of A (N)
-  double* x;                // N: variable updated by the solves (w or alpha), device
-  float2* x2;               // N: scratch for the (hi, lo) FP32 split of x (recompute)
-  const double* yv;         // dual: y (device), primal: nullptr
-  double cG, cI, cP, cY, cU;
-  // recompute of v: v = c0 * y0 + c1 * sum_r A[r] x[r]
-  const double* y0;
-  double c0, c1;
-  int method = 0;           // 0: primal (A = X), 1: dual (A = X^T)
-  // stopping test: check_rows(o, N, K) doubles of scratch (zero between uses)
-  // and kCheckAcc accumulators
-  double* rq = nullptr;
-  double* racc = nullptr;
-};
 
 // Stopping test (Sec. 5.1.5).  A check forms ||r||_2 of the current
 // iterate, r = cP A v - cI x - cY y (one pass over A, then a wait for the
@@ -213,31 +130,6 @@ struct DenseProblem {
 // objective rule it also forms f(w) of the model from the maintained vectors:
 // primal lambda/2 ||w||^2 + ||rho||^2/(2n); dual ||y||^2/(2n) - D(alpha) +
 // gap with D(alpha) = lambda/2 ||w||^2 + ||alpha + y||^2/(2n).
-constexpr int kCheckAcc = 4;  // ||r||^2, then the sums of squares behind f(w)
-
-// Rows of the check's zero scratch: the residual's N row sums; the objective
-// rule also runs the sums of squares over the K entries of v through it.
-long long check_rows(const ca_opts* o, long long N, long long K) {
-  return o->stop == CA_STOP_OBJECTIVE ? std::max(N, K) : N;
-}
-
-struct CheckArgs {
-  int method;
-  bool objective;
-  double lam;
-  const void* A;  // dense A (nullptr with csr)
-  bool f64, panel;
-  long long lda, N, K;
-  const double* v;
-  const float2* v2;
-  const ca_csr_dev* csr;
-  double* rq;     // check_rows zeros
-  double* racc;   // kCheckAcc doubles
-  const double* x;
-  const double* yv;
-  double cP, cI, cY;
-};
-
 int full_check(ca_ctx* ctx, const CheckArgs& c, long long h_at, double* res, double* gap,
                double* fval) {
   const int nacc = c.objective ? kCheckAcc : 1;
@@ -491,16 +383,9 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   int prev_sb = 0;
   const double* prev_delta = nullptr;
   auto update_alone = [&]() -> int {
-    const size_t usm = align256((size_t)prev_sb * 4) + (size_t)prev_sb * 8;  // sidx | delta
-    const unsigned ug = (unsigned)((K + 255) / 256);
-    prof_mark(ctx, PC_UPDATE);
-    launch_update_dense(pb.xfmt == CA_DENSE_F64, ug, usm, ctx->stream, pb.A, pb.lda, pb.N, K,
-                        prev_idx, prev_sb, prev_delta, pb.cU, pb.v, pb.v2, ctx->d_err, pb.panel);
-    prof_mark(ctx, PC_UPDATE);
-    ctx->prof.kernel_launches += 1;
     pending = false;
     after_rc = false;
-    return cuda_status(cudaGetLastError());
+    return launch_update_alone(ctx, pb, prev_idx, prev_sb, prev_delta);
   };
 
   const long long n_outer = (H + s - 1) / s;
@@ -628,7 +513,26 @@ T* stage(ca_ctx* ctx, Carve& cv, const T* p, size_t count, bool in, bool* staged
   return d;
 }
 
-}  // namespace
+int launch_update_alone(ca_ctx* ctx, const DenseProblem& pb, const int* prev_idx, int prev_sb,
+                        const double* prev_delta) {
+  const size_t usm = align256((size_t)prev_sb * 4) + (size_t)prev_sb * 8;  // sidx | delta
+  const unsigned ug = (unsigned)((pb.K + 255) / 256);
+  prof_mark(ctx, PC_UPDATE);
+  launch_update_dense(pb.xfmt == CA_DENSE_F64, ug, usm, ctx->stream, pb.A, pb.lda, pb.N, pb.K,
+                      prev_idx, prev_sb, prev_delta, pb.cU, pb.v, pb.v2, ctx->d_err, pb.panel);
+  prof_mark(ctx, PC_UPDATE);
+  ctx->prof.kernel_launches += 1;
+  return cuda_status(cudaGetLastError());
+}
+
+void launch_row_scale_ctx(ca_ctx* ctx, const float* A, long long N, long long K, float* rscale) {
+  launch_row_scale(ctx->stream, A, 0, N, K, true, rscale);
+  ctx->prof.kernel_launches += 1;
+}
+
+}  // namespace caint
+
+using namespace caint;
 
 // ===========================================================================
 // C ABI

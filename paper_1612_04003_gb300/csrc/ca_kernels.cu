@@ -883,6 +883,31 @@ template __global__ void k_reduce_chain<float, 16, 3>(const float*, const double
                                                       double*, float2*, double*, float2*, int,
                                                       SolveArgs, unsigned*, unsigned*);
 
+// Shared launches over several problems (the batched solves): one grid
+// reduces every problem's split-K partials (role table: problem and CTA index
+// within it), one grid runs one chain CTA per problem.  No CTA waits on
+// another, so neither grid needs its CTAs resident at once.
+__global__ void __launch_bounds__(256)
+k_reduce_batch(const RedInst* __restrict__ insts, const RedRole* __restrict__ roles,
+               unsigned* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
+  const RedRole ro = roles[blockIdx.x];
+  const RedInst ri = insts[ro.inst];
+  reduce_body<float>(ri.part, ri.ppart, ri.P, ri.sbp, ri.R, ri.Rs, ri.pvec, ri.Ginv, ri.ndiag,
+                     ri.sa, err, ro.cta, ro.ncta);
+}
+
+template <int BMAX, int DEPTH>
+__global__ void __launch_bounds__(256)
+k_chain_batch(const RedInst* __restrict__ insts, unsigned* __restrict__ err) {
+  extern __shared__ double smem_d[];
+  pdl_wait();
+  pdl_trigger();
+  const RedInst ri = insts[blockIdx.x];
+  chain_la_body<BMAX, DEPTH>(ri.Rs, ri.pvec, ri.Ginv, ri.sa, err, smem_d);
+}
+
 template __global__ void k_chain<8, 4>(const float2*, const double*, const float2*, SolveArgs,
                                        unsigned*);
 template __global__ void k_chain<16, 3>(const float2*, const double*, const float2*, SolveArgs,
@@ -1547,15 +1572,31 @@ static cudaError_t set_dyn_smem(K kernel, int bytes) {
                               bytes < cap ? bytes : cap);
 }
 
+int launch_reduce_batch(int grid, cudaStream_t st, const RedInst* insts, const RedRole* roles,
+                        unsigned* err) {
+  return (int)launch_programmatic(k_reduce_batch, (unsigned)grid, 0, st, insts, roles, err);
+}
+
+int launch_chain_batch(int count, int bmax, size_t smem, cudaStream_t st, const RedInst* insts,
+                       unsigned* err) {
+  if (bmax <= 8)
+    return (int)launch_programmatic(k_chain_batch<8, 4>, (unsigned)count, smem, st, insts, err);
+  if (bmax <= 16)
+    return (int)launch_programmatic(k_chain_batch<16, 3>, (unsigned)count, smem, st, insts, err);
+  return (int)cudaErrorInvalidValue;
+}
+
 int set_solve_smem_limit(int bytes) {
-  cudaError_t e[8] = {set_dyn_smem(k_solve, bytes),
+  cudaError_t e[10] = {set_dyn_smem(k_solve, bytes),
                       set_dyn_smem(k_chain<8, 4>, bytes),
                       set_dyn_smem(k_chain<16, 3>, bytes),
                       set_dyn_smem(k_chain<32, 2>, bytes),
                       set_dyn_smem(k_reduce<float>, bytes),
                       set_dyn_smem(k_reduce_chain<float, 8, 4>, bytes),
                       set_dyn_smem(k_reduce_chain<float, 16, 3>, bytes),
-                      set_dyn_smem(k_reduce<double>, bytes)};
+                      set_dyn_smem(k_reduce<double>, bytes),
+                      set_dyn_smem(k_chain_batch<8, 4>, bytes),
+                      set_dyn_smem(k_chain_batch<16, 3>, bytes)};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return (int)x;
   return 0;

@@ -83,6 +83,55 @@ struct GramUpdate {
   bool early;
 };
 
+// A shared Gram launch over several problems (the batched solves): problem
+// descriptors, the units of work (atoms [a0, a1) of one problem into one of
+// its split-K partial slots) and each CTA's range of units.
+struct GramInst {
+  const float* A;       // the problem's A in 32-column panels
+  long long lda, N, K;
+  const int* idx;       // sampled rows of its current outer step
+  int sb;
+  const float2* v2;     // FP32 pairs of its projection vector (updated in place)
+  float* part;          // its partial slots: nslots x SBP x SBP
+  double* ppart;        // nslots x SBP
+  GramUpdate u;         // its pending deferred update (u.sb = 0: none; u.v2 = v2)
+};
+struct GramUnit {
+  int inst, slot;
+  long long a0, a1;
+};
+struct GramBatchArgs {
+  const GramInst* insts;
+  const GramUnit* units;
+  const int* unit_begin;  // units of CTA c: unit_begin[c] .. unit_begin[c+1]-1
+  bool early;             // as GramUpdate::early, for the whole launch
+};
+// Shared launch of P CTAs; sbp = 32, 64 or 128 (>= every problem's s*b).
+int launch_gram_tc_batch(const GramBatchArgs& bt, int P, int sbp, int three_pass, unsigned* err,
+                         cudaStream_t stream);
+
+// a4 of a shared launch: per problem its partial slots, reduction targets,
+// solve arguments and the number of reducing CTAs (>= ndiag + 1); role of a
+// CTA of the reduce grid: problem and index among that problem's CTAs.
+struct RedInst {
+  const float* part;
+  const double* ppart;
+  int P, sbp, ndiag;
+  double* R;
+  float2* Rs;
+  double* pvec;
+  float2* Ginv;
+  SolveArgs sa;
+};
+struct RedRole {
+  int inst, cta, ncta;
+};
+int launch_reduce_batch(int grid, cudaStream_t st, const RedInst* insts, const RedRole* roles,
+                        unsigned* err);
+// one chain CTA per problem (b <= bmax <= 16, s*b <= 256)
+int launch_chain_batch(int count, int bmax, size_t smem, cudaStream_t st, const RedInst* insts,
+                       unsigned* err);
+
 // Stopping criterion: *out += ||cP A v - cI x - cY y||^2 over the N rows of
 // A (dense: row-major FP64 / FP32 or FP32 panels, v2 the FP32 split of v for
 // FP32 A; csr: rows of the CSR matrix, FP64 v).  q: N doubles, zero on entry

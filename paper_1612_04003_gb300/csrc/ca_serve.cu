@@ -7,6 +7,10 @@
 // the sum of the workers' arenas within the budget.  Requests submitted with
 // opts.s = 0 get their unrolling depth from a measured-cost tuner shared by
 // requests of the same shape class.
+// Batching (ca_server_set_batching): the scheduler may start the queue's
+// head together with the requests queued right behind it that a batched
+// solve accepts (FP32 X, one tcgen05 Gram mode, b <= 16, s*b <= 128), as one
+// ca_batch_solve on one worker: their outer steps share launches.
 #include <cuda_runtime.h>
 
 #include <deque>
@@ -36,6 +40,31 @@ caserve::STuner::Key tuner_key(const ca_request& r) {
   const long long N = r.method == 0 ? r.d : r.n, K = r.method == 0 ? r.n : r.d;
   return {r.method, r.xfmt, r.opts.prec, r.opts.b, caserve::STuner::binade(N),
           caserve::STuner::binade(K)};
+}
+
+int run_batch(ca_server* s, int w, const std::vector<long long>& ids) {
+  std::vector<ca_request> rs;
+  {
+    std::lock_guard<std::mutex> lk(s->m);
+    for (long long id : ids) rs.push_back(s->reqs[(size_t)id]);
+  }
+  if (cudaSetDevice(s->device) != cudaSuccess) {
+    cudaGetLastError();
+    return CA_ERR_CUDA;
+  }
+  std::vector<ca_result> res(rs.size());
+  const int st = ca_batch_solve(s->ctxs[(size_t)w], (int)rs.size(), rs.data(), CA_BATCH_GRAPH,
+                                res.data());
+  std::lock_guard<std::mutex> lk(s->m);
+  for (size_t k = 0; k < ids.size(); ++k) {
+    ca_result& out = s->results[(size_t)ids[k]];
+    const size_t need = out.scratch_bytes;
+    out = res[k];
+    out.status = st;
+    out.worker = w;
+    out.scratch_bytes = need;
+  }
+  return st;
 }
 
 int run_request(ca_server* s, int w, long long id) {
@@ -126,7 +155,10 @@ int ca_server_create(ca_server** out, int device, int workers, size_t budget_byt
   }
   ca_server* raw = s.get();
   s->sched = std::make_unique<caserve::Scheduler>(
-      workers, budget_bytes, [raw](int w, long long id) { return run_request(raw, w, id); },
+      workers, budget_bytes,
+      [raw](int w, const std::vector<long long>& ids) {
+        return ids.size() == 1 ? run_request(raw, w, ids[0]) : run_batch(raw, w, ids);
+      },
       [raw](int w) { ca_bcd_release_scratch(raw->ctxs[(size_t)w]); });
   *out = s.release();
   return CA_OK;
@@ -148,6 +180,10 @@ int ca_server_submit(ca_server* s, const ca_request* r, long long* id) {
   if (e != CA_OK) return e;
   // the request's entries exist before the scheduler can start it (ids are
   // the submission order in both tables: submissions are serialised here)
+  // its share of a batched solve (alone: the shared pools of one problem,
+  // which bound its part of any group's pools)
+  size_t bneed = 0;
+  const bool bable = ca_batch_scratch_bytes(s->ctxs[0], 1, r, &bneed) == CA_OK;
   std::lock_guard<std::mutex> lk(s->m);
   s->reqs.push_back(*r);
   ca_result res{};
@@ -155,7 +191,14 @@ int ca_server_submit(ca_server* s, const ca_request* r, long long* id) {
   res.scratch_bytes = need;
   if (need > s->budget) res.status = CA_ERR_OOM;  // the scheduler rejects it at once
   s->results.push_back(res);
-  *id = s->sched->submit(need);
+  // batchable requests group by Gram mode (a batched solve runs one)
+  *id = s->sched->submit(need, bable ? (long long)r->opts.prec : -1LL, bneed);
+  return CA_OK;
+}
+
+int ca_server_set_batching(ca_server* s, int max_group) {
+  if (!s || max_group < 1) return CA_ERR_ARG;
+  s->sched->set_grouping(max_group);
   return CA_OK;
 }
 

@@ -14,9 +14,16 @@
 // request to finish.  A request needing more than the whole budget is
 // rejected at submission.  Strict FIFO: no request overtakes an earlier one.
 //
-// run(worker, id) executes request id on that worker and returns a status;
-// release(worker) frees an idle worker's arena.  Both are called without the
-// scheduler's lock held.
+// Grouping (optional, set_grouping): a request may be submitted with a group
+// key >= 0 and its need inside a group; the head may then take along the
+// longest run of requests queued right behind it with the head's key, up to
+// max_group, as long as the group's need (the sum of its members' group
+// needs) fits as above; the group starts on one worker and its requests end
+// together.  Requests still start in submission order.
+//
+// run(worker, ids) executes the requests ids (one, or a group) on that worker
+// and returns a status for all of them; release(worker) frees an idle
+// worker's arena.  Both are called without the scheduler's lock held.
 #pragma once
 
 #include <algorithm>
@@ -39,6 +46,8 @@ using Clock = std::chrono::steady_clock;
 
 struct JobState {
   size_t need = 0;
+  long long gkey = -1;  // group key (-1: never grouped)
+  size_t gneed = 0;     // need inside a group
   int status = 0;
   int worker = -1;
   long long admitted = -1;  // position in the admission order
@@ -56,8 +65,9 @@ struct Stats {
 
 class Scheduler {
  public:
-  using RunFn = std::function<int(int worker, long long id)>;
+  using RunFn = std::function<int(int worker, const std::vector<long long>& ids)>;
   using ReleaseFn = std::function<void(int worker)>;
+
   static constexpr int kRejected = -6;  // status of a request larger than the budget
 
   Scheduler(int workers, size_t budget, RunFn run, ReleaseFn release)
@@ -81,13 +91,22 @@ class Scheduler {
   Scheduler(const Scheduler&) = delete;
   Scheduler& operator=(const Scheduler&) = delete;
 
-  // Queue a request needing `need` bytes of scratch; returns its id.
-  long long submit(size_t need) {
+  // Groups of up to max_group requests (1: no grouping).
+  void set_grouping(int max_group) {
+    std::lock_guard<std::mutex> lk(m_);
+    max_group_ = std::max(1, max_group);
+  }
+
+  // Queue a request needing `need` bytes of scratch alone (and gneed inside a
+  // group of requests with the same gkey >= 0); returns its id.
+  long long submit(size_t need, long long gkey = -1, size_t gneed = 0) {
     std::lock_guard<std::mutex> lk(m_);
     const long long id = (long long)jobs_.size();
     jobs_.emplace_back();
     JobState& j = jobs_.back();
     j.need = need;
+    j.gkey = gkey;
+    j.gneed = gneed;
     j.t_submit = Clock::now();
     if (first_ == Clock::time_point()) first_ = j.t_submit;
     if (need > budget_) {
@@ -157,7 +176,7 @@ class Scheduler {
  private:
   struct Worker {
     size_t arena = 0;
-    long long job = -1;  // assigned request
+    std::vector<long long> jobs;  // assigned requests (empty: none)
     bool busy = false;   // running, or being released
     std::thread th;
     std::condition_variable cv;
@@ -169,29 +188,57 @@ class Scheduler {
       const unsigned long long seen = gen_;
       if (stop_ && queue_.empty()) return;
       if (!queue_.empty()) {
-        JobState& j = jobs_[(size_t)queue_.front()];
         size_t total = 0;
         for (const Worker& w : ws_) total += w.arena;
+        // the idle worker on which `need` leaves the smallest sum of arenas
+        auto fit = [&](size_t need, int* best, size_t* best_total) {
+          *best = -1;
+          for (int w = 0; w < (int)ws_.size(); ++w) {
+            if (ws_[w].busy) continue;
+            const size_t t = total - ws_[w].arena + std::max(ws_[w].arena, need);
+            if (t <= budget_ && (*best < 0 || t < *best_total)) {
+              *best = w;
+              *best_total = t;
+            }
+          }
+          return *best >= 0;
+        };
+        const long long head = queue_.front();
+        std::vector<long long> grp{head};
+        size_t gneed = jobs_[(size_t)head].need;
         int best = -1;
         size_t best_total = 0;
-        for (int w = 0; w < (int)ws_.size(); ++w) {
-          if (ws_[w].busy) continue;
-          const size_t t = total - ws_[w].arena + std::max(ws_[w].arena, j.need);
-          if (t <= budget_ && (best < 0 || t < best_total)) {
-            best = w;
-            best_total = t;
+        if (fit(gneed, &best, &best_total)) {
+          // grouping: requests right behind the head with its key
+          const long long key = jobs_[(size_t)head].gkey;
+          size_t gsum = jobs_[(size_t)head].gneed;
+          for (size_t k = 1; k < queue_.size() && (int)grp.size() < max_group_ && key >= 0 &&
+                             jobs_[(size_t)queue_[k]].gkey == key;
+               ++k) {
+            grp.push_back(queue_[k]);
+            gsum += jobs_[(size_t)queue_[k]].gneed;
+            const size_t n2 = std::max(gsum, jobs_[(size_t)head].need);
+            int b2 = -1;
+            size_t t2 = 0;
+            if (!fit(n2, &b2, &t2)) {
+              grp.pop_back();
+              break;
+            }
+            gneed = n2;
+            best = b2;
+            best_total = t2;
           }
-        }
-        if (best >= 0) {
-          const long long id = queue_.front();
-          queue_.pop_front();
+          for (size_t k = 0; k < grp.size(); ++k) queue_.pop_front();
           Worker& w = ws_[best];
-          w.arena = std::max(w.arena, j.need);  // the arena the request grows it to
+          w.arena = std::max(w.arena, gneed);  // the arena the group grows it to
           w.busy = true;
-          w.job = id;
-          j.worker = best;
-          j.admitted = admitted_++;
-          ++running_;
+          w.jobs = grp;
+          for (long long id : grp) {
+            JobState& j = jobs_[(size_t)id];
+            j.worker = best;
+            j.admitted = admitted_++;
+          }
+          running_ += (int)grp.size();
           peak_running_ = std::max(peak_running_, running_);
           peak_footprint_ = std::max(peak_footprint_, best_total);
           w.cv.notify_one();
@@ -218,20 +265,24 @@ class Scheduler {
   void worker_loop(int w) {
     std::unique_lock<std::mutex> lk(m_);
     for (;;) {
-      ws_[w].cv.wait(lk, [&] { return stop_ || ws_[w].job >= 0; });
-      if (ws_[w].job < 0) return;
-      const long long id = ws_[w].job;
-      jobs_[(size_t)id].t_start = Clock::now();
+      ws_[w].cv.wait(lk, [&] { return stop_ || !ws_[w].jobs.empty(); });
+      if (ws_[w].jobs.empty()) return;
+      const std::vector<long long> ids = ws_[w].jobs;
+      const Clock::time_point t0 = Clock::now();
+      for (long long id : ids) jobs_[(size_t)id].t_start = t0;
       lk.unlock();
-      const int st = run_(w, id);
+      const int st = run_(w, ids);
       lk.lock();
-      JobState& j = jobs_[(size_t)id];
-      j.status = st;
-      j.t_end = Clock::now();
-      j.done = true;
-      ws_[w].job = -1;
+      const Clock::time_point t1 = Clock::now();
+      for (long long id : ids) {
+        JobState& j = jobs_[(size_t)id];
+        j.status = st;
+        j.t_end = t1;
+        j.done = true;
+      }
+      ws_[w].jobs.clear();
       ws_[w].busy = false;
-      --running_;
+      running_ -= (int)ids.size();
       ++gen_;
       cv_disp_.notify_one();
       cv_done_.notify_all();
@@ -241,6 +292,7 @@ class Scheduler {
   const size_t budget_;
   RunFn run_;
   ReleaseFn release_;
+  int max_group_ = 1;
   std::mutex m_;
   std::condition_variable cv_disp_, cv_done_;
   std::deque<JobState> jobs_;  // element references stay valid as it grows

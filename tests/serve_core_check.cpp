@@ -30,21 +30,29 @@ struct Fake {
   bool over = false;
   std::atomic<int> releases{0};
   Fake(int workers, size_t b) : arena(workers, 0), budget(b) {}
-  int run(int w, long long id) {
+  size_t group_need(const std::vector<long long>& ids) const {
+    size_t t = 0;
+    for (long long id : ids) t += need[(size_t)id];
+    return t;
+  }
+  int run(int w, const std::vector<long long>& ids) {
     {
       std::lock_guard<std::mutex> lk(m);
-      arena[w] = std::max(arena[w], need[(size_t)id]);
+      arena[w] = std::max(arena[w], group_need(ids));
       size_t tot = 0;
       for (size_t a : arena) tot += a;
       if (tot > budget) over = true;
-      starts.push_back(id);
-      peak = std::max(peak, ++running);
+      for (long long id : ids) starts.push_back(id);
+      groups.push_back(ids);
+      running += (int)ids.size();
+      peak = std::max(peak, running);
     }
-    std::this_thread::sleep_for(std::chrono::microseconds(200 + (id * 7919) % 1800));
+    std::this_thread::sleep_for(std::chrono::microseconds(200 + (ids[0] * 7919) % 1800));
     std::lock_guard<std::mutex> lk(m);
-    --running;
+    running -= (int)ids.size();
     return 0;
   }
+  std::vector<std::vector<long long>> groups;
   void release(int w) {
     std::lock_guard<std::mutex> lk(m);
     arena[w] = 0;
@@ -52,7 +60,8 @@ struct Fake {
   }
 };
 
-static void scenario(int workers, size_t budget, int njobs, size_t lo, size_t hi, unsigned seed) {
+static void scenario(int workers, size_t budget, int njobs, size_t lo, size_t hi, unsigned seed,
+                     int max_group = 1) {
   Fake f(workers, budget);
   std::mt19937 rng(seed);
   std::uniform_int_distribution<size_t> dist(lo, hi);
@@ -60,9 +69,14 @@ static void scenario(int workers, size_t budget, int njobs, size_t lo, size_t hi
   std::vector<long long> ids, order;
   {
     caserve::Scheduler s(
-        workers, budget, [&](int w, long long id) { return f.run(w, id); },
+        workers, budget, [&](int w, const std::vector<long long>& g) { return f.run(w, g); },
         [&](int w) { f.release(w); });
-    for (int i = 0; i < njobs; ++i) ids.push_back(s.submit(f.need[(size_t)i]));
+    if (max_group > 1) s.set_grouping(max_group);
+    // groups of requests with the same parity of their need
+    for (int i = 0; i < njobs; ++i)
+      ids.push_back(max_group > 1 ? s.submit(f.need[(size_t)i], (long long)(f.need[(size_t)i] % 2),
+                                             f.need[(size_t)i])
+                                  : s.submit(f.need[(size_t)i]));
     for (int i = 0; i < njobs; ++i) {
       caserve::JobState j = s.wait(ids[(size_t)i]);
       CHECK(j.done);
@@ -80,12 +94,25 @@ static void scenario(int workers, size_t budget, int njobs, size_t lo, size_t hi
     CHECK(st.submitted == njobs && st.rejected == nrej && st.completed == njobs - nrej);
     CHECK(st.p50_ms > 0 && st.p50_ms <= st.p99_ms && st.p99_ms <= st.max_ms);
     CHECK(st.peak_footprint <= budget);
-    CHECK(st.peak_concurrency <= workers && st.peak_concurrency == f.peak);
+    CHECK(st.peak_concurrency <= workers * max_group && st.peak_concurrency == f.peak);
   }
   CHECK(!f.over);
   // admission follows the submission order (rejected requests never start)
   for (size_t k = 0; k < order.size(); ++k) CHECK(order[k] == (long long)k);
   CHECK(f.starts.size() == order.size());
+  // groups: consecutive submissions, all accepted by the grouping rule, at
+  // most max_group, never more than the budget
+  size_t grouped = 0;
+  for (const auto& g : f.groups) {
+    CHECK((int)g.size() <= max_group && !g.empty());
+    for (size_t k = 1; k < g.size(); ++k) {
+      CHECK(g[k] > g[k - 1]);
+      CHECK(f.need[(size_t)g[k]] % 2 == f.need[(size_t)g[0]] % 2);
+    }
+    CHECK(f.group_need(g) <= budget);
+    grouped += g.size() > 1;
+  }
+  if (max_group > 1) CHECK(grouped > 0);
   std::printf("scenario workers=%d budget=%zu jobs=%d: peak concurrency %d, releases %d\n", workers,
               budget, njobs, f.peak, f.releases.load());
 }
@@ -134,11 +161,14 @@ int main() {
   scenario(4, 100, 40, 30, 120, 2);  // large requests: releases, rejections
   scenario(1, 50, 20, 1, 50, 3);     // one worker: strictly one at a time
   scenario(8, 1000, 200, 1, 100, 4); // wide
+  scenario(2, 400, 120, 1, 60, 5, 8);  // grouping: up to 8 requests per start
+  scenario(3, 100, 80, 5, 40, 6, 4);   // grouping under a tight budget
   {  // a request that needs the whole budget after others grew their arenas
     Fake f(3, 90);
     f.need = {30, 30, 30, 90, 10};
     caserve::Scheduler s(
-        3, 90, [&](int w, long long id) { return f.run(w, id); }, [&](int w) { f.release(w); });
+        3, 90, [&](int w, const std::vector<long long>& g) { return f.run(w, g); },
+        [&](int w) { f.release(w); });
     std::vector<long long> ids;
     for (size_t v : f.need) ids.push_back(s.submit(v));
     for (size_t k = 0; k < ids.size(); ++k) CHECK(s.wait(ids[k]).admitted == (long long)k);

@@ -122,3 +122,47 @@ def test_request_larger_than_budget_is_refused(ca):
     assert srv.stats()["rejected"] == 1
     assert float(x.abs().max()) == 0.0  # never ran
     srv.close()
+
+
+def test_served_batches_share_launches(ca):
+    """Continuous batching: with ca_server_set_batching the scheduler starts
+    the queue's head with the batchable requests queued right behind it (one
+    Gram mode, FP32 X, b <= 16, s b <= 128) as one batched solve.  Each
+    batched result is held to the same request alone at the FP32-path
+    tolerance (the shared plan splits its Gram sums differently); requests
+    that do not batch (FP64 X, a second Gram mode) run alone and equal the
+    solve alone to 1e-12; more requests run at once than there are workers."""
+    reqs = []
+    for i, (d, n, b, s) in enumerate([(256, 4096, 8, 16), (512, 2048, 4, 16), (128, 8192, 16, 8),
+                                      (384, 4000, 8, 8), (200, 1024, 4, 32), (640, 3000, 8, 16),
+                                      (96, 2048, 16, 4), (300, 5000, 8, 16)]):
+        m = synth.dense_primal(d=d, n=n, cond=1e2, seed=30 + i)
+        reqs.append(dict(method="primal", X=_dev(np.ascontiguousarray(m.X[:, :n])),
+                         y=_dev(m.y[:n]), xs=d, auxs=n,
+                         kw=dict(b=b, s=s, H=256, lam=1e-3, seed=40 + i, prec="bf16x3")))
+    p = synth.dense_dual(d=1028, n=400, seed=6)
+    reqs.insert(3, dict(method="dual", X=_dev(np.ascontiguousarray(p.X.astype(np.float32).T)),
+                        y=_dev(p.y), xs=400, auxs=1028,
+                        kw=dict(b=8, s=16, H=256, lam=1e-2, seed=2, prec="bf16x3")))
+    t = synth.tiny_primal(d=64, n=1024, seed=1)
+    reqs.insert(5, dict(method="primal", X=_dev(t.X), y=_dev(t.y), xs=64, auxs=1024,
+                        kw=dict(b=4, s=4, H=200, lam=1e-3, seed=42, prec="f64")))
+    alone = [_run_alone(ca, r) for r in reqs]
+    workers = 2
+    srv = ca.Server(0, workers=workers, budget_bytes=8 << 30, batch=8)
+    outs, ids = [], []
+    for r in reqs:
+        x = torch.zeros(r["xs"], dtype=torch.float64, device="cuda")
+        aux = torch.zeros(r["auxs"], dtype=torch.float64, device="cuda")
+        ids.append(srv.submit(r["method"], r["X"], r["y"], x, aux, **r["kw"]))
+        outs.append((x, aux))
+    results = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    for k, (r, res, (x, aux), (xa, auxa, info)) in enumerate(zip(reqs, results, outs, alone)):
+        assert res["status"] == ca.CA_OK and res["h_done"] == info["h_done"], (k, res)
+        tol = 1e-12 if r["kw"]["prec"] == "f64" else 1e-5
+        assert _rel(x.cpu().numpy(), xa) < tol, k
+        assert _rel(aux.cpu().numpy(), auxa) < tol, k
+    assert st["completed"] == len(reqs)
+    assert st["peak_concurrency"] > workers  # some requests ran as a group
