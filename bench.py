@@ -317,6 +317,175 @@ def secondary_workloads(ctx, stream):
     return out
 
 
+def _uneven_problems(count, seed, d_range, n_range, H_sweeps=4, Hmax=2048, prec="bf16x3",
+                     s_rule="fixed"):
+    """Uneven dense ridge problems shaped like the served-batch workload:
+    d and n log-uniform, FP32 X N(0,1) generated on the device, lambda
+    log-uniform in [1e-6, 1e-1], half primal / half dual, b in {4, 8, 16},
+    H = min(Hmax, H_sweeps N / b) block updates (N the sampled dimension)."""
+    import math
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        d = int(math.exp(rng.uniform(math.log(d_range[0]), math.log(d_range[1])))) // 32 * 32
+        n = int(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))) // 32 * 32
+        lam = float(math.exp(rng.uniform(math.log(1e-6), math.log(1e-1))))
+        method = "primal" if i % 2 == 0 else "dual"
+        b = int(rng.choice([4, 8, 16]))
+        N = d if method == "primal" else n
+        s_ = 0 if s_rule == "tuned" else max(1, 64 // b)
+        H = int(max(b, min(Hmax, H_sweeps * N // b)))
+        g = torch.Generator(device="cuda").manual_seed(1000 + i)
+        if method == "primal":
+            X = torch.randn(d, n, device="cuda", generator=g)
+            y = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+            xs, auxs = d, n
+        else:
+            X = torch.randn(n, d, device="cuda", generator=g)
+            y = torch.sign(torch.randn(n, dtype=torch.float64, device="cuda", generator=g))
+            xs, auxs = n, d
+        out.append(dict(method=method, X=X, y=y, xs=xs, auxs=auxs, d=d, n=n,
+                        kw=dict(b=b, s=s_, H=H, lam=lam, seed=7 + i, prec=prec)))
+    return out
+
+
+def batch_study(ctx, stream, count=24):
+    """The batched solves (ca_batch_solve) on uneven problems shaped like the
+    served-batch workload, scaled to a short run (d 256-2048, n 4096-32768):
+    the same problems one after another (each its own solve), in shared
+    launches (plain and CUDA-graph-captured), and with the depth chosen by
+    measured cost.  Block updates per second of the whole set."""
+    import torch
+    probs = _uneven_problems(count, 5, (256, 2048), (4096, 32768))
+    total_h = sum(p["kw"]["H"] for p in probs)
+
+    def fresh(p):
+        return dict(method=p["method"], X=p["X"], y=p["y"],
+                    x=torch.zeros(p["xs"], dtype=torch.float64, device="cuda"),
+                    aux=torch.zeros(p["auxs"], dtype=torch.float64, device="cuda"), **p["kw"])
+
+    def seq():
+        for p in probs:
+            x = torch.zeros(p["xs"], dtype=torch.float64, device="cuda")
+            aux = torch.zeros(p["auxs"], dtype=torch.float64, device="cuda")
+            (ctx.ca_bcd_solve if p["method"] == "primal" else ctx.ca_bdcd_solve)(
+                p["X"], p["y"], x, aux, **p["kw"])
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    out = {"problems": count, "block_updates": total_h,
+           "workload": "uneven dense ridge problems, d 256-2048 and n 4096-32768 log-uniform, "
+                       "FP32 X N(0,1), lambda 1e-6..1e-1, half primal / half dual, b in {4,8,16}, "
+                       "s b = 64, H = min(2048, 4 N / b), BF16x3 Gram"}
+    t = timed(seq)
+    out["one_after_another"] = {"seconds": t, "block_updates_per_s": total_h / t}
+    for name, graph in (("shared_launches", False), ("shared_launches_graph", True)):
+        t = timed(lambda: ctx.ca_batch_solve([fresh(p) for p in probs], graph=graph))
+        out[name] = {"seconds": t, "block_updates_per_s": total_h / t}
+    tuned = [dict(fresh(p), s=0) for p in probs]
+    t = timed(lambda: ctx.ca_batch_solve([dict(q, x=torch.zeros_like(q["x"]),
+                                               aux=torch.zeros_like(q["aux"])) for q in tuned]))
+    res = ctx.ca_batch_solve(tuned)
+    out["shared_launches_graph_depth_by_cost"] = {
+        "seconds": t, "block_updates_per_s": total_h / t,
+        "rows_per_step_chosen": sorted({r["s"] * p["kw"]["b"] for r, p in zip(res, probs)})}
+    del probs
+    return out
+
+
+def serve_config5(args):
+    """The served-batch workload scaled to a bench-length run: a Poisson
+    stream (2000 arrivals/s) of dense ridge requests with the configuration's
+    distributions -- d log-uniform in [256, 8192], n log-uniform in [4096,
+    131072], FP32 X N(0,1), lambda log-uniform in [1e-6, 1e-1], half primal /
+    half dual, b in {4, 8, 16}, s by measured cost -- each stopping at a
+    certified relative objective error of 1e-6 (duality gap, a check every 4
+    outer steps) or after 32 sweeps of its sampled dimension (at most 32768
+    block updates; a dual request with n >> d and a small lambda is
+    conditioned like 1/lambda and certifies far later); batching on
+    (groups of up to 8 requests share launches), 4 workers, 64 GB budget.
+    Reports latency percentiles, throughput and how many results are
+    certified, beside the same requests run one after another."""
+    import numpy as np
+    import torch
+    import paper_1612_04003_gb300 as ca
+    M = args.serve5_requests
+    probs = _uneven_problems(M, 11, (256, 8192), (4096, 131072), H_sweeps=32, Hmax=1 << 15,
+                             s_rule="tuned")
+    for p in probs:
+        p["kw"].update(check_every=4, tol=1e-6, stop="objective")
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(12)
+    arrivals = np.cumsum(rng.exponential(1.0 / 2000.0, size=M))
+
+    def fresh(p):
+        return (torch.zeros(p["xs"], dtype=torch.float64, device="cuda"),
+                torch.zeros(p["auxs"], dtype=torch.float64, device="cuda"))
+
+    # one after another on one context (s = 16 for b <= 8, 8 for b = 16)
+    ctx = ca.Context(0)
+    t0 = time.perf_counter()
+    h_seq, cert_seq = 0, 0
+    for p in probs:
+        x, aux = fresh(p)
+        kw = dict(p["kw"], s=128 // p["kw"]["b"] if p["kw"]["b"] > 8 else 16)
+        (ctx.ca_bcd_solve if p["method"] == "primal" else ctx.ca_bdcd_solve)(
+            p["X"], p["y"], x, aux, **kw)
+        inf = ctx.solve_info()
+        h_seq += inf["h_done"]
+        cert_seq += inf["bound"] is not None and inf["bound"] <= 1e-6
+    seq_s = time.perf_counter() - t0
+    ctx.close()
+    srv = ca.Server(0, workers=4, budget_bytes=64 << 30, batch=8)
+    ids = []
+    t0 = time.perf_counter()
+    for p, at in zip(probs, arrivals):
+        delay = at - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        x, aux = fresh(p)
+        ids.append(srv.submit(p["method"], p["X"], p["y"], x, aux, **p["kw"]))
+    res = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    certified = [r for r in res if r["status"] == ca.CA_OK and r["bound"] is not None
+                 and r["bound"] <= 1e-6]
+    cert = len(certified)
+    lat_c = sorted(r["latency_ms"] for r in certified)
+    pct = (lambda q: lat_c[min(len(lat_c), max(1, int(np.ceil(q * len(lat_c))))) - 1]
+           if lat_c else None)
+    out = {"workload": "served-batch distributions (d 256-8192, n 4096-131072 log-uniform, "
+                       "half primal / half dual, b in {4,8,16}, lambda 1e-6..1e-1, FP32 X), "
+                       "%d requests (of the configuration's 4000) at 2000/s; stop at a certified "
+                       "1e-6 relative objective error or 32 sweeps (<= 32768 block updates); BF16x3 Gram" % M,
+           "requests": M, "ok": sum(1 for r in res if r["status"] == ca.CA_OK),
+           "certified_1e-6": cert,
+           "certified_p50_ms": pct(0.50), "certified_p99_ms": pct(0.99),
+           "certified_primal": sum(1 for r, p in zip(res, probs) if p["method"] == "primal"
+                                   and r["bound"] is not None and r["bound"] <= 1e-6),
+           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+           "mean_ms": st["mean_ms"], "max_ms": st["max_ms"], "wall_s": st["wall_s"],
+           "requests_per_s": st["completed"] / max(st["wall_s"], 1e-9),
+           "block_updates_per_s": st["block_updates_per_s"],
+           "peak_concurrency": st["peak_concurrency"],
+           "peak_footprint_gb": st["peak_footprint"] / 2**30,
+           "arrival_span_s": float(arrivals[-1]),
+           "sequential": {"wall_s": seq_s, "block_updates_per_s": h_seq / seq_s,
+                          "certified_1e-6": cert_seq,
+                          "how": "the same requests one after another on one context"}}
+    del probs
+    return out
+
+
 def gram_conditioning(ctx, X, lam, b, n_outer=64, s_list=(1, 2, 4, 8, 16)):
     """Condition numbers of the s*b x s*b Gram matrices Y Y^T / n + lambda I
     that the solve factors (the first n_outer outer steps of the seed-42
@@ -344,7 +513,7 @@ def gram_conditioning(ctx, X, lam, b, n_outer=64, s_list=(1, 2, 4, 8, 16)):
     return {"b": b, "outer_steps": n_outer, "cond_gram": out}
 
 
-def precision_study(args) -> int:
+def precision_study(args, emit=True):
     """--precision-study: the precision configuration of the benchmark family:
     X 8192 x 131072 FP32 with geometric row scaling (condition 1e2, 1e4, 1e6),
     lambda 1e-6, b = s = 16, H = 8192, recompute every 8 outer steps.  Each
@@ -391,11 +560,14 @@ def precision_study(args) -> int:
                      "rel_objective_diff": 0.0, "block_updates_per_s": H / (t64 * 1e-3)})
         gram_cond.append({"cond": cond, **gram_conditioning(ctx, X, lam, b)})
         del X, y
-    print(json.dumps({"study": "precision", "workload": "dense primal CA-BCD, X 8192 x 131072 FP32, "
-                      "lambda 1e-6, b=16, s=16, H=8192, recompute every 8 outer steps",
-                      "rows": rows, "gram_conditioning": gram_cond}), flush=True)
+    out = {"study": "precision", "workload": "dense primal CA-BCD, X 8192 x 131072 FP32, "
+           "lambda 1e-6, b=16, s=16, H=8192, recompute every 8 outer steps",
+           "rows": rows, "gram_conditioning": gram_cond}
     ctx.close()
-    return 0
+    if emit:
+        print(json.dumps(out), flush=True)
+        return 0
+    return out
 
 
 def _trajectory(tr, f_star, keep=48):
@@ -608,6 +780,10 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="samples (columns of X); smaller than the default only for profiler captures")
     ap.add_argument("--h", type=int, default=None, help="block updates per solve (default %d)" % H)
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the batch, served-stream and precision legs of the default line")
+    ap.add_argument("--serve5-requests", type=int, default=160,
+                    help="requests of the served-batch leg of the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -769,10 +945,19 @@ def main():
                                  "kernel": f"k_gram_tc<128,{prec_},fused update>"}
         secondary = secondary_workloads(ctx, stream)
 
+    batch = serve5 = prec_study = None
+    if not args.no_sweep and not args.quick and rank == 0:
+        batch = batch_study(ctx, stream)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(X.cpu().numpy(), y.cpu().numpy())
 
+    if not args.no_sweep and not args.quick and rank == 0:
+        del X, XP
+        torch.cuda.empty_cache()
+        serve5 = serve_config5(args)
+        torch.cuda.empty_cache()
+        prec_study = precision_study(args, emit=False)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -786,6 +971,7 @@ def main():
             "solve_fp64": solve_f64, "time_to_certified_1e-6": race,
             **{f"roofline_{p}_gram": r for p, r in roof_other.items()},
             "other_workloads": secondary,
+            "batch": batch, "serve": serve5, "precision_study": prec_study,
             "input_layout": "X resident on the device in the library's 32-column panel layout "
                             "(ca_pack_panels once before the timed region, CA_DENSE_F32_PANELS)",
             "value_rowmajor_input": {"value": world * h_run / (ms_step_rm * 1e-3),

@@ -502,7 +502,9 @@ class Server:
         if st != CA_OK:
             raise CaError(st, "ca_server_wait")
         self._keep.pop(int(rid), None)
-        return {f: getattr(out, f) for f, _ in ca_result._fields_}
+        res = {f: getattr(out, f) for f, _ in ca_result._fields_}
+        res["bound"] = res["bound"] if res["bound"] >= 0.0 else None  # -1: none formed
+        return res
 
     def drain(self):
         st = self._lib.ca_server_drain(self.handle)
