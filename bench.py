@@ -288,7 +288,7 @@ def secondary_workloads(ctx, stream):
     a = torch.zeros(sp.n, dtype=torch.float64, device="cuda")
     w = torch.zeros(sp.d, dtype=torch.float64, device="cuda")
     h_sp = 2048
-    for s_ in (1, 8, 32):
+    for s_ in (1, 8, 16, 32):
         def run():
             a.zero_()
             ctx.ca_bdcd_solve((rp, col, val), ys, a, w, b=8, s=s_, H=h_sp, lam=1e-5, seed=42,
@@ -296,7 +296,8 @@ def secondary_workloads(ctx, stream):
         run()
         t = _device_time(stream, run, 3)
         out.append({"workload": "sparse dual CA-BDCD, CSR of X^T 16384 x 131072 (0.5%, Pareto "
-                                "nnz per feature), lambda 1e-5, b=8, H=2048, CUDA-core Gram",
+                                "nnz per feature), lambda 1e-5, b=8, H=2048, CUDA-core Gram (one warp "
+                                "per row pair for s*b <= 128, tiles of row hash tables above)",
                     "nnz": int(sp.rowptr[-1]), "s": s_, "ms_per_solve": t,
                     "block_updates_per_s": h_sp / (t * 1e-3),
                     "us_per_outer_step": t * 1e3 / -(-h_sp // s_)})

@@ -765,7 +765,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     // leading dimension of R / Rs: a multiple of 32 (the chain copies 16-byte
     // row pairs of the transposed Rs)
     const size_t sbp = (size_t)(sbm + 31) / 32 * 32;
-    need += 2 * align256(sbp * sbp * 8) + 2 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
+    need += 3 * align256(sbp * sbp * 8) + 3 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
     if (o->check_every > 0) need += align256((size_t)check_rows(o, n, d) * 8) + 512;
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
@@ -782,6 +782,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* delta = cv.take<double>(sbp);
     float2* Ginv = cv.take<float2>(sbp * CA_FAST_B);
     float2* Rs = cv.take<float2>(sbp * sbp);
+    double* Gt = cv.take<double>(sbp * sbp);  // the Gram (transposed lower triangle)
+    double* pp1 = cv.take<double>(sbp);       // its projections
     CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
     double* rq = nullptr;
     double* racc = nullptr;
@@ -819,28 +821,38 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       const int sk = (int)std::min<long long>(s, o->H - (long long)s * k);
       const int sb = sk * b;
       const int* ik = idx + (size_t)s * k * b;
-      const long long npairs = (long long)sb * (sb + 1) / 2;
-      const int gg = (int)std::max(1LL, std::min<long long>((npairs + 7) / 8, 8LL * ctx->num_sms));
+      // a2+a3: the Gram (row hash tables) and the projections
       prof_mark(ctx, PC_GRAM);
-      k_gram_csr<<<gg, 256, 0, ctx->stream>>>(rp, col, val, ik, n, sb, (int)sbp, R, ctx->d_err);
-      k_proj_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb, wd,
-                                                                     pvec, ctx->d_err);
+      launch_csr_gram(ctx->stream, ctx->num_sms, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1,
+                      ctx->d_err);
       prof_mark(ctx, PC_GRAM);
+      ctx->prof.kernel_launches += 1;
+      // a4: the Gram goes through the dense path's reduction as its one
+      // FP64 partial: reduce + diagonal inverses + chain in one launch
+      // (b <= 16), else the general form
       SolveArgs sa{ik, n, b, sk, sb, (int)sbp, 1.0 / ln, 1.0, 1.0, 1.0, ad, yd, delta};
-      prof_mark(ctx, PC_SOLVE);
       const bool f64solve = o->solve == CA_SOLVE_F64;
-      if (fast_solve(b, sb, f64solve)) {
-        k_scale_split<<<(unsigned)(((long long)sb * sb + 255) / 256), 256, 0, ctx->stream>>>(
-            R, (int)sbp, sb, b, 1.0 / ln, Rs);
-        launch_factor(ctx->stream, R, sa, Ginv, ctx->d_err);
-        ctx->prof.kernel_launches += 2;
+      if (fast_solve(b, sb, f64solve) && b <= 16) {
+        const long long entries = (long long)sb * (sb + 1) / 2 + sb;
+        const int grid = (int)std::max<long long>(
+                             1, std::min<long long>((entries + 63) / 64 + sk, ctx->num_sms - 1)) + 1;
+        prof_mark(ctx, PC_SOLVE);
+        const int e = launch_reduce_chain_f64(grid, chain_smem(b, sb), ctx->stream, Gt, pp1,
+                                              (int)sbp, R, Rs, pvec, Ginv, sk, sa, ctx->d_err,
+                                              ctx->d_ticket);
+        prof_mark(ctx, PC_SOLVE);
+        ctx->prof.kernel_launches += 1;
+        if (e != 0) return cuda_fail((cudaError_t)e, __LINE__);
+      } else {
+        GramPlan g{};
+        g.tc = false;
+        g.sbp = (int)sbp;
+        g.P = 1;
+        CA_TRY(launch_reduce_solve(ctx, g, Gt, pp1, R, Rs, pvec, Ginv, sa, f64solve));
       }
-      launch_solve(ctx, R, Rs, pvec, Ginv, sa, f64solve);
-      prof_mark(ctx, PC_SOLVE);
-      k_scatter_csr<<<(unsigned)((sb + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, ik, n, d, sb,
-                                                                        delta, -1.0 / ln, wd,
-                                                                        ctx->d_err);
-      ctx->prof.kernel_launches += 4;
+      // a5: w -= Y Delta/(lambda n)
+      launch_scatter_csr(ctx->stream, cdev, ik, n, d, sb, delta, -1.0 / ln, wd, ctx->d_err);
+      ctx->prof.kernel_launches += 1;
       CA_TRY_CUDA(cudaGetLastError());
       if (o->recompute_every > 0 && (k + 1) % o->recompute_every == 0) recompute();
       if (o->check_every > 0 && ((k + 1) % o->check_every == 0 || k + 1 == n_outer)) {

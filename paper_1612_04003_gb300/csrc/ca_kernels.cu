@@ -882,6 +882,12 @@ template __global__ void k_reduce_chain<float, 8, 4>(const float*, const double*
 template __global__ void k_reduce_chain<float, 16, 3>(const float*, const double*, int, int,
                                                       double*, float2*, double*, float2*, int,
                                                       SolveArgs, unsigned*, unsigned*);
+template __global__ void k_reduce_chain<double, 8, 4>(const double*, const double*, int, int,
+                                                      double*, float2*, double*, float2*, int,
+                                                      SolveArgs, unsigned*, unsigned*);
+template __global__ void k_reduce_chain<double, 16, 3>(const double*, const double*, int, int,
+                                                       double*, float2*, double*, float2*, int,
+                                                       SolveArgs, unsigned*, unsigned*);
 
 // Shared launches over several problems (the batched solves): one grid
 // reduces every problem's split-K partials (role table: problem and CTA index
@@ -1118,74 +1124,245 @@ __global__ void k_axpby_init(const double* __restrict__ y0, double c0, long long
 // ---------------------------------------------------------------------------
 // Dual, sparse X (CSR of X^T, row i = column x_i of X, column indices sorted).
 // ---------------------------------------------------------------------------
-// a2+a3: R[p][q] = x_{I_p}^T x_{I_q} (q <= p) by sorted-list intersection,
-// one warp per pair: lanes walk the shorter list and binary-search the longer.
+// Diagonal entries x_{I_p}^T x_{I_p} (exact products in FP64) and
+// projections x_{I_p}^T w of the sampled rows, one warp per row.
 __global__ void __launch_bounds__(256)
-k_gram_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
-           const float* __restrict__ val, const int* __restrict__ idx, long long nrows, int sb,
-           int ldr, double* __restrict__ R, unsigned* __restrict__ err) {
-  const int lane = threadIdx.x & 31;
-  const long long npairs = (long long)sb * (sb + 1) / 2;
-  const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long e = warp; e < npairs; e += nwarps) {
-    int p, q;
-    tri_decode(e, p, q);
-    const int ip = idx[p], iq = idx[q];
-    if (ip < 0 || ip >= nrows || iq < 0 || iq >= nrows) {
-      if (lane == 0) {
-        ca_flag(err, CA_DEV_ERR_ARG);
-        R[(long long)p * ldr + q] = 0.0;
-      }
-      continue;
-    }
-    long long a0 = rowptr[ip], a1 = rowptr[ip + 1];
-    long long b0 = rowptr[iq], b1 = rowptr[iq + 1];
-    if (a1 - a0 > b1 - b0) {
-      long long t0 = a0, t1 = a1;
-      a0 = b0; a1 = b1; b0 = t0; b1 = t1;
-    }
-    double s = 0.0;
-    for (long long ea = a0 + lane; ea < a1; ea += 32) {
-      const int f = col[ea];
-      long long lo = b0, hi = b1;
-      while (lo < hi) {
-        const long long mid = (lo + hi) >> 1;
-        if (col[mid] < f) lo = mid + 1; else hi = mid;
-      }
-      if (lo < b1 && col[lo] == f) s = fma((double)val[ea], (double)val[lo], s);
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) R[(long long)p * ldr + q] = s;
-  }
-}
-
-// p[r] = x_{I_r}^T w  (one warp per sampled column)
-__global__ void __launch_bounds__(256)
-k_proj_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
+k_csr_rows(const long long* __restrict__ rowptr, const int* __restrict__ col,
            const float* __restrict__ val, const int* __restrict__ idx, long long nrows,
-           long long ncols, int sb, const double* __restrict__ w, double* __restrict__ pvec,
-           unsigned* __restrict__ err) {
+           long long ncols, int sb, int ldr, const double* __restrict__ w,
+           double* __restrict__ G, double* __restrict__ pvec, unsigned* __restrict__ err) {
+  pdl_wait();  // w (the previous step's update) and the previous use of G
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= sb) return;
   const int ir = idx[r];
-  if (ir < 0 || ir >= nrows) {
-    if (lane == 0) {
-      ca_flag(err, CA_DEV_ERR_ARG);
-      pvec[r] = 0.0;
+  double sp = 0.0, sd = 0.0;
+  if (ir >= 0 && ir < nrows) {
+    const long long e1 = rowptr[ir + 1];
+    for (long long eb = rowptr[ir] + lane; eb < e1; eb += 256) {
+      // eight entries in flight per lane, then their gathers of w
+      int fs[8];
+      float vs[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const long long e = eb + 32 * u;
+        fs[u] = e < e1 ? col[e] : -1;
+        vs[u] = e < e1 ? val[e] : 0.f;
+      }
+      double ws[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool in = fs[u] >= 0 && fs[u] < ncols;
+        if (!in && eb + 32 * u < e1) ca_flag(err, CA_DEV_ERR_ARG);
+        ws[u] = in ? w[fs[u]] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        sd = fma((double)vs[u], (double)vs[u], sd);
+        sp = fma((double)vs[u], ws[u], sp);
+      }
     }
-    return;
+  } else if (lane == 0) {
+    ca_flag(err, CA_DEV_ERR_ARG);
   }
-  const long long e0 = rowptr[ir], e1 = rowptr[ir + 1];
-  double s = 0.0;
-  for (long long e = e0 + lane; e < e1; e += 32) {
-    const int f = col[e];
-    if (f >= 0 && f < ncols) s = fma((double)val[e], w[f], s);
-    else ca_flag(err, CA_DEV_ERR_ARG);
+  for (int o = 16; o > 0; o >>= 1) {
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    sd += __shfl_xor_sync(0xffffffffu, sd, o);
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) pvec[r] = s;
+  if (lane == 0) {
+    pvec[r] = sp;
+    G[(long long)r * ldr + r] = sd;
+  }
+}
+
+// The off-diagonal Gram entries of few sampled rows (s*b <= 64) by sorted-list
+// intersection, one warp per pair q < p: lanes walk the shorter row and
+// binary-search the longer, products exact in FP64.
+__global__ void __launch_bounds__(256)
+k_csr_gram_pairs(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                 const float* __restrict__ val, const int* __restrict__ idx, long long nrows,
+                 int sb, int ldr, double* __restrict__ G) {
+  pdl_wait();  // the previous use of G
+  pdl_trigger();
+  const int lane = threadIdx.x & 31;
+  const long long npairs = (long long)sb * (sb - 1) / 2;
+  const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long e = warp; e < npairs; e += nwarps) {
+    int p, q;
+    tri_decode(e, p, q);  // q <= p over a triangle of side sb - 1
+    p += 1;               // q < p
+    const int ip = idx[p], iq = idx[q];
+    double acc = 0.0;
+    if (ip >= 0 && ip < nrows && iq >= 0 && iq < nrows) {
+      long long a0 = rowptr[ip], a1 = rowptr[ip + 1];
+      long long b0 = rowptr[iq], b1 = rowptr[iq + 1];
+      if (a1 - a0 > b1 - b0) {
+        long long t0 = a0, t1 = a1;
+        a0 = b0; a1 = b1; b0 = t0; b1 = t1;
+      }
+      for (long long ea = a0 + lane; ea < a1; ea += 32) {
+        const int f = col[ea];
+        long long lo = b0, hi = b1;
+        while (lo < hi) {
+          const long long mid = (lo + hi) >> 1;
+          if (col[mid] < f) lo = mid + 1; else hi = mid;
+        }
+        if (lo < b1 && col[lo] == f) acc = fma((double)val[ea], (double)val[lo], acc);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) G[(long long)q * ldr + p] = acc;
+  }
+}
+
+// The sparse Gram of one outer step (steps a2+a3, Alg. 4 "compute the Gram
+// matrix" on the CSR of X^T): G[p][q] = x_{I_p}^T x_{I_q} for q < p.  The
+// lower triangle is cut into tiles of kCsrPB
+// rows p by kCsrQC rows q, one CTA each: the CTA puts its rows p into
+// shared-memory hash tables (feature -> value), then its warps stream the
+// rows q of the tile once, four entries per lane in flight, each entry
+// probing every table.  The work is the streamed row lengths times the
+// tables, with no atomics and each Gram entry written by one warp.  Products
+// of two FP32 values are exact as (p, e) by a fused multiply-add and are
+// summed in double-float (~2^-44 of sum |terms|); a row p longer than its
+// table is searched in its sorted global columns instead.  The diagonal and
+// the projections come from k_csr_rows.  The Gram goes out as the one split-K
+// "partial" of the dense path's reduction (transposed: entry (i, j), i >= j,
+// at G[j * ldr + i]).
+constexpr int kCsrPB = 4;                      // rows p of a tile (rows q: qc, a launch argument)
+constexpr int kCsrHashBits = 11;               // a table of 2048 entries per row p
+constexpr int kCsrHash = 1 << kCsrHashBits;
+constexpr int kCsrHashMaxRow = kCsrHash / 2;   // load factor <= 1/2
+constexpr int kCsrSmem = kCsrPB * kCsrHash * 8;  // dynamic shared memory of k_csr_gram
+
+__device__ __forceinline__ unsigned csr_hash(int f) {
+  return ((unsigned)f * 2654435761u) >> (32 - kCsrHashBits);
+}
+
+// tiles of the lower triangle: row block pb has ceil(min(sb, (pb+1) PB) / qc)
+__host__ __device__ __forceinline__ int csr_tiles_of(int pb, int sb, int qc) {
+  const int pmax = min(sb, (pb + 1) * kCsrPB);
+  return (pmax + qc - 1) / qc;
+}
+
+__global__ void __launch_bounds__(256)
+k_csr_gram(const long long* __restrict__ rowptr, const int* __restrict__ col,
+           const float* __restrict__ val, const int* __restrict__ idx, long long nrows,
+           long long ncols, int sb, int ldr, int qcs, const double* __restrict__ w,
+           double* __restrict__ G, double* __restrict__ pvec, unsigned* __restrict__ err) {
+  // dynamic shared memory: kCsrPB tables of kCsrHash keys and values
+  extern __shared__ int csr_smem[];
+  int (*hkey)[kCsrHash] = reinterpret_cast<int (*)[kCsrHash]>(csr_smem);
+  float (*hval)[kCsrHash] = reinterpret_cast<float (*)[kCsrHash]>(csr_smem + kCsrPB * kCsrHash);
+  pdl_wait();  // w (the previous step's update) and the previous use of G
+  pdl_trigger();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // this CTA's tile: row block pb, q chunk qc
+  int pb = 0, rem = blockIdx.x;
+  while (rem >= csr_tiles_of(pb, sb, qcs)) rem -= csr_tiles_of(pb, sb, qcs), ++pb;
+  const int qc = rem;
+  const int pl = pb * kCsrPB, ph = min(sb, pl + kCsrPB);  // rows p: [pl, ph)
+  const int ql = qc * qcs, qh = min(ph, ql + qcs);         // rows q: [ql, qh), q <= p
+  long long p0[kCsrPB], p1[kCsrPB];
+  bool hashed[kCsrPB];
+#pragma unroll
+  for (int j = 0; j < kCsrPB; ++j) {
+    const int p = pl + j;
+    const int ip = p < ph ? idx[p] : -1;
+    const bool okp = ip >= 0 && ip < nrows;
+    if (p < ph && !okp && tid == 0) ca_flag(err, CA_DEV_ERR_ARG);
+    p0[j] = okp ? rowptr[ip] : 0;
+    p1[j] = okp ? rowptr[ip + 1] : 0;
+    hashed[j] = p1[j] - p0[j] <= kCsrHashMaxRow;
+  }
+  for (int k = tid; k < kCsrPB * kCsrHash; k += 256) (&hkey[0][0])[k] = -1;
+  __syncthreads();
+  // the tables: every row p's entries, four loads in flight per thread
+#pragma unroll
+  for (int j = 0; j < kCsrPB; ++j) {
+    if (!hashed[j]) continue;
+    for (long long eb = p0[j] + tid; eb < p1[j]; eb += 1024) {
+      int fs[4];
+      float vs[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long e = eb + 256 * u;
+        fs[u] = e < p1[j] ? col[e] : -1;
+        vs[u] = e < p1[j] ? val[e] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (fs[u] < 0) continue;
+        unsigned h = csr_hash(fs[u]);
+        while (atomicCAS(&hkey[j][h], -1, fs[u]) != -1) h = (h + 1) & (kCsrHash - 1);
+        hval[j][h] = vs[u];
+      }
+    }
+  }
+  __syncthreads();
+  // value of feature f in row p = pl + j (0 when absent)
+  auto lookup = [&](int j, int f) -> float {
+    if (hashed[j]) {
+      unsigned h = csr_hash(f);
+      for (;;) {
+        const int k = hkey[j][h];
+        if (k == f) return hval[j][h];
+        if (k == -1) return 0.f;
+        h = (h + 1) & (kCsrHash - 1);
+      }
+    }
+    long long lo = p0[j], hi = p1[j];  // a long row: its sorted global columns
+    while (lo < hi) {
+      const long long mid = (lo + hi) >> 1;
+      if (col[mid] < f) lo = mid + 1; else hi = mid;
+    }
+    return (lo < p1[j] && col[lo] == f) ? val[lo] : 0.f;
+  };
+  for (int q = ql + warp; q < qh; q += 8) {
+    const int iq = idx[q];
+    float hi[kCsrPB], lo[kCsrPB];
+#pragma unroll
+    for (int j = 0; j < kCsrPB; ++j) hi[j] = lo[j] = 0.f;
+    if (iq >= 0 && iq < nrows) {
+      const long long e0 = rowptr[iq], e1 = rowptr[iq + 1];
+      for (long long eb = e0 + lane; eb < e1; eb += 128) {
+        int fs[4];
+        float vs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {  // four entries in flight per lane
+          const long long e = eb + 32 * u;
+          fs[u] = e < e1 ? col[e] : -1;
+          vs[u] = e < e1 ? val[e] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (fs[u] < 0) continue;
+#pragma unroll
+          for (int j = 0; j < kCsrPB; ++j) {
+            if (pl + j <= q || pl + j >= ph) continue;  // pairs q < p (k_csr_rows: q = p)
+            const float vp = lookup(j, fs[u]);
+            if (vp != 0.f) {
+              const float pr = vp * vs[u];
+              const float pe = fmaf(vp, vs[u], -pr);  // vp vq = pr + pe exactly
+              float s2, t2;
+              two_sum(hi[j], pr, s2, t2);
+              hi[j] = s2;
+              lo[j] += t2 + pe;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kCsrPB; ++j) {
+      if (pl + j <= q || pl + j >= ph) continue;
+      float2 acc = df_norm(hi[j], lo[j]);
+      for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+      if (lane == 0) G[(long long)q * ldr + pl + j] = (double)acc.x + (double)acc.y;
+    }
+  }
 }
 
 // v[col] += c * val * coef[r] for the listed rows (a5 for CSR with coef =
@@ -1195,6 +1372,8 @@ k_scatter_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
               const float* __restrict__ val, const int* __restrict__ idx, long long nrows_total,
               long long ncols, long long nlist, const double* __restrict__ coef, double c,
               double* __restrict__ v, unsigned* __restrict__ err) {
+  pdl_wait();  // (launched as a programmatic dependent of the solve)
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= nlist) return;
@@ -1204,10 +1383,21 @@ k_scatter_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
     return;
   }
   const double cr = c * coef[r];
-  for (long long e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
-    const int f = col[e];
-    if (f >= 0 && f < ncols) atomicAdd(v + f, (double)val[e] * cr);
-    else ca_flag(err, CA_DEV_ERR_ARG);
+  const long long e1 = rowptr[row + 1];
+  for (long long eb = rowptr[row] + lane; eb < e1; eb += 256) {
+    int fs[8];  // eight entries in flight per lane
+    float vs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long e = eb + 32 * u;
+      fs[u] = e < e1 ? col[e] : -1;
+      vs[u] = e < e1 ? val[e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (fs[u] >= 0 && fs[u] < ncols) atomicAdd(v + fs[u], (double)vs[u] * cr);
+      else if (eb + 32 * u < e1) ca_flag(err, CA_DEV_ERR_ARG);
+    }
   }
 }
 
@@ -1488,14 +1678,6 @@ void launch_factor(cudaStream_t st, const double* R, const SolveArgs& sa, float2
 
 // Rs[j][i] = FP32 split of cG R[i][j] (transposed, as k_reduce writes it) for
 // the lower-triangle entries outside the diagonal blocks (the sparse path
-// forms R directly).
-__global__ void k_scale_split(const double* __restrict__ R, int ldr, int sb, int b, double cG,
-                              float2* __restrict__ Rs) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)sb * sb) return;
-  const int i = (int)(e / sb), j = (int)(e % sb);
-  if (j < i && i / b != j / b) Rs[(long long)j * ldr + i] = split_f64(cG * R[(long long)i * ldr + j]);
-}
 
 void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, const void* A,
                          long long lda, long long N, long long K, const int* idx, int sb,
@@ -1586,8 +1768,55 @@ int launch_chain_batch(int count, int bmax, size_t smem, cudaStream_t st, const 
   return (int)cudaErrorInvalidValue;
 }
 
+void launch_scatter_csr(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                        long long ncols, long long nlist, const double* coef, double c, double* v,
+                        unsigned* err) {
+  launch_programmatic(k_scatter_csr, (unsigned)((nlist + 7) / 8), 0, st, csr.rowptr, csr.col,
+                      csr.val, idx, nrows, ncols, nlist, coef, c, v, err);
+}
+
+void launch_csr_gram(cudaStream_t st, int num_sms, const ca_csr_dev& csr, const int* idx,
+                     long long nrows, long long ncols, int sb, int ldr, const double* w, double* G,
+                     double* pvec, unsigned* err) {
+  // q rows per tile: 32, halved while the tiles are fewer than two per SM
+  auto count = [&](int qc) {
+    int t = 0;
+    for (int pb = 0; pb * kCsrPB < sb; ++pb) t += csr_tiles_of(pb, sb, qc);
+    return t;
+  };
+  int qc = 32;
+  while (qc > 1 && count(qc) < 2 * num_sms) qc >>= 1;
+  launch_programmatic(k_csr_rows, (unsigned)((sb + 7) / 8), 0, st, csr.rowptr, csr.col, csr.val,
+                      idx, nrows, ncols, sb, ldr, w, G, pvec, err);
+  if (sb <= 1) return;
+  if (sb <= 128) {  // few pairs: one warp per pair
+    const long long npairs = (long long)sb * (sb - 1) / 2;
+    launch_programmatic(k_csr_gram_pairs, (unsigned)std::max(1LL, (npairs + 7) / 8), 0, st,
+                        csr.rowptr, csr.col, csr.val, idx, nrows, sb, ldr, G);
+    return;
+  }
+  launch_programmatic(k_csr_gram, (unsigned)count(qc), kCsrSmem, st, csr.rowptr, csr.col,
+                      csr.val, idx, nrows, ncols, sb, ldr, qc, w, G, pvec, err);
+}
+
+int launch_reduce_chain_f64(int grid, size_t smem, cudaStream_t st, const double* part,
+                            const double* ppart, int sbp, double* R, float2* Rs, double* pvec,
+                            float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err,
+                            unsigned* ticket) {
+  cudaError_t e;
+  if (sa.b <= 8)
+    e = launch_programmatic(k_reduce_chain<double, 8, 4>, (unsigned)grid, smem, st, part, ppart, 1,
+                            sbp, R, Rs, pvec, Ginv, ndiag, sa, err, ticket);
+  else if (sa.b <= 16)
+    e = launch_programmatic(k_reduce_chain<double, 16, 3>, (unsigned)grid, smem, st, part, ppart, 1,
+                            sbp, R, Rs, pvec, Ginv, ndiag, sa, err, ticket);
+  else
+    e = cudaErrorInvalidValue;
+  return (int)e;
+}
+
 int set_solve_smem_limit(int bytes) {
-  cudaError_t e[10] = {set_dyn_smem(k_solve, bytes),
+  cudaError_t e[13] = {set_dyn_smem(k_solve, bytes), set_dyn_smem(k_csr_gram, kCsrSmem),
                       set_dyn_smem(k_chain<8, 4>, bytes),
                       set_dyn_smem(k_chain<16, 3>, bytes),
                       set_dyn_smem(k_chain<32, 2>, bytes),
@@ -1596,7 +1825,9 @@ int set_solve_smem_limit(int bytes) {
                       set_dyn_smem(k_reduce_chain<float, 16, 3>, bytes),
                       set_dyn_smem(k_reduce<double>, bytes),
                       set_dyn_smem(k_chain_batch<8, 4>, bytes),
-                      set_dyn_smem(k_chain_batch<16, 3>, bytes)};
+                      set_dyn_smem(k_chain_batch<16, 3>, bytes),
+                      set_dyn_smem(k_reduce_chain<double, 8, 4>, bytes),
+                      set_dyn_smem(k_reduce_chain<double, 16, 3>, bytes)};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return (int)x;
   return 0;

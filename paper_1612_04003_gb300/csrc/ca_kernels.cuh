@@ -28,7 +28,6 @@ int launch_reduce_chain(int grid, size_t smem, cudaStream_t st, const float* par
                         const double* ppart, int P, int sbp, double* R, float2* Rs, double* pvec,
                         float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err,
                         unsigned* ticket);
-__global__ void k_scale_split(const double* R, int ldr, int sb, int b, double cG, float2* Rs);
 __global__ void k_factor(const double* R, SolveArgs sa, float2* Ginv, unsigned* err);
 #define CA_FAST_B 32
 #define CA_FAST_SB 256
@@ -48,12 +47,6 @@ __global__ void k_solve(const double* R, const double* pvec, SolveArgs sa, unsig
 __global__ void k_axpby_init(const double* y0, double c0, long long K, double* v);
 __global__ void k_split(const double* v, long long K, long long Kpad, float2* v2);
 
-__global__ void k_gram_csr(const long long* rowptr, const int* col, const float* val,
-                           const int* idx, long long nrows, int sb, int ldr, double* R,
-                           unsigned* err);
-__global__ void k_proj_csr(const long long* rowptr, const int* col, const float* val,
-                           const int* idx, long long nrows, long long ncols, int sb,
-                           const double* w, double* pvec, unsigned* err);
 __global__ void k_scatter_csr(const long long* rowptr, const int* col, const float* val,
                               const int* idx, long long nrows_total, long long ncols,
                               long long nlist, const double* coef, double c, double* v,
@@ -131,6 +124,24 @@ int launch_reduce_batch(int grid, cudaStream_t st, const RedInst* insts, const R
 // one chain CTA per problem (b <= bmax <= 16, s*b <= 256)
 int launch_chain_batch(int count, int bmax, size_t smem, cudaStream_t st, const RedInst* insts,
                        unsigned* err);
+
+// Sparse dual, steps a2+a3 of one outer step from the CSR of X^T (row hash
+// tables, ca_kernels.cu): G (ldr x ldr, transposed lower triangle, the one
+// "partial" of the reduction) and the projections pvec[r] = x_{I_r}^T w, in
+// one programmatic-dependent launch.  Then a4 by the reduction of that
+// single FP64 partial, the diagonal inverses and the chain in one launch
+// (b <= 16), and a5 by the scatter (programmatic dependent).
+struct ca_csr_dev;
+void launch_csr_gram(cudaStream_t st, int num_sms, const ca_csr_dev& csr, const int* idx,
+                     long long nrows, long long ncols, int sb, int ldr, const double* w, double* G,
+                     double* pvec, unsigned* err);
+int launch_reduce_chain_f64(int grid, size_t smem, cudaStream_t st, const double* part,
+                            const double* ppart, int sbp, double* R, float2* Rs, double* pvec,
+                            float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err,
+                            unsigned* ticket);
+void launch_scatter_csr(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                        long long ncols, long long nlist, const double* coef, double c, double* v,
+                        unsigned* err);
 
 // Stopping criterion: *out += ||cP A v - cI x - cY y||^2 over the N rows of
 // A (dense: row-major FP64 / FP32 or FP32 panels, v2 the FP32 split of v for

@@ -10,8 +10,7 @@ tolerance 1e-5, and to its solo solve at the same 1e-5: both are FP32-Gram
 roundings of one exact path, each within 1e-5 of it (measured: batch vs
 solo 1.2e-7 .. 1.05e-6, each vs the oracle 8e-8 .. 2.5e-6).  The
 graph-captured and the plainly launched batch run the same kernels on the
-same data and must agree bit for bit in the iterates (the final z = X^T w_H
-adds row splits with FP64 atomics: to rounding).
+same data and agree up to the order of FP64 atomic additions (1e-13).
 """
 import numpy as np
 import pytest
@@ -129,9 +128,10 @@ def test_graph_and_plain_launches_agree_bitwise(ca_ctx):
     ctx.ca_batch_solve(a, graph=True)
     ctx.ca_batch_solve(b, graph=False)
     for pa, pb in zip(a, b):
-        assert torch.equal(pa["x"], pb["x"])
-        # (z = X^T w_H of a primal problem sums its row splits with FP64
-        # atomics, in no fixed order)
+        # the same kernels on the same data: equal up to the order of FP64
+        # atomic additions (an index recurring across the blocks of an outer
+        # step is updated atomically; z = X^T w_H adds row splits atomically)
+        assert _rel(pa["x"], pb["x"]) < 1e-13
         assert _rel(pa["aux"], pb["aux"]) < 1e-13
 
 
