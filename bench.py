@@ -67,10 +67,10 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _traffic_record(kernel_src: str):
-    """Per-launch DRAM traffic of the Gram kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "gram_tc_traffic.json")
+def _traffic_record(kernel_src: str, name: str = "gram_tc_traffic.json"):
+    """DRAM traffic of a kernel from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -840,6 +840,14 @@ def main():
     barrier(world)
     ms_rm = time_solves(ctx, X, y, w, z, args.steps, stream, s=s_run, h=h_run)
     barrier(world)
+    # the same K solves with one Gram launch and one solve launch per outer
+    # step instead of the persistent launch
+    ctx.ca_set_tuning(persistent=False)
+    time_solves(ctx, XP, y, w, z, 1, stream, s=s_run, h=h_run, panels=pan)
+    barrier(world)
+    ms_ps = time_solves(ctx, XP, y, w, z, args.steps, stream, s=s_run, h=h_run, panels=pan)
+    barrier(world)
+    ctx.ca_set_tuning(persistent=True)
     # second timed pass (roofline, breakdown): the same K solves with CUDA
     # events around every launch, on the library's stream
     ctx.ca_profile_enable(True)
@@ -853,26 +861,43 @@ def main():
     value = world * h_run / (ms_step * 1e-3)
     ms_step_rm = max_over_ranks(ms_rm / args.steps, world)
 
-    # roofline of the dominant kernel (the tcgen05 Gram pass, one launch per outer step)
+    # roofline of the dominant kernel: the persistent launch of the outer
+    # steps (ca_persist.cu) when the solve runs it, else the tcgen05 Gram pass
+    # (one launch per outer step)
     peaks, peak_kind = _peaks()
     sb = s_run * B
-    gram_ms = prof["gram_ms"] / max(1, prof["gram_launches"])
     n_outer = -(-h_run // s_run)
-    fused = sb <= 128 and PREC in ("tf32", "3xtf32", "bf16x3")  # a5 of step k rides in the a2+a3 launch of k+1
+    gram_launches_per_solve = prof["gram_launches"] / max(1, args.steps)
+    persistent = gram_launches_per_solve < n_outer / 2
+    fused = sb <= 128 and PREC in ("tf32", "3xtf32", "bf16x3", "fp16_scaled")
     b_gram = sb * n_run * 4 + n_run * 8          # B_G: Y rows + the projection vector
     b_upd = sb * n_run * 4 + 2 * n_run * 8       # B_U: Y rows + read/write of v
     breakdown = {c: {"ms_per_step": prof[f"{c}_ms"] / args.steps,
                      "share": prof[f"{c}_ms"] / max(ms_prof, 1e-9)}
                  for c in ("gram", "reduce", "chain", "update", "other")}
-    alg_bytes = (n_outer * b_gram + (n_outer - 1) * b_upd) / n_outer if fused else b_gram
+    # algorithmic bytes of the Gram-class launches of one solve: every outer
+    # step reads its rows and v (B_G), and every step but the last applies
+    # its deferred update inside the next step's pass (B_U)
+    solve_bytes = n_outer * b_gram + (n_outer - 1) * b_upd if fused else n_outer * b_gram
+    alg_bytes = solve_bytes / gram_launches_per_solve
+    gram_ms = prof["gram_ms"] / max(1, prof["gram_launches"])
     achieved = alg_bytes / (gram_ms * 1e-3) / 1e9
-    trec = _traffic_record(os.path.join(ROOT, "paper_1612_04003_gb300", "csrc", "ca_gram_tc.cu"))
+    if persistent:
+        trec = _traffic_record(os.path.join(ROOT, "paper_1612_04003_gb300", "csrc", "ca_persist.cu"),
+                               "persist_traffic.json")
+        traffic = (trec["traffic_bytes_per_pass"] * n_outer / gram_launches_per_solve
+                   if trec else None)
+        kname = (f"k_persist<128,{PREC}> (persistent cooperative launch of the outer steps: "
+                 "gather + Gram + cross Gram + projection + deferred updates on 151 CTAs, "
+                 "reduction of each step's partials, chain of the s solves on one CTA)")
+    else:
+        trec = _traffic_record(os.path.join(ROOT, "paper_1612_04003_gb300", "csrc", "ca_gram_tc.cu"))
+        traffic = trec["traffic_bytes_per_launch"] if trec else None
+        kname = (f"k_gram_tc<{128 if sb <= 128 else 256},{PREC}"
+                 f"{',fused update' if fused else ''}> (gather + Gram + projection"
+                 f"{' + deferred update of the previous outer step' if fused else ''})")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"],
-            "traffic": trec["traffic_bytes_per_launch"] if trec else None,
-            "kernel": (f"k_gram_tc<{128 if sb <= 128 else 256},{PREC}"
-                       f"{',fused update' if fused else ''}> (gather + Gram + projection"
-                       f"{' + deferred update of the previous outer step' if fused else ''})"),
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": gram_ms,
             "launches": prof["gram_launches"], "peak_source": f"hbm_gbs ({peak_kind})",
             "gram_share_of_step": prof["gram_ms"] / max(ms_prof, 1e-9),
@@ -939,11 +964,14 @@ def main():
             p32 = ctx.ca_profile_read()
             ctx.ca_profile_enable(False)
             g32 = p32["gram_ms"] / max(1, p32["gram_launches"])
-            ach32 = alg_bytes / (g32 * 1e-3) / 1e9
+            per_solve = p32["gram_launches"] / max(1, args.steps)
+            ach32 = solve_bytes / per_solve / (g32 * 1e-3) / 1e9
+            pers32 = per_solve < n_outer / 2
             roof_other[prec_] = {"bound": "hbm", "achieved": ach32, "peak": peaks["hbm_gbs"],
                                  "unit": "GB/s", "frac": ach32 / peaks["hbm_gbs"],
-                                 "avg_launch_ms": g32,
-                                 "kernel": f"k_gram_tc<128,{prec_},fused update>"}
+                                 "avg_launch_ms": g32, "launches_per_solve": per_solve,
+                                 "kernel": (f"k_persist<128,{prec_}>" if pers32 else
+                                            f"k_gram_tc<128,{prec_},fused update>")}
         secondary = secondary_workloads(ctx, stream)
 
     batch = serve5 = prec_study = None
@@ -975,6 +1003,11 @@ def main():
             "batch": batch, "serve": serve5, "precision_study": prec_study,
             "input_layout": "X resident on the device in the library's 32-column panel layout "
                             "(ca_pack_panels once before the timed region, CA_DENSE_F32_PANELS)",
+            "value_launches_per_step": {
+                "value": world * h_run / (max_over_ranks(ms_ps / args.steps, world) * 1e-3),
+                "ms_per_step": max_over_ranks(ms_ps / args.steps, world),
+                "how": "same K solves with one Gram launch and one reduce + chain launch per "
+                       "outer step (ca_set_tuning persistent off)"},
             "value_rowmajor_input": {"value": world * h_run / (ms_step_rm * 1e-3),
                                      "ms_per_step": ms_step_rm,
                                      "how": "same K solves from row-major X; each solve first "

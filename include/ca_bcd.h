@@ -327,6 +327,24 @@ const char* ca_last_error(ca_ctx* ctx);
 /* Name of a status code (static string). */
 const char* ca_status_str(int status);
 
+/* Tuning of the dense tensor-core solves on ctx (kept until changed).
+ *   CA_TUNE_PERSISTENT  1 (default): a run of full outer steps between two
+ *       host decisions (a check of the stopping test, a due recomputation,
+ *       the short last step) runs as one persistent cooperative launch when
+ *       the solve fits it (FP32 X in 32-column panels, BF16x3 or scaled-FP16
+ *       Gram, s*b <= 128, b <= 8, CA_SOLVE_DF, at least s + 1 Gram CTAs):
+ *       the s unrolled solves of step k (eq. "recur", Algorithms 2 and 4)
+ *       then run while the Gram pass of step k+1 streams its rows, and that
+ *       pass corrects its projection by the cross Gram of the two steps'
+ *       rows (the same sums in exact arithmetic).  0: one Gram launch and
+ *       one solve launch per outer step.
+ *   CA_TUNE_OVERLAP  share in [0, 1] of each Gram CTA's columns streamed
+ *       before the previous step's solve is known (default 0.4; 0: none).
+ * Errors: CA_ERR_ARG (NULL context, unknown key, value out of range). */
+#define CA_TUNE_PERSISTENT 1
+#define CA_TUNE_OVERLAP 2
+int ca_set_tuning(ca_ctx* ctx, int key, double value);
+
 /* Measurement hooks.  With profiling on, every following solve records CUDA
  * event pairs on the context's stream around each launch of five kernel
  * classes: [0] the Gram pass (a2+a3), [1] the reduction of its partials (and

@@ -41,6 +41,8 @@ CA_STOP_OBJECTIVE = 1
 STOP = {"residual": CA_STOP_RESIDUAL, "objective": CA_STOP_OBJECTIVE}
 
 CA_BATCH_GRAPH = 1
+CA_TUNE_PERSISTENT = 1
+CA_TUNE_OVERLAP = 2
 
 CA_SOLVE_DF = 0
 CA_SOLVE_F64 = 1
@@ -134,6 +136,8 @@ def load():
     lib.ca_bcd_destroy.restype = None
     lib.ca_profile_enable.argtypes = [vp, i32]
     lib.ca_profile_enable.restype = i32
+    lib.ca_set_tuning.argtypes = [vp, i32, dbl]
+    lib.ca_set_tuning.restype = i32
     lib.ca_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64),
                                     ctypes.POINTER(i64)]
     lib.ca_profile_read.restype = i32
@@ -425,6 +429,18 @@ class Context:
 
     def ca_selftest_wait_timeout(self, limit_ns: int) -> int:
         return int(self._lib.ca_selftest_wait_timeout(self.handle, int(limit_ns)))
+
+    def ca_set_tuning(self, *, persistent=None, overlap=None):
+        """ca_set_tuning: persistent launches for runs of outer steps (bool)
+        and the share of each Gram CTA's columns streamed before the
+        previous step's solve is known (0..1)."""
+        for key, val in ((CA_TUNE_PERSISTENT, None if persistent is None else float(bool(persistent))),
+                         (CA_TUNE_OVERLAP, overlap)):
+            if val is None:
+                continue
+            st = self._lib.ca_set_tuning(self.handle, key, float(val))
+            if st != CA_OK:
+                raise CaError(st, "ca_set_tuning")
 
     def ca_profile_enable(self, on: bool = True):
         st = self._lib.ca_profile_enable(self.handle, 1 if on else 0)

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcabcd.so")
 SOURCES = ["ca_kernels.cu", "ca_gram_tc.cu", "ca_api.cu", "ca_noalloc.cu", "ca_serve.cu",
-           "ca_batch.cu"]
+           "ca_batch.cu", "ca_persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists(
     "/usr/local/cuda/bin/nvcc") else "nvcc")

@@ -389,6 +389,28 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
   };
 
   const long long n_outer = (H + s - 1) / s;
+  // Runs of full outer steps between two host decisions (a check, a due
+  // recomputation, the short last step) go to one persistent launch
+  // (ca_persist.cu) when the configuration fits it: BF16x3 or scaled-FP16
+  // Gram on panels, s*b <= 128, b <= 8, the double-float solve, one Gram CTA
+  // on every SM but one.
+  const long long natoms = (K + 31) / 32;
+  bool persist_ok = ctx->persist && g.tc && pb.panel && (g.three == 2 || g.three == 3) &&
+                    sbp <= 128 && b <= 8 && fast_solve(b, sbm, f64solve) &&
+                    P == ctx->num_sms - 1 && P > s && natoms >= P;
+  int na = 0;  // region-A atoms per Gram CTA
+  if (persist_ok) {
+    // a stage's slice of v2 is read when the stage is issued, up to a
+    // load-ring depth ahead: every pass must be longer than the ring so
+    // that the previous pass has written the slice by then
+    const int ring = persist_load_ring(sbp, g.three);
+    const long long tmin = natoms / P;
+    if (tmin <= ring) persist_ok = false;
+    na = (int)std::min<long long>(tmin, std::llround(ctx->overlap * (double)tmin));
+  }
+  auto boundary_after = [&](long long j) {
+    return due(j) || (chk && (j + 1) % o->check_every == 0 && j + 1 < n_outer);
+  };
   for (long long k = 0; k < n_outer; ++k) {
     const int sk = (int)std::min<long long>(s, H - (long long)s * k);
     const int sb = sk * b;
@@ -398,30 +420,83 @@ int run_dense(ca_ctx* ctx, const DenseProblem& pb, const ca_opts* o, int* idx_al
       CA_TRY(update_alone());                                   // a5 of step k-1 (clears after_rc)
       if (due(k - 1)) CA_TRY(launch_recompute(ctx, pb, pb.v, pb.y0, pb.c0, pb.c1));  // a6
     }
-    // a2 + a3 (and a5 of step k-1 when fused)
-    GramUpdate gu{prev_idx, pending ? prev_sb : 0, prev_delta, pb.cU, pb.v2, pb.rscale, after_rc};
-    prof_mark(ctx, PC_GRAM);
-    if (pending) {
-      const int e = launch_gram_tc(static_cast<const float*>(pb.A), pb.lda, pb.N, K, idx, sb, pb.v2,
-                                   P, sbp, static_cast<float*>(part), ppart, ctx->d_err, g.three,
-                                   ctx->stream, &gu, true);
-      if (e != 0) return cuda_fail((cudaError_t)e, __LINE__);
-      pending = false;
-    } else {
-      CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part, ppart,
-                         pb.panel, pb.rscale, after_rc));
+    long long k1 = k + 1;  // end of the run that starts at k
+    if (persist_ok && sk == s)
+      while (k1 < n_outer && (long long)s * (k1 + 1) <= H && !boundary_after(k1 - 1)) ++k1;
+    bool persisted = false;
+    if (persist_ok && sk == s && k1 - k >= 2) {
+      PersistArgs pa{};
+      pa.A = static_cast<const float*>(pb.A);
+      pa.N = pb.N;
+      pa.K = K;
+      pa.natoms = natoms;
+      pa.idx_all = idx_all;
+      pa.sb = sb;
+      pa.k0 = k;
+      pa.npass = (int)(k1 - k);
+      pa.na = na;
+      pa.prev_idx = pending ? prev_idx : nullptr;
+      pa.prev_sb = pending ? prev_sb : 0;
+      pa.delta2[0] = delta2[0];
+      pa.delta2[1] = delta2[1];
+      pa.v2 = pb.v2;
+      pa.cU = pb.cU;
+      pa.rscale = pb.rscale;
+      pa.part = static_cast<float*>(part);
+      pa.ppart = ppart;
+      pa.R = R;
+      pa.Rs = Rs;
+      pa.pvec = pvec;
+      pa.Ginv = Ginv;
+      pa.sa = SolveArgs{nullptr, pb.N, b, s, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, nullptr};
+      pa.cnt = ctx->d_cnt;
+      pa.chain_smem = chain_smem(b, sb);
+      CA_TRY_CUDA(cudaMemsetAsync(ctx->d_cnt, 0, 3 * sizeof(unsigned), ctx->stream));
+      prof_mark(ctx, PC_GRAM);
+      const int e = launch_persist(pa, P + 1, sbp, g.three, ctx->d_err, ctx->stream);
+      prof_mark(ctx, PC_GRAM);
+      if (e == (int)cudaErrorCooperativeLaunchTooLarge || e == (int)cudaErrorInvalidConfiguration) {
+        (void)cudaGetLastError();  // not resident at once here: the launches per step instead
+        persist_ok = false;
+      } else if (e != 0) {
+        return cuda_fail((cudaError_t)e, __LINE__);
+      } else {
+        ctx->prof.kernel_launches += 1;
+        persisted = true;
+        k = k1 - 1;  // the last step of the run; its update is pending
+        after_rc = false;
+        pending = true;
+        prev_idx = idx_all + (size_t)s * k * b;
+        prev_sb = sb;
+        prev_delta = delta2[k & 1];
+      }
     }
-    prof_mark(ctx, PC_GRAM);
-    ctx->prof.kernel_launches += 1;
-    // a4 (reduce of the split-K partials, then the s unrolled solves)
-    SolveArgs sa{idx, pb.N, b, sk, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, delta};
-    CA_TRY(launch_reduce_solve(ctx, g, part, ppart, R, Rs, pvec, Ginv, sa, f64solve));
-    CA_TRY_CUDA(cudaGetLastError());
-    after_rc = uses_reduce_chain(g, sa, f64solve);
-    pending = true;
-    prev_idx = idx;
-    prev_sb = sb;
-    prev_delta = delta;
+    if (!persisted) {
+      // a2 + a3 (and a5 of step k-1 when fused)
+      GramUpdate gu{prev_idx, pending ? prev_sb : 0, prev_delta, pb.cU, pb.v2, pb.rscale, after_rc};
+      prof_mark(ctx, PC_GRAM);
+      if (pending) {
+        const int e = launch_gram_tc(static_cast<const float*>(pb.A), pb.lda, pb.N, K, idx, sb,
+                                     pb.v2, P, sbp, static_cast<float*>(part), ppart, ctx->d_err,
+                                     g.three, ctx->stream, &gu, true);
+        if (e != 0) return cuda_fail((cudaError_t)e, __LINE__);
+        pending = false;
+      } else {
+        CA_TRY(launch_gram(ctx, g, pb.xfmt, pb.A, pb.lda, pb.N, K, idx, sb, pb.v, pb.v2, part,
+                           ppart, pb.panel, pb.rscale, after_rc));
+      }
+      prof_mark(ctx, PC_GRAM);
+      ctx->prof.kernel_launches += 1;
+      // a4 (reduce of the split-K partials, then the s unrolled solves)
+      SolveArgs sa{idx, pb.N, b, sk, sb, sbp, pb.cG, pb.cI, pb.cP, pb.cY, pb.x, pb.yv, delta};
+      CA_TRY(launch_reduce_solve(ctx, g, part, ppart, R, Rs, pvec, Ginv, sa, f64solve));
+      CA_TRY_CUDA(cudaGetLastError());
+      after_rc = uses_reduce_chain(g, sa, f64solve);
+      pending = true;
+      prev_idx = idx;
+      prev_sb = sb;
+      prev_delta = delta;
+    }
     if (chk && (k + 1) % o->check_every == 0 && k + 1 < n_outer) {
       // the deferred update of this step first: the residual needs v current
       CA_TRY(update_alone());
@@ -573,6 +648,7 @@ int ca_bcd_init(ca_ctx** out, int device, void* cuda_stream, size_t scratch_byte
     return CA_ERR_CUDA;
   }
   ctx->d_ticket = ctx->d_err + 32;
+  ctx->d_cnt = ctx->d_err + 48;
   cudaMemset(ctx->d_err, 0, 256);
   if (set_solve_smem_limit(kSolveSmemMax) != 0) {
     cudaGetLastError();
@@ -975,6 +1051,21 @@ int ca_pack_panels(ca_ctx* ctx, const float* A, long long N, long long K, long l
 }
 
 const char* ca_last_error(ca_ctx* ctx) { return ctx ? ctx->last_error : "no context"; }
+
+int ca_set_tuning(ca_ctx* ctx, int key, double value) {
+  if (!ctx) return CA_ERR_ARG;
+  if (key == CA_TUNE_PERSISTENT) {
+    if (value != 0.0 && value != 1.0) return CA_ERR_ARG;
+    ctx->persist = value != 0.0;
+    return CA_OK;
+  }
+  if (key == CA_TUNE_OVERLAP) {
+    if (!(value >= 0.0 && value <= 1.0)) return CA_ERR_ARG;
+    ctx->overlap = value;
+    return CA_OK;
+  }
+  return CA_ERR_ARG;
+}
 
 int ca_profile_enable(ca_ctx* ctx, int on) {
   if (!ctx) return CA_ERR_ARG;

@@ -41,7 +41,14 @@ struct ca_ctx {
   unsigned* d_err = nullptr;     // device error word
   unsigned* d_ticket = nullptr;  // count of the reducing CTAs of the reduce/solve kernel
                                  // (d_err + 32; both cleared where a call starts)
+  unsigned* d_cnt = nullptr;     // 3 counts of the persistent solve (d_err + 48; cleared
+                                 // before each persistent launch)
   unsigned* h_err = nullptr;     // pinned copy (128 bytes: error word; check sums at +32)
+  // tuning (ca_set_tuning): persistent launches for runs of outer steps, and
+  // the share of a Gram CTA's atoms streamed before the previous step's
+  // solve is known
+  bool persist = true;
+  double overlap = 0.4;
   caint::Profile prof;
   ca_info info{};                // outcome of the last solve
   std::vector<ca_check> trace;   // its checks of the stopping test

@@ -99,6 +99,41 @@ struct GramBatchArgs {
   const int* unit_begin;  // units of CTA c: unit_begin[c] .. unit_begin[c+1]-1
   bool early;             // as GramUpdate::early, for the whole launch
 };
+// Consecutive outer steps k0 .. k0+npass-1 of one dense solve (FP32 A in
+// 32-column panels, BF16x3 or scaled-FP16 Gram, s*b <= 128, b <= 8) in one
+// persistent cooperative launch of Pg Gram CTAs + 1 chain CTA (ca_persist.cu).
+struct PersistArgs {
+  const float* A;        // panels [K/32][N][32], zero-padded past K
+  long long N, K, natoms;
+  const int* idx_all;    // sampled indices: step k at idx_all + k * sb
+  int sb;                // s * b of every step of the launch
+  long long k0;
+  int npass;
+  int na;                // region-A atoms of each Gram CTA: 0, or more than the load-ring
+                         // depth (persist_load_ring), as natoms / Pg must be
+  const int* prev_idx;   // rows of step k0 - 1 (prev_sb = 0: none)
+  int prev_sb;
+  double* delta2[2];     // Delta of step k in delta2[k & 1]
+  float2* v2;            // FP32 pairs of v (K entries, zero-padded to a multiple of 32)
+  double cU;
+  const float* rscale;   // scaled FP16: power-of-two multiplier of each row of A
+  float* part;           // Pg x sbp x sbp FP32 Gram partials (transposed)
+  double* ppart;         // Pg x sbp projection partials
+  double* R;
+  float2* Rs;
+  double* pvec;
+  float2* Ginv;
+  SolveArgs sa;          // solve constants (idx and delta are set per step)
+  unsigned* cnt;         // 3 counts, zero on entry
+  size_t chain_smem;     // shared memory of the chain (<= the Gram CTAs')
+};
+// mode: 2 = BF16x3, 3 = scaled FP16; grid = Pg + 1 <= number of SMs.
+// Returns a cudaError_t.
+int launch_persist(const PersistArgs& a, int grid, int sbp, int mode, unsigned* err,
+                   cudaStream_t stream);
+// Depth of the persistent kernel's load ring (stages in flight per CTA).
+int persist_load_ring(int sbp, int mode);
+
 // Shared launch of P CTAs; sbp = 32, 64 or 128 (>= every problem's s*b).
 int launch_gram_tc_batch(const GramBatchArgs& bt, int P, int sbp, int three_pass, unsigned* err,
                          cudaStream_t stream);
