@@ -170,20 +170,21 @@ int launch_recompute(ca_ctx* ctx, const DenseProblem& pb, double* vout, const do
                      double c0, double c1) {
   const long long K = pb.K, N = pb.N;
   const long long gx = (K + 1023) / 1024;
-  long long ysplit = (2LL * ctx->num_sms + gx - 1) / gx;
+  long long ysplit = (4LL * ctx->num_sms + gx - 1) / gx;  // about 4 CTAs per SM
   ysplit = std::max(1LL, std::min(ysplit, (N + 63) / 64));
   const long long rps = (N + ysplit - 1) / ysplit;
   ysplit = (N + rps - 1) / rps;
   dim3 grid((unsigned)gx, (unsigned)ysplit);
   prof_mark(ctx, PC_OTHER);
-  k_axpby_init<<<(unsigned)((K + 255) / 256), 256, 0, ctx->stream>>>(y0, c0, K, vout);
-  if (pb.xfmt == CA_DENSE_F32) {
-    k_split<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(pb.x, N, N, pb.x2);
-    ctx->prof.kernel_launches += 1;
-  }
+  // x = 0 (a solve started from zero) leaves v = c0 y0 without reading A:
+  // the recomputation skips its pass when k_nonzero finds no nonzero x
+  unsigned* nz = ctx->d_err + 56;
+  k_axpby_init<<<(unsigned)((K + 255) / 256), 256, 0, ctx->stream>>>(y0, c0, K, vout, nz);
+  k_nonzero<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(
+      pb.x, N, pb.xfmt == CA_DENSE_F32 ? pb.x2 : nullptr, nz);
   launch_recompute_dense(pb.xfmt == CA_DENSE_F64, grid, ctx->stream, pb.A, pb.lda, N, K, pb.x, pb.x2,
-                         c1, rps, vout, pb.panel);
-  ctx->prof.kernel_launches += 2;
+                         c1, rps, vout, pb.panel, nz);
+  ctx->prof.kernel_launches += 3;
   if (vout == pb.v && pb.v2) {
     const long long Kp = (K + 31) / 32 * 32;
     k_split<<<(unsigned)((Kp + 255) / 256), 256, 0, ctx->stream>>>(pb.v, K, Kp, pb.v2);
@@ -876,7 +877,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       return full_check(ctx, ck, h_at, out, &ctx->info.gap, &ctx->info.fval);
     };
     auto recompute = [&]() {  // w = -X alpha/(lambda n)  (eq. "3")
-      k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd);
+      k_axpby_init<<<(unsigned)((d + 255) / 256), 256, 0, ctx->stream>>>(nullptr, 0.0, d, wd, nullptr);
       k_scatter_csr<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(rp, col, val, nullptr, n, d,
                                                                        n, ad, -1.0 / ln, wd,
                                                                        ctx->d_err);

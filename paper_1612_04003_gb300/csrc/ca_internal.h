@@ -42,7 +42,8 @@ struct ca_ctx {
   unsigned* d_ticket = nullptr;  // count of the reducing CTAs of the reduce/solve kernel
                                  // (d_err + 32; both cleared where a call starts)
   unsigned* d_cnt = nullptr;     // 3 counts of the persistent solve (d_err + 48; cleared
-                                 // before each persistent launch)
+                                 // before each persistent launch); d_err + 56: whether
+                                 // the x of a recomputation has a nonzero entry
   unsigned* h_err = nullptr;     // pinned copy (128 bytes: error word; check sums at +32)
   // tuning (ca_set_tuning): persistent launches for runs of outer steps, and
   // the share of a Gram CTA's atoms streamed before the previous step's

@@ -731,7 +731,10 @@ template <typename T, bool PANEL>
 __global__ void __launch_bounds__(256)
 k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long K,
                   const double* __restrict__ x, const float2* __restrict__ x2, double c1,
-                  long long rows_per_split, double* __restrict__ v) {
+                  long long rows_per_split, double* __restrict__ v,
+                  const unsigned* __restrict__ nz) {
+  // x = 0 (a solve started from zero): sum_r A[r] x[r] = 0, A is not read
+  if (nz && *nz == 0u) return;
   const long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
   if (k >= K) return;
   const int nk = (int)min(4ll, K - k);
@@ -775,13 +778,14 @@ k_recompute_dense(const T* __restrict__ A, long long lda, long long N, long long
 
 template __global__ void k_recompute_dense<double, false>(const double*, long long, long long,
                                                           long long, const double*, const float2*,
-                                                          double, long long, double*);
+                                                          double, long long, double*,
+                                                          const unsigned*);
 template __global__ void k_recompute_dense<float, true>(const float*, long long, long long, long long,
                                                         const double*, const float2*, double,
-                                                        long long, double*);
+                                                        long long, double*, const unsigned*);
 template __global__ void k_recompute_dense<float, false>(const float*, long long, long long, long long,
                                                   const double*, const float2*, double, long long,
-                                                  double*);
+                                                  double*, const unsigned*);
 
 // v2[k] = (hi, lo) FP32 split of v[k]; zero for K <= k < Kpad
 __global__ void k_split(const double* __restrict__ v, long long K, long long Kpad,
@@ -790,11 +794,22 @@ __global__ void k_split(const double* __restrict__ v, long long K, long long Kpa
   if (k < Kpad) v2[k] = k < K ? split_f64(v[k]) : make_float2(0.f, 0.f);
 }
 
-// v = c0 * y0 (or 0 when y0 is null)
+// v = c0 * y0 (or 0 when y0 is null); clears *nz (when not null) for k_nonzero
 __global__ void k_axpby_init(const double* __restrict__ y0, double c0, long long K,
-                             double* __restrict__ v) {
+                             double* __restrict__ v, unsigned* __restrict__ nz) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < K) v[k] = y0 ? c0 * y0[k] : 0.0;
+  if (nz && k == 0) *nz = 0u;
+}
+
+// *nz = 1 if any x[r] != 0 (r < N); x2 (when not null) receives the (hi, lo)
+// FP32 split of x
+__global__ void k_nonzero(const double* __restrict__ x, long long N, float2* __restrict__ x2,
+                          unsigned* __restrict__ nz) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double xv = r < N ? x[r] : 0.0;
+  if (x2 && r < N) x2[r] = split_f64(xv);
+  if (__any_sync(0xffffffffu, xv != 0.0) && (threadIdx.x & 31) == 0) atomicOr(nz, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -1372,16 +1387,16 @@ void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, 
 
 void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
                             long long N, long long K, const double* x, const float2* x2, double c1,
-                            long long rows_per_split, double* v, bool panel) {
+                            long long rows_per_split, double* v, bool panel, const unsigned* nz) {
   if (f64)
     k_recompute_dense<double, false><<<grid, 256, 0, st>>>(static_cast<const double*>(A), lda, N, K,
-                                                            x, x2, c1, rows_per_split, v);
+                                                            x, x2, c1, rows_per_split, v, nz);
   else if (panel)
     k_recompute_dense<float, true><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K, x,
-                                                          x2, c1, rows_per_split, v);
+                                                          x2, c1, rows_per_split, v, nz);
   else
     k_recompute_dense<float, false><<<grid, 256, 0, st>>>(static_cast<const float*>(A), lda, N, K,
-                                                           x, x2, c1, rows_per_split, v);
+                                                           x, x2, c1, rows_per_split, v, nz);
 }
 
 // Repack a row-major N x K FP32 matrix (leading dimension lda, 16-byte aligned

@@ -38,13 +38,15 @@ void launch_update_dense(bool f64, unsigned grid, size_t smem, cudaStream_t st, 
                          bool panel);
 void launch_recompute_dense(bool f64, dim3 grid, cudaStream_t st, const void* A, long long lda,
                             long long N, long long K, const double* x, const float2* x2, double c1,
-                            long long rows_per_split, double* v, bool panel);
+                            long long rows_per_split, double* v, bool panel,
+                            const unsigned* nz = nullptr);
 __global__ void k_pack_panels(const float* A, long long N, long long K, long long lda, float* Pn);
 int set_solve_smem_limit(int bytes);
 
 __global__ void k_solve(const double* R, const double* pvec, SolveArgs sa, unsigned* err);
 
-__global__ void k_axpby_init(const double* y0, double c0, long long K, double* v);
+__global__ void k_axpby_init(const double* y0, double c0, long long K, double* v, unsigned* nz);
+__global__ void k_nonzero(const double* x, long long N, float2* x2, unsigned* nz);
 __global__ void k_split(const double* v, long long K, long long Kpad, float2* v2);
 
 __global__ void k_scatter_csr(const long long* rowptr, const int* col, const float* val,

@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_persist(PersistArgs a, unsigne
     };
     // NS - 1 stages in flight: a slot is refilled once its MMA has read the
     // tiles converted in place, one stage after it was consumed
-    for (int t = 0; t < NS - 1; ++t) {
+    constexpr int LAG = 1;  // a slot is refilled one stage after its consumption
+    for (int t = 0; t < NS - LAG; ++t) {
       if (t < S_tot) issue(t, t);
       cp_async_commit();
     }
@@ -329,6 +330,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_persist(PersistArgs a, unsigne
     }
     long long gs = 0;        // stages consumed so far (= Gram stages until the final update)
     bool prev_gram = false;  // the previous stage's slot holds tiles the MMA reads
+    bool prev_gram2 = false;  // ... the stage before it
     auto load_delta = [&](const double* dl, int psb) {
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_persist(PersistArgs a, unsigne
       constexpr int KIND = decltype(kind)::value;
       constexpr bool GRAM = KIND <= 3, REGA = KIND <= 1, UPD = KIND == 1 || KIND == 2 || KIND == 4;
       constexpr int UOFF = KIND == 1 ? 2 * C::kTile : C::kTile;  // rows of the update
-      cp_async_wait<NS - 2>();  // this thread's copies of stage gs have landed
+      cp_async_wait<NS - LAG - 1>();  // this thread's copies of stage gs have landed
       const int st = (int)(gs % NS);
       unsigned char* big = raw + st * C::kRaw;
       if constexpr (UPD) {
@@ -419,12 +421,14 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_persist(PersistArgs a, unsigne
         if (lane == 0) mbar_arrive(&full[st]);
       }
       // refill the slot of stage gs - 1 (consumed; its tiles read by the MMA)
-      if (gs + NS - 1 < S_tot) {
-        const int ps = (int)((gs + NS - 1) % NS);
-        if (gs >= 1 && prev_gram) warp_wait(&empty[ps], (uint32_t)(((gs - 1) / NS) & 1));
-        issue(gs + NS - 1, ps);
+      if (gs + NS - LAG < S_tot) {
+        const int ps = (int)((gs + NS - LAG) % NS);
+        const bool was_gram = LAG == 1 ? prev_gram : prev_gram2;
+        if (gs >= LAG && was_gram) warp_wait(&empty[ps], (uint32_t)(((gs - LAG) / NS) & 1));
+        issue(gs + NS - LAG, ps);
       }
       cp_async_commit();
+      prev_gram2 = prev_gram;
       prev_gram = GRAM;
       float vh[4], vl[4];
       if constexpr (UPD) {
