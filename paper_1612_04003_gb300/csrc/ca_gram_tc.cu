@@ -359,7 +359,10 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
         auto handoff = [&]() {
           if constexpr (THREE) {
             const int ms = (int)(gt % MS);
-            if (gt >= (uint32_t)MS) ok = warp_wait(&empty[ms], (uint32_t)((gt / MS - 1) & 1), ok);
+            // every lane polls the slot's barrier itself (cheaper than one
+            // lane waiting and the warp converging on it)
+            if (gt >= (uint32_t)MS && ok)
+              ok = mbar_wait_bounded(&empty[ms], (uint32_t)((gt / MS - 1) & 1), err);
             unsigned char* hi = mring + ms * C::kMmaSlotBytes;
 #pragma unroll
             for (int i = 0; i < RPT; ++i) {

