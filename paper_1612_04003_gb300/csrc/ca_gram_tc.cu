@@ -193,9 +193,9 @@ k_gram_tc(const float* __restrict__ A, long long lda, long long N, long long K,
     const uint32_t raw0 = smem_u32(raw);
     const uint32_t vring0 = smem_u32(vring);
     bool ok = true;
-    // one lane waits on the barrier, the warp follows (a wait by every lane
-    // would serialise 32 accesses to the same shared-memory word); once a
-    // wait has timed out no further waits are made
+    // one lane waits on the barrier, the warp follows; once a wait has timed
+    // out no further waits are made (the per-stage slot wait polls on every
+    // lane instead, which measured cheaper than the convergence)
     auto warp_wait = [&](uint64_t* bar, uint32_t parity, bool ok_in) -> bool {
       bool r = ok_in;
       if (lane == 0 && r) r = mbar_wait_bounded(bar, parity, err);

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_persist(PersistArgs a, unsigne
 
   if (tid == 0) {
     for (int s2 = 0; s2 < NS; ++s2) {
-      mbar_init(&full[s2], kLW);
+      mbar_init(&full[s2], kLT);  // one arrival per loader thread
       mbar_init(&empty[s2], 1);
     }
     mbar_init(done, 1);
@@ -417,8 +417,7 @@ __global__ void __launch_bounds__(kThreadsP, 1) k_persist(PersistArgs a, unsigne
           }
         }
         fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[st]);
+        mbar_arrive(&full[st]);  // every loader thread arrives (count 256)
       }
       // refill the slot of stage gs - 1 (consumed; its tiles read by the MMA)
       if (gs + NS - LAG < S_tot) {
