@@ -844,6 +844,12 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     const size_t sbp = (size_t)(sbm + 31) / 32 * 32;
     need += 3 * align256(sbp * sbp * 8) + 3 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
     if (o->check_every > 0) need += align256((size_t)check_rows(o, n, d) * 8) + 512;
+    // the dense-sparse split of the Gram (s*b >= 32): column counts, the
+    // dense map, and Xd (nrows x fd FP32, 64 MB at most)
+    constexpr int kSplitMinSB = 32;  // below it the pair kernel is as fast
+    const bool split = sbm >= kSplitMinSB && sbm <= 4096;
+    const int fdmax = (int)std::min<long long>(CA_CSR_DENSE_MAX, (64LL << 20) / (4 * std::max(1LL, n)));
+    if (split) need += 2 * align256((size_t)d * 4) + align256((size_t)n * fdmax * 4) + 512;
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
     bool st;
@@ -886,6 +892,39 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     recompute();
     k_sample<<<(unsigned)((o->H + 7) / 8), 256, 0, ctx->stream>>>(o->seed, o->h0, o->H, o->b, n, idx);
     CA_TRY_CUDA(cudaGetLastError());
+    // heavy features (in at least a quarter of the rows; the heaviest fdmax
+    // at most) become the columns of Xd, chosen on the host from the counts
+    int fd = 0;
+    int* dmap = nullptr;
+    float* Xd = nullptr;
+    if (split) {
+      int* cnt = cv.take<int>((size_t)d);
+      dmap = cv.take<int>((size_t)d);
+      CA_TRY_CUDA(cudaMemsetAsync(cnt, 0, (size_t)d * 4, ctx->stream));
+      launch_csr_prepare(ctx->stream, ctx->num_sms, cdev, n, d, nnz, cnt, nullptr, 0, nullptr, false);
+      std::vector<int> hc((size_t)d);
+      CA_TRY_CUDA(cudaMemcpyAsync(hc.data(), cnt, (size_t)d * 4, cudaMemcpyDeviceToHost, ctx->stream));
+      CA_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+      const long long heavy = (n + 3) / 4;
+      std::vector<int> cand;
+      for (long long f = 0; f < d; ++f)
+        if (hc[(size_t)f] >= heavy) cand.push_back((int)f);
+      if ((int)cand.size() > fdmax) {
+        std::stable_sort(cand.begin(), cand.end(), [&](int x, int y2) { return hc[x] > hc[y2]; });
+        cand.resize((size_t)fdmax);
+        std::sort(cand.begin(), cand.end());
+      }
+      std::vector<int> hm((size_t)d, -1);
+      for (size_t j = 0; j < cand.size(); ++j) hm[(size_t)cand[j]] = (int)j;
+      fd = (int)cand.size();
+      CA_TRY_CUDA(cudaMemcpy(dmap, hm.data(), (size_t)d * 4, cudaMemcpyHostToDevice));
+      Xd = cv.take<float>((size_t)n * std::max(fd, 1));
+      if (fd > 0) {
+        CA_TRY_CUDA(cudaMemsetAsync(Xd, 0, (size_t)n * fd * 4, ctx->stream));
+        launch_csr_prepare(ctx->stream, ctx->num_sms, cdev, n, d, nnz, nullptr, dmap, fd, Xd, true);
+      }
+      ctx->prof.kernel_launches += fd > 0 ? 2 : 1;
+    }
     const int b = o->b, s = o->s;
     const long long n_outer = (o->H + s - 1) / s;
     ctx->info = ca_info{o->H, 0, 0.0, 0.0, 0.0, 0.0, -1.0};
@@ -900,8 +939,12 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       const int* ik = idx + (size_t)s * k * b;
       // a2+a3: the Gram (row hash tables) and the projections
       prof_mark(ctx, PC_GRAM);
-      launch_csr_gram(ctx->stream, ctx->num_sms, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1,
-                      ctx->d_err);
+      if (split && sb >= kSplitMinSB)
+        launch_csr_gram_split(ctx->stream, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1, dmap, Xd, fd,
+                              ctx->d_err);
+      else
+        launch_csr_gram(ctx->stream, ctx->num_sms, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1,
+                        ctx->d_err);
       prof_mark(ctx, PC_GRAM);
       ctx->prof.kernel_launches += 1;
       // a4: the Gram goes through the dense path's reduction as its one

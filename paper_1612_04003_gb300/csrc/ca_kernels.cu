@@ -1056,6 +1056,208 @@ k_csr_gram(const long long* __restrict__ rowptr, const int* __restrict__ col,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Sparse Gram by a dense-sparse split of the features (steps a2+a3 of Alg. 4
+// on the CSR of X^T).  A feature present in a large share of the samples
+// makes almost every sampled pair nonzero: its contribution to G = Y Y^T is
+// a dense rank-one term, cheaper to form as part of a small dense Gram than
+// pair by pair.  Once per solve the heavy features get a column of the dense
+// n x fd matrix Xd (k_colcount, host choice, k_dense_fill); every outer step
+// k_dgram forms the Gram of the sampled rows of Xd (exact products summed
+// in double-float) and writes the strict lower triangle of G, then k_sgram
+// adds the products of the remaining features: each CTA takes a range of
+// features, gathers the sampled rows' entries in it (a binary search per row
+// in its sorted columns), buckets them by feature in shared memory and adds
+// the exact product of every pair of entries of a feature to G with FP64
+// atomics.  Together with k_csr_rows (diagonal, projections) this is the
+// same G as the pair kernels form, up to the order of FP64 additions.
+// ---------------------------------------------------------------------------
+// cnt[f] += 1 for every stored entry of column f (cnt zero on entry)
+__global__ void __launch_bounds__(256)
+k_colcount(const int* __restrict__ col, long long nnz, long long ncols, int* __restrict__ cnt) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int f = col[e];
+    if (f >= 0 && f < ncols) atomicAdd(cnt + f, 1);
+  }
+}
+
+// Xd[r][dmap[f]] = X^T[r][f] for the mapped (heavy) features (Xd zero on entry)
+__global__ void __launch_bounds__(256)
+k_dense_fill(const long long* __restrict__ rowptr, const int* __restrict__ col,
+             const float* __restrict__ val, long long nrows, long long ncols,
+             const int* __restrict__ dmap, int fd, float* __restrict__ Xd) {
+  const int lane = threadIdx.x & 31;
+  const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nrows) return;
+  for (long long e = rowptr[r] + lane; e < rowptr[r + 1]; e += 32) {
+    const int f = col[e];
+    const int j = (f >= 0 && f < ncols) ? dmap[f] : -1;
+    if (j >= 0) Xd[r * fd + j] = val[e];
+  }
+}
+
+constexpr int kDgT = 16;  // G tile of k_dgram: 16 x 16 entries, one per thread
+constexpr int kCsrDenseMax = CA_CSR_DENSE_MAX;  // dense features at most
+
+// G[q][p] (q < p, transposed: at G[q * ldr + p]) = x_{I_p}^T x_{I_q} over the
+// dense features: exact products summed in double-float.  One CTA per 16 x 16
+// tile of the lower triangle (tile pairs qb <= pb); fd = 0 writes zeros.
+__global__ void __launch_bounds__(256)
+k_dgram(const float* __restrict__ Xd, int fd, const int* __restrict__ idx, int sb,
+        long long nrows, int ldr, double* __restrict__ G) {
+  extern __shared__ float dg_smem[];  // [2 kDgT][fd + 1]: rows p, then rows q
+  pdl_wait();  // the previous use of G
+  pdl_trigger();
+  int pb, qb;
+  tri_decode(blockIdx.x, pb, qb);
+  const int ld = fd + 1;
+  for (int s = threadIdx.x >> 5; s < 2 * kDgT; s += 8) {  // a warp per row
+    const int r = s < kDgT ? pb * kDgT + s : qb * kDgT + s - kDgT;
+    const int i = r < sb ? idx[r] : -1;
+    const bool ok = i >= 0 && i < nrows;
+    for (int f = threadIdx.x & 31; f < fd; f += 32)
+      dg_smem[s * ld + f] = ok ? Xd[(long long)i * fd + f] : 0.f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / kDgT, tx = threadIdx.x % kDgT;
+  const int p = pb * kDgT + ty, q = qb * kDgT + tx;
+  if (p < sb && q < p) {
+    const float* yp = dg_smem + ty * ld;
+    const float* yq = dg_smem + (kDgT + tx) * ld;
+    float hi = 0.f, lo = 0.f;
+    for (int f = 0; f < fd; ++f) df_dot_acc(yp[f], yq[f], 0.f, hi, lo);
+    G[(long long)q * ldr + p] = (double)hi + (double)lo;
+  }
+}
+
+constexpr int kSgFR = 512;    // features per CTA of k_sgram
+constexpr int kSgCap = 4096;  // entries per pass (a range with more is split)
+constexpr int kSgSmem = 3 * (kSgFR + 1) * 4 + kSgCap * (4 + 4 + 2) + kSgCap * (4 + 4) + 64;
+
+// G[q][p] (q < p) += products of the sampled rows' entries in the features
+// dmap[f] < 0, FP64 atomics (G holds the dense part on entry).
+__global__ void __launch_bounds__(256)
+k_sgram(const long long* __restrict__ rowptr, const int* __restrict__ col,
+        const float* __restrict__ val, const int* __restrict__ idx, long long nrows,
+        long long ncols, int sb, const int* __restrict__ dmap, int ldr, double* __restrict__ G) {
+  extern __shared__ int sg_smem[];
+  int* cntf = sg_smem;                   // [kSgFR + 1] entries per feature
+  int* off = cntf + (kSgFR + 1);         // [kSgFR + 1] their start (then a fill cursor)
+  int* pc = off + (kSgFR + 1);           // [kSgFR + 1] pairs before feature f
+  int* er = pc + (kSgFR + 1);            // [kSgCap] gathered: row slot
+  float* ev = reinterpret_cast<float*>(er + kSgCap);       // value
+  short* ef = reinterpret_cast<short*>(ev + kSgCap);       // feature within the range
+  int* sr = reinterpret_cast<int*>(ef + kSgCap);           // bucketed: row slot
+  float* sv = reinterpret_cast<float*>(sr + kSgCap);       // value
+  int* scal = reinterpret_cast<int*>(sv + kSgCap);         // [0] entries gathered
+  pdl_wait();  // G written by k_dgram
+  pdl_trigger();
+  const int tid = threadIdx.x;
+  const long long f0 = (long long)blockIdx.x * kSgFR;
+  const long long f1 = f0 + kSgFR < ncols ? f0 + kSgFR : ncols;
+  long long fa = f0;
+  while (fa < f1) {
+    long long fb = f1;
+    for (;;) {  // gather [fa, fb); halve the range while it holds too many entries
+      for (int k = tid; k <= kSgFR; k += 256) cntf[k] = 0;
+      if (tid == 0) scal[0] = 0;
+      __syncthreads();
+      for (int r = tid; r < sb; r += 256) {
+        const int i = idx[r];
+        if (i < 0 || i >= nrows) continue;
+        long long lo = rowptr[i], hi = rowptr[i + 1];
+        const long long end = hi;
+        while (lo < hi) {  // first entry with column >= fa
+          const long long mid = (lo + hi) >> 1;
+          if (col[mid] < fa) lo = mid + 1; else hi = mid;
+        }
+        for (long long e = lo; e < end; ++e) {
+          const int f = col[e];
+          if (f >= fb) break;
+          if (dmap[f] >= 0) continue;
+          const int pos = atomicAdd(scal, 1);
+          if (pos < kSgCap) {
+            er[pos] = r;
+            ev[pos] = val[e];
+            ef[pos] = (short)(f - fa);
+            atomicAdd(cntf + (f - fa), 1);
+          }
+        }
+      }
+      __syncthreads();
+      if (scal[0] <= kSgCap || fb - fa <= 1) break;  // (one feature holds <= sb <= kSgCap)
+      fb = fa + (fb - fa) / 2;
+      __syncthreads();
+    }
+    const int ne = scal[0] < kSgCap ? scal[0] : kSgCap;
+    const int nf = (int)(fb - fa);
+    {  // offsets and pair counts: exclusive scans over the nf <= 512 features,
+       // two per thread, then across the warps
+      const int fa2 = 2 * tid, fb2 = 2 * tid + 1;
+      const int c0 = fa2 < nf ? cntf[fa2] : 0, c1 = fb2 < nf ? cntf[fb2] : 0;
+      int so = c0 + c1, sq = c0 * (c0 - 1) / 2 + c1 * (c1 - 1) / 2;
+      const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {  // inclusive warp scans
+        const int xo = __shfl_up_sync(0xffffffffu, so, o), xq = __shfl_up_sync(0xffffffffu, sq, o);
+        if (lane >= o) {
+          so += xo;
+          sq += xq;
+        }
+      }
+      __shared__ int wtot[2][8];
+      if (lane == 31) {
+        wtot[0][warp] = so;
+        wtot[1][warp] = sq;
+      }
+      __syncthreads();
+      int bo = 0, bq = 0;
+      for (int w2 = 0; w2 < warp; ++w2) {
+        bo += wtot[0][w2];
+        bq += wtot[1][w2];
+      }
+      const int eo = bo + so - (c0 + c1), eq = bq + sq - (c0 * (c0 - 1) / 2 + c1 * (c1 - 1) / 2);
+      if (fa2 < nf) {
+        off[fa2] = eo;
+        pc[fa2] = eq;
+      }
+      if (fb2 < nf) {
+        off[fb2] = eo + c0;
+        pc[fb2] = eq + c0 * (c0 - 1) / 2;
+      }
+      if (tid == 255) {
+        off[nf] = bo + so;
+        pc[nf] = bq + sq;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < ne; e += 256) {  // bucket by feature
+      const int f = ef[e];
+      const int pos = off[f] + atomicAdd(cntf + f, -1) - 1;
+      sr[pos] = er[e];
+      sv[pos] = ev[e];
+    }
+    __syncthreads();
+    const int np = pc[nf];
+    for (int t = tid; t < np; t += 256) {
+      int lo = 0, hi = nf;  // feature f: pc[f] <= t < pc[f + 1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pc[mid] <= t) lo = mid; else hi = mid;
+      }
+      int a, b2;
+      tri_decode(t - pc[lo], a, b2);  // b2 <= a over side c - 1: the pair (b2, a + 1)
+      const int base = off[lo];
+      const int r1 = sr[base + b2], r2 = sr[base + a + 1];
+      const int p = r1 > r2 ? r1 : r2, q = r1 > r2 ? r2 : r1;
+      atomicAdd(G + (long long)q * ldr + p, (double)sv[base + b2] * (double)sv[base + a + 1]);
+    }
+    __syncthreads();
+    fa = fb;
+  }
+}
+
 // v[col] += c * val * coef[r] for the listed rows (a5 for CSR with coef =
 // Delta alpha, c = -1/(lambda n); a6 with all rows, coef = alpha).
 __global__ void __launch_bounds__(256)
@@ -1490,6 +1692,33 @@ void launch_csr_gram(cudaStream_t st, int num_sms, const ca_csr_dev& csr, const 
                       csr.val, idx, nrows, ncols, sb, ldr, qc, w, G, pvec, err);
 }
 
+void launch_csr_prepare(cudaStream_t st, int num_sms, const ca_csr_dev& csr, long long nrows,
+                        long long ncols, long long nnz, int* cnt, const int* dmap, int fd,
+                        float* Xd, bool fill) {
+  if (!fill) {
+    const long long blocks = std::max(1LL, std::min<long long>((nnz + 255) / 256, 8LL * num_sms));
+    k_colcount<<<(unsigned)blocks, 256, 0, st>>>(csr.col, nnz, ncols, cnt);
+    return;
+  }
+  if (fd > 0)
+    k_dense_fill<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(csr.rowptr, csr.col, csr.val, nrows,
+                                                                ncols, dmap, fd, Xd);
+}
+
+void launch_csr_gram_split(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                           long long ncols, int sb, int ldr, const double* w, double* G,
+                           double* pvec, const int* dmap, const float* Xd, int fd,
+                           unsigned* err) {
+  launch_programmatic(k_csr_rows, (unsigned)((sb + 7) / 8), 0, st, csr.rowptr, csr.col, csr.val,
+                      idx, nrows, ncols, sb, ldr, w, G, pvec, err);
+  if (sb <= 1) return;
+  const int nb = (sb + kDgT - 1) / kDgT;
+  launch_programmatic(k_dgram, (unsigned)(nb * (nb + 1) / 2), (size_t)2 * kDgT * (fd + 1) * 4, st,
+                      Xd, fd, idx, sb, nrows, ldr, G);
+  launch_programmatic(k_sgram, (unsigned)((ncols + kSgFR - 1) / kSgFR), (size_t)kSgSmem, st,
+                      csr.rowptr, csr.col, csr.val, idx, nrows, ncols, sb, dmap, ldr, G);
+}
+
 int launch_reduce_chain_f64(int grid, size_t smem, cudaStream_t st, const double* part,
                             const double* ppart, int sbp, double* R, float2* Rs, double* pvec,
                             float2* Ginv, int ndiag, const SolveArgs& sa, unsigned* err,
@@ -1507,7 +1736,9 @@ int launch_reduce_chain_f64(int grid, size_t smem, cudaStream_t st, const double
 }
 
 int set_solve_smem_limit(int bytes) {
-  cudaError_t e[13] = {set_dyn_smem(k_solve, bytes), set_dyn_smem(k_csr_gram, kCsrSmem),
+  cudaError_t e[15] = {set_dyn_smem(k_solve, bytes), set_dyn_smem(k_csr_gram, kCsrSmem),
+                      set_dyn_smem(k_sgram, kSgSmem),
+                      set_dyn_smem(k_dgram, 2 * kDgT * (kCsrDenseMax + 1) * 4),
                       set_dyn_smem(k_chain<8, 4>, bytes),
                       set_dyn_smem(k_chain<16, 3>, bytes),
                       set_dyn_smem(k_chain<32, 2>, bytes),
