@@ -847,6 +847,11 @@ def main():
     barrier(world)
     ms_ps = time_solves(ctx, XP, y, w, z, args.steps, stream, s=s_run, h=h_run, panels=pan)
     barrier(world)
+    # ... and its Gram pass alone (events around each launch, two solves)
+    ctx.ca_profile_enable(True)
+    time_solves(ctx, XP, y, w, z, 2, stream, s=s_run, h=h_run, panels=pan)
+    prof_ps = ctx.ca_profile_read()
+    ctx.ca_profile_enable(False)
     ctx.ca_set_tuning(persistent=True)
     # second timed pass (roofline, breakdown): the same K solves with CUDA
     # events around every launch, on the library's stream
@@ -905,6 +910,18 @@ def main():
                         "timed pass of the same K solves (ms_per_step of that pass: %.3f)"
                         % (ms_prof / args.steps)}
     roof["breakdown"] = breakdown
+    # the per-step path's Gram pass (one fused launch per outer step): the
+    # roofline of that kernel alone, HBM idle between its launches
+    g_ps = prof_ps["gram_ms"] / max(1, prof_ps["gram_launches"])
+    per_launch_ps = solve_bytes / max(1.0, prof_ps["gram_launches"] / 2)
+    ach_ps = per_launch_ps / (g_ps * 1e-3) / 1e9
+    trec_ps = _traffic_record(os.path.join(ROOT, "paper_1612_04003_gb300", "csrc", "ca_gram_tc.cu"))
+    roof_gram_pass = {"bound": "hbm", "achieved": ach_ps, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                      "frac": ach_ps / peaks["hbm_gbs"], "avg_launch_ms": g_ps,
+                      "algorithmic_bytes_per_launch": per_launch_ps,
+                      "traffic": trec_ps["traffic_bytes_per_launch"] if trec_ps else None,
+                      "kernel": f"k_gram_tc<128,{PREC},fused update> (launches per step)",
+                      "share_of_step": prof_ps["gram_ms"] / max(1e-9, 2 * ms_ps / args.steps)}
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     Xh = torch.empty((D, n_run), dtype=torch.float32, pin_memory=True)
@@ -1003,6 +1020,7 @@ def main():
             "batch": batch, "serve": serve5, "precision_study": prec_study,
             "input_layout": "X resident on the device in the library's 32-column panel layout "
                             "(ca_pack_panels once before the timed region, CA_DENSE_F32_PANELS)",
+            "roofline_gram_pass_launches_per_step": roof_gram_pass,
             "value_launches_per_step": {
                 "value": world * h_run / (max_over_ranks(ms_ps / args.steps, world) * 1e-3),
                 "ms_per_step": max_over_ranks(ms_ps / args.steps, world),

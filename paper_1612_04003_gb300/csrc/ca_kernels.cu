@@ -1125,9 +1125,18 @@ k_dgram(const float* __restrict__ Xd, int fd, const int* __restrict__ idx, int s
   if (p < sb && q < p) {
     const float* yp = dg_smem + ty * ld;
     const float* yq = dg_smem + (kDgT + tx) * ld;
-    float hi = 0.f, lo = 0.f;
-    for (int f = 0; f < fd; ++f) df_dot_acc(yp[f], yq[f], 0.f, hi, lo);
-    G[(long long)q * ldr + p] = (double)hi + (double)lo;
+    // four independent double-float sums (features f = u mod 4): four
+    // dependency chains in flight instead of one
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    int f = 0;
+    for (; f + 4 <= fd; f += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) df_dot_acc(yp[f + u], yq[f + u], 0.f, hi[u], lo[u]);
+    }
+    for (; f < fd; ++f) df_dot_acc(yp[f], yq[f], 0.f, hi[0], lo[0]);
+    const float2 s2 = df_add(df_add(df_norm(hi[0], lo[0]), df_norm(hi[1], lo[1])),
+                             df_add(df_norm(hi[2], lo[2]), df_norm(hi[3], lo[3])));
+    G[(long long)q * ldr + p] = (double)s2.x + (double)s2.y;
   }
 }
 
