@@ -668,6 +668,12 @@ void ca_bcd_destroy(ca_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  for (cudaEvent_t e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -842,7 +848,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     // leading dimension of R / Rs: a multiple of 32 (the chain copies 16-byte
     // row pairs of the transposed Rs)
     const size_t sbp = (size_t)(sbm + 31) / 32 * 32;
-    need += 3 * align256(sbp * sbp * 8) + 3 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
+    need += 4 * align256(sbp * sbp * 8) + 3 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
     if (o->check_every > 0) need += align256((size_t)check_rows(o, n, d) * 8) + 512;
     // the dense-sparse split of the Gram (s*b >= 32): column counts, the
     // dense map, and Xd (nrows x fd FP32, 64 MB at most)
@@ -865,7 +871,10 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* delta = cv.take<double>(sbp);
     float2* Ginv = cv.take<float2>(sbp * CA_FAST_B);
     float2* Rs = cv.take<float2>(sbp * sbp);
-    double* Gt = cv.take<double>(sbp * sbp);  // the Gram (transposed lower triangle)
+    // the Gram (transposed lower triangle), two buffers: the off-diagonal
+    // part of step k+1 is formed on the side stream while step k's solves
+    // read the other
+    double* Gbuf[2] = {cv.take<double>(sbp * sbp), cv.take<double>(sbp * sbp)};
     double* pp1 = cv.take<double>(sbp);       // its projections
     CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
     double* rq = nullptr;
@@ -933,20 +942,65 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       CA_TRY(residual(&ctx->info.res0, 0));
       ctx->info.res = ctx->info.res0;
     }
+    // s*b <= 4096: the strict lower triangle of each step's Gram (the split,
+    // or one warp per pair) has no input that the solves change, so it runs
+    // on the side stream one step ahead; events: ev[0] the start and the
+    // join, ev[1 + k%2] buffer k%2 formed, ev[3 + k%2] buffer k%2 read
+    const bool two = sbm <= 4096;
+    if (two && !ctx->side) {
+      for (cudaEvent_t& e : ctx->ev)
+        if (!e) CA_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      CA_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    }
+    struct SideJoin {  // every exit: the main stream waits for the side stream's work
+      ca_ctx* c;
+      bool on;
+      void operator()() {
+        if (!on) return;
+        on = false;
+        cudaEventRecord(c->ev[0], c->side);
+        cudaStreamWaitEvent(c->stream, c->ev[0], 0);
+      }
+      ~SideJoin() { (*this)(); }
+    } join{ctx, false};
+    auto offdiag = [&](long long kk) {
+      const int sbk = (int)std::min<long long>(s, o->H - (long long)s * kk) * b;
+      const bool sp = split && sbk >= kSplitMinSB;
+      launch_csr_offdiag(ctx->side, cdev, idx + (size_t)s * kk * b, n, d, sbk, (int)sbp,
+                         Gbuf[kk & 1], dmap, Xd, fd, sp);
+      ctx->prof.kernel_launches += sbk <= 1 ? 0 : (sp ? 2 : 1);
+    };
+    if (two && n_outer > 0) {
+      CA_TRY_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
+      CA_TRY_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev[0], 0));
+      join.on = true;
+      offdiag(0);
+      CA_TRY_CUDA(cudaEventRecord(ctx->ev[1], ctx->side));
+    }
     for (long long k = 0; k < n_outer; ++k) {
       const int sk = (int)std::min<long long>(s, o->H - (long long)s * k);
       const int sb = sk * b;
       const int* ik = idx + (size_t)s * k * b;
+      double* Gt = Gbuf[k & 1];
       // a2+a3: the Gram (row hash tables) and the projections
       prof_mark(ctx, PC_GRAM);
-      if (split && sb >= kSplitMinSB)
-        launch_csr_gram_split(ctx->stream, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1, dmap, Xd, fd,
-                              ctx->d_err);
-      else
+      if (two) {
+        launch_csr_rows(ctx->stream, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1, ctx->d_err);
+        ctx->prof.kernel_launches += 1;
+      } else {
         launch_csr_gram(ctx->stream, ctx->num_sms, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1,
                         ctx->d_err);
+        ctx->prof.kernel_launches += sb > 1 ? 2 : 1;
+      }
       prof_mark(ctx, PC_GRAM);
-      ctx->prof.kernel_launches += 1;
+      if (two) {
+        if (k + 1 < n_outer) {  // buffer (k+1)%2 was last read by the solves of step k-1
+          if (k >= 1) CA_TRY_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev[3 + ((k + 1) & 1)], 0));
+          offdiag(k + 1);
+          CA_TRY_CUDA(cudaEventRecord(ctx->ev[1 + ((k + 1) & 1)], ctx->side));
+        }
+        CA_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev[1 + (k & 1)], 0));
+      }
       // a4: the Gram goes through the dense path's reduction as its one
       // FP64 partial: reduce + diagonal inverses + chain in one launch
       // (b <= 16), else the general form
@@ -970,6 +1024,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
         g.P = 1;
         CA_TRY(launch_reduce_solve(ctx, g, Gt, pp1, R, Rs, pvec, Ginv, sa, f64solve));
       }
+      if (two) CA_TRY_CUDA(cudaEventRecord(ctx->ev[3 + (k & 1)], ctx->stream));
       // a5: w -= Y Delta/(lambda n)
       launch_scatter_csr(ctx->stream, cdev, ik, n, d, sb, delta, -1.0 / ln, wd, ctx->d_err);
       ctx->prof.kernel_launches += 1;
@@ -984,6 +1039,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
         }
       }
     }
+    join();
     if (a_host)
       CA_TRY_CUDA(cudaMemcpyAsync(alpha, ad, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (w_host) CA_TRY_CUDA(cudaMemcpyAsync(w, wd, (size_t)d * 8, cudaMemcpyDeviceToHost, ctx->stream));

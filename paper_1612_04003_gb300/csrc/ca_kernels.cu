@@ -1714,13 +1714,23 @@ void launch_csr_prepare(cudaStream_t st, int num_sms, const ca_csr_dev& csr, lon
                                                                 ncols, dmap, fd, Xd);
 }
 
-void launch_csr_gram_split(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
-                           long long ncols, int sb, int ldr, const double* w, double* G,
-                           double* pvec, const int* dmap, const float* Xd, int fd,
-                           unsigned* err) {
+void launch_csr_rows(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                     long long ncols, int sb, int ldr, const double* w, double* G, double* pvec,
+                     unsigned* err) {
   launch_programmatic(k_csr_rows, (unsigned)((sb + 7) / 8), 0, st, csr.rowptr, csr.col, csr.val,
                       idx, nrows, ncols, sb, ldr, w, G, pvec, err);
+}
+
+void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                        long long ncols, int sb, int ldr, double* G, const int* dmap,
+                        const float* Xd, int fd, bool split) {
   if (sb <= 1) return;
+  if (!split) {
+    const long long npairs = (long long)sb * (sb - 1) / 2;
+    launch_programmatic(k_csr_gram_pairs, (unsigned)std::max(1LL, (npairs + 7) / 8), 0, st,
+                        csr.rowptr, csr.col, csr.val, idx, nrows, sb, ldr, G);
+    return;
+  }
   const int nb = (sb + kDgT - 1) / kDgT;
   launch_programmatic(k_dgram, (unsigned)(nb * (nb + 1) / 2), (size_t)2 * kDgT * (fd + 1) * 4, st,
                       Xd, fd, idx, sb, nrows, ldr, G);

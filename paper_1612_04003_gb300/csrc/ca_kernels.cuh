@@ -173,18 +173,23 @@ struct ca_csr_dev;
 // at least a quarter of the rows, CA_CSR_DENSE_MAX at most) get a column of
 // the dense nrows x fd matrix Xd.  launch_csr_prepare: fill = false counts
 // each column's entries into cnt (zero on entry); fill = true scatters the
-// mapped entries into Xd (zero on entry).  launch_csr_gram_split: the
-// diagonal and projections (k_csr_rows), the Gram of the sampled rows of Xd
-// (k_dgram, writes the strict lower triangle) and the remaining features'
-// pair products (k_sgram, FP64 atomics); sb <= 4096.
+// mapped entries into Xd (zero on entry).  The split Gram of a step: the
+// Gram of the sampled rows of Xd (k_dgram, writes the strict lower
+// triangle), then the remaining features' pair products (k_sgram, FP64
+// atomics); sb <= 4096.
 #define CA_CSR_DENSE_MAX 512
 void launch_csr_prepare(cudaStream_t st, int num_sms, const ca_csr_dev& csr, long long nrows,
                         long long ncols, long long nnz, int* cnt, const int* dmap, int fd,
                         float* Xd, bool fill);
-void launch_csr_gram_split(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
-                           long long ncols, int sb, int ldr, const double* w, double* G,
-                           double* pvec, const int* dmap, const float* Xd, int fd,
-                           unsigned* err);
+// The diagonal and projections of the sampled rows (k_csr_rows), and the
+// strict lower triangle of their Gram: the split (k_dgram + k_sgram) or,
+// split = false, one warp per pair (k_csr_gram_pairs, sb <= 128).
+void launch_csr_rows(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                     long long ncols, int sb, int ldr, const double* w, double* G, double* pvec,
+                     unsigned* err);
+void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                        long long ncols, int sb, int ldr, double* G, const int* dmap,
+                        const float* Xd, int fd, bool split);
 void launch_csr_gram(cudaStream_t st, int num_sms, const ca_csr_dev& csr, const int* idx,
                      long long nrows, long long ncols, int sb, int ldr, const double* w, double* G,
                      double* pvec, unsigned* err);
