@@ -848,7 +848,8 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     // leading dimension of R / Rs: a multiple of 32 (the chain copies 16-byte
     // row pairs of the transposed Rs)
     const size_t sbp = (size_t)(sbm + 31) / 32 * 32;
-    need += 4 * align256(sbp * sbp * 8) + 3 * align256(sbp * 8) + align256(sbp * CA_FAST_B * 8) + 4096;
+    need += 5 * align256(sbp * sbp * 8) + 3 * align256(sbp * 8) + 2 * align256(sbp * CA_FAST_B * 8) +
+            4096;
     if (o->check_every > 0) need += align256((size_t)check_rows(o, n, d) * 8) + 512;
     // the dense-sparse split of the Gram (s*b >= 32): column counts, the
     // dense map, and Xd (nrows x fd FP32, 64 MB at most)
@@ -871,10 +872,12 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* delta = cv.take<double>(sbp);
     float2* Ginv = cv.take<float2>(sbp * CA_FAST_B);
     float2* Rs = cv.take<float2>(sbp * sbp);
-    // the Gram (transposed lower triangle), two buffers: the off-diagonal
-    // part of step k+1 is formed on the side stream while step k's solves
-    // read the other
+    // the Gram (transposed lower triangle), Rs and the diagonal-block
+    // inverses, two buffers each: what step k+1 needs of them is formed on
+    // the side stream while step k's solves read the other
     double* Gbuf[2] = {cv.take<double>(sbp * sbp), cv.take<double>(sbp * sbp)};
+    float2* RsB[2] = {Rs, cv.take<float2>(sbp * sbp)};
+    float2* GinvB[2] = {Ginv, cv.take<float2>(sbp * CA_FAST_B)};
     double* pp1 = cv.take<double>(sbp);       // its projections
     CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
     double* rq = nullptr;
@@ -963,12 +966,28 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       }
       ~SideJoin() { (*this)(); }
     } join{ctx, false};
+    // the fast a4 (b <= 16): the diagonal blocks' inverses and Rs come from
+    // the side stream too, and the library stream runs the projections, the
+    // chain and the scatter
+    const bool f64solve = o->solve == CA_SOLVE_F64;
+    auto fast_step = [&](int sbk) { return two && fast_solve(b, sbk, f64solve) && b <= 16; };
+    auto step_args = [&](long long kk) {
+      const int skk = (int)std::min<long long>(s, o->H - (long long)s * kk);
+      return SolveArgs{idx + (size_t)s * kk * b, n, b, skk, skk * b, (int)sbp, 1.0 / ln, 1.0, 1.0,
+                       1.0, ad, yd, delta};
+    };
     auto offdiag = [&](long long kk) {
-      const int sbk = (int)std::min<long long>(s, o->H - (long long)s * kk) * b;
+      const SolveArgs sk_args = step_args(kk);
+      const int sbk = sk_args.sb;
       const bool sp = split && sbk >= kSplitMinSB;
-      launch_csr_offdiag(ctx->side, cdev, idx + (size_t)s * kk * b, n, d, sbk, (int)sbp,
-                         Gbuf[kk & 1], dmap, Xd, fd, sp);
+      launch_csr_offdiag(ctx->side, cdev, sk_args.idx, n, d, sbk, (int)sbp, Gbuf[kk & 1], dmap, Xd,
+                         fd, sp);
       ctx->prof.kernel_launches += sbk <= 1 ? 0 : (sp ? 2 : 1);
+      if (fast_step(sbk)) {
+        launch_csr_prep(ctx->side, ctx->num_sms, cdev, n, Gbuf[kk & 1], sk_args, RsB[kk & 1],
+                        GinvB[kk & 1], ctx->d_err);
+        ctx->prof.kernel_launches += 1;
+      }
     };
     if (two && n_outer > 0) {
       CA_TRY_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
@@ -983,8 +1002,12 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       const int* ik = idx + (size_t)s * k * b;
       double* Gt = Gbuf[k & 1];
       // a2+a3: the Gram (row hash tables) and the projections
+      const bool fk = fast_step(sb);
       prof_mark(ctx, PC_GRAM);
-      if (two) {
+      if (fk) {
+        launch_csr_proj(ctx->stream, cdev, ik, n, d, sb, wd, pp1, ctx->d_err);
+        ctx->prof.kernel_launches += 1;
+      } else if (two) {
         launch_csr_rows(ctx->stream, cdev, ik, n, d, sb, (int)sbp, wd, Gt, pp1, ctx->d_err);
         ctx->prof.kernel_launches += 1;
       } else {
@@ -1001,19 +1024,25 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
         }
         CA_TRY_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev[1 + (k & 1)], 0));
       }
-      // a4: the Gram goes through the dense path's reduction as its one
-      // FP64 partial: reduce + diagonal inverses + chain in one launch
-      // (b <= 16), else the general form
-      SolveArgs sa{ik, n, b, sk, sb, (int)sbp, 1.0 / ln, 1.0, 1.0, 1.0, ad, yd, delta};
-      const bool f64solve = o->solve == CA_SOLVE_F64;
-      if (fast_solve(b, sb, f64solve) && b <= 16) {
+      // a4: with b <= 16 the chain alone (its other inputs are ready), or
+      // the Gram through the dense path's reduction as its one FP64
+      // partial: reduce + diagonal inverses + chain in one launch, else the
+      // general form
+      const SolveArgs sa = step_args(k);
+      if (fk) {
+        prof_mark(ctx, PC_SOLVE);
+        launch_chain(b, chain_smem(b, sb), ctx->stream, RsB[k & 1], pp1, GinvB[k & 1], sa,
+                     ctx->d_err);
+        prof_mark(ctx, PC_SOLVE);
+        ctx->prof.kernel_launches += 1;
+      } else if (fast_solve(b, sb, f64solve) && b <= 16) {
         const long long entries = (long long)sb * (sb + 1) / 2 + sb;
         const int grid = (int)std::max<long long>(
                              1, std::min<long long>((entries + 63) / 64 + sk, ctx->num_sms - 1)) + 1;
         prof_mark(ctx, PC_SOLVE);
         const int e = launch_reduce_chain_f64(grid, chain_smem(b, sb), ctx->stream, Gt, pp1,
-                                              (int)sbp, R, Rs, pvec, Ginv, sk, sa, ctx->d_err,
-                                              ctx->d_ticket);
+                                              (int)sbp, R, RsB[k & 1], pvec, GinvB[k & 1], sk, sa,
+                                              ctx->d_err, ctx->d_ticket);
         prof_mark(ctx, PC_SOLVE);
         ctx->prof.kernel_launches += 1;
         if (e != 0) return cuda_fail((cudaError_t)e, __LINE__);
@@ -1022,7 +1051,10 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
         g.tc = false;
         g.sbp = (int)sbp;
         g.P = 1;
-        CA_TRY(launch_reduce_solve(ctx, g, Gt, pp1, R, Rs, pvec, Ginv, sa, f64solve));
+        // (Rs and Ginv of this step's parity: the side stream may be
+        // writing the other pair for the next step)
+        CA_TRY(launch_reduce_solve(ctx, g, Gt, pp1, R, RsB[k & 1], pvec, GinvB[k & 1], sa,
+                                   f64solve));
       }
       if (two) CA_TRY_CUDA(cudaEventRecord(ctx->ev[3 + (k & 1)], ctx->stream));
       // a5: w -= Y Delta/(lambda n)

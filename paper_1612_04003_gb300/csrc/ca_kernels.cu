@@ -514,6 +514,7 @@ __global__ void __launch_bounds__(256)
 k_chain(const float2* __restrict__ Rs, const double* __restrict__ pvec,
         const float2* __restrict__ Ginv, SolveArgs a, unsigned* __restrict__ err) {
   extern __shared__ double smem_d[];
+  pdl_wait();  // (as a programmatic dependent: p from the launch before it)
   if constexpr (BMAX <= 16)
     chain_la_body<BMAX, DEPTH>(Rs, pvec, Ginv, a, err, smem_d);
   else
@@ -867,6 +868,122 @@ k_csr_rows(const long long* __restrict__ rowptr, const int* __restrict__ col,
   }
 }
 
+// Projections x_{I_p}^T w of the sampled rows alone (the part of a2+a3 that
+// needs the current w), one CTA per row: thread t takes entries t, t + 256,
+// ... of the row, four in flight, then a CTA sum (FP64 products and sums).
+__global__ void __launch_bounds__(256)
+k_csr_proj(const long long* __restrict__ rowptr, const int* __restrict__ col,
+           const float* __restrict__ val, const int* __restrict__ idx, long long nrows,
+           long long ncols, const double* __restrict__ w, double* __restrict__ pvec,
+           unsigned* __restrict__ err) {
+  __shared__ double red[8];
+  pdl_wait();  // w (the previous step's update)
+  pdl_trigger();
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const int ir = idx[r];
+  double sp = 0.0;
+  if (ir >= 0 && ir < nrows) {
+    const long long e1 = rowptr[ir + 1];
+    for (long long eb = rowptr[ir] + tid; eb < e1; eb += 4 * 256) {
+      int fs[4];
+      float vs[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long e = eb + 256 * u;
+        fs[u] = e < e1 ? col[e] : -1;
+        vs[u] = e < e1 ? val[e] : 0.f;
+      }
+      double ws[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = fs[u] >= 0 && fs[u] < ncols;
+        if (!in && eb + 256 * u < e1) ca_flag(err, CA_DEV_ERR_ARG);
+        ws[u] = in ? w[fs[u]] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sp = fma((double)vs[u], ws[u], sp);
+    }
+  } else if (tid == 0) {
+    ca_flag(err, CA_DEV_ERR_ARG);
+  }
+  for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+  if ((tid & 31) == 0) red[tid >> 5] = sp;
+  __syncthreads();
+  if (tid == 0)
+    pvec[r] = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+}
+
+// The part of a4's input that depends on neither w nor alpha (so it can be
+// formed while the previous outer step still runs): CTAs 0 .. s'-1 take the
+// diagonal block j: the sums of squares of its b sampled rows (exact
+// products, FP64 sums), the strict lower part from G, Gamma_j = cG G_jj +
+// cI I in double-float and its inverse (cta_sweep_inverse) into Ginv[j];
+// the other CTAs write Rs = cG G (FP32 pairs) over the strict lower
+// triangle, in G's transposed layout (entry (i, c), i > c, at c * ldr + i),
+// which is the layout the chain reads.  b <= 16.
+__global__ void __launch_bounds__(256)
+k_csr_prep(const long long* __restrict__ rowptr, const float* __restrict__ val,
+           const int* __restrict__ idx, long long nrows, const double* __restrict__ G,
+           SolveArgs sa, float2* __restrict__ Rs, float2* __restrict__ Ginv,
+           unsigned* __restrict__ err) {
+  __shared__ double dsum[16];
+  __shared__ float2 Mb[256];
+  __shared__ float2 colbuf[66];
+  pdl_wait();  // G's strict lower triangle (the Gram kernels before this one)
+  pdl_trigger();
+  const int b = sa.b, sb = sa.sb, ldr = sa.ldr;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float2 cG2 = split_f64(sa.cG), cI2 = split_f64(sa.cI);
+  if ((int)blockIdx.x < sa.s_cur) {
+    const int jb = (int)blockIdx.x * b;
+    for (int q = warp; q < b; q += 8) {  // a warp per row
+      const int ir = idx[jb + q];
+      double sd = 0.0;
+      if (ir >= 0 && ir < nrows) {
+        const long long e1 = rowptr[ir + 1];
+        for (long long eb = rowptr[ir] + lane; eb < e1; eb += 8 * 32) {
+          float vs[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) vs[u] = eb + 32 * u < e1 ? val[eb + 32 * u] : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sd = fma((double)vs[u], (double)vs[u], sd);
+        }
+      } else if (lane == 0) {
+        ca_flag(err, CA_DEV_ERR_ARG);
+      }
+      for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+      if (lane == 0) dsum[q] = sd;
+    }
+    __syncthreads();
+    if (tid < b * b) {
+      const int i = tid / b, c = tid - (tid / b) * b;
+      const double v = i == c ? dsum[i]
+                              : G[(long long)(jb + (i < c ? i : c)) * ldr + jb + (i < c ? c : i)];
+      float2 m = df_mul(cG2, split_f64(v));
+      if (i == c) m = df_add(m, cI2);
+      Mb[tid] = m;
+    }
+    __syncthreads();
+    float2* out = Ginv + (long long)blockIdx.x * b * b;
+    if (b <= 8) {
+      if (tid < 64) {
+        float2 a[1] = {tid < b * b ? Mb[tid] : make_float2(0.f, 0.f)};
+        cta_sweep_inverse<1, 64>(a, b, colbuf, out, err);
+      }
+    } else {
+      float2 a[1] = {tid < b * b ? Mb[tid] : make_float2(0.f, 0.f)};
+      cta_sweep_inverse<1>(a, b, colbuf, out, err);
+    }
+    return;
+  }
+  const long long ne = (long long)sb * sb;
+  const long long stride = (long long)(gridDim.x - sa.s_cur) * 256;
+  for (long long e = (long long)(blockIdx.x - sa.s_cur) * 256 + tid; e < ne; e += stride) {
+    const int c = (int)(e / sb), i = (int)(e - (long long)c * sb);
+    if (i > c) Rs[(long long)c * ldr + i] = df_mul(cG2, split_f64(G[(long long)c * ldr + i]));
+  }
+}
+
 // The off-diagonal Gram entries of few sampled rows (s*b <= 64) by sorted-list
 // intersection, one warp per pair q < p: lanes walk the shorter row and
 // binary-search the longer, products exact in FP64.
@@ -1112,13 +1229,22 @@ k_dgram(const float* __restrict__ Xd, int fd, const int* __restrict__ idx, int s
   int pb, qb;
   tri_decode(blockIdx.x, pb, qb);
   const int ld = fd + 1;
+  // the 2 kDgT rows into shared memory: every 4-byte copy in flight at once
+  // (cp.async), rows outside the sample zero
+  const uint32_t sm0 = smem_u32(dg_smem);
   for (int s = threadIdx.x >> 5; s < 2 * kDgT; s += 8) {  // a warp per row
     const int r = s < kDgT ? pb * kDgT + s : qb * kDgT + s - kDgT;
     const int i = r < sb ? idx[r] : -1;
-    const bool ok = i >= 0 && i < nrows;
-    for (int f = threadIdx.x & 31; f < fd; f += 32)
-      dg_smem[s * ld + f] = ok ? Xd[(long long)i * fd + f] : 0.f;
+    if (i >= 0 && i < nrows) {
+      const float* src = Xd + (long long)i * fd;
+      for (int f = threadIdx.x & 31; f < fd; f += 32)
+        cp_async_4(sm0 + 4u * (uint32_t)(s * ld + f), src + f);
+    } else {
+      for (int f = threadIdx.x & 31; f < fd; f += 32) dg_smem[s * ld + f] = 0.f;
+    }
   }
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
   const int ty = threadIdx.x / kDgT, tx = threadIdx.x % kDgT;
   const int p = pb * kDgT + ty, q = qb * kDgT + tx;
@@ -1303,6 +1429,41 @@ k_scatter_csr(const long long* __restrict__ rowptr, const int* __restrict__ col,
   }
 }
 
+// a5 for the sampled rows of the sparse dual: v[col] += c * val * coef[r],
+// one CTA per listed row (entries t, t + 256, ... of the row, four in
+// flight; FP64 atomics).
+__global__ void __launch_bounds__(256)
+k_scatter_csr_rows(const long long* __restrict__ rowptr, const int* __restrict__ col,
+                   const float* __restrict__ val, const int* __restrict__ idx,
+                   long long nrows_total, long long ncols, const double* __restrict__ coef,
+                   double c, double* __restrict__ v, unsigned* __restrict__ err) {
+  pdl_wait();  // coef (the solve's Delta)
+  pdl_trigger();
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const long long row = idx[r];
+  if (row < 0 || row >= nrows_total) {
+    if (tid == 0) ca_flag(err, CA_DEV_ERR_ARG);
+    return;
+  }
+  const double cr = c * coef[r];
+  const long long e1 = rowptr[row + 1];
+  for (long long eb = rowptr[row] + tid; eb < e1; eb += 4 * 256) {
+    int fs[4];
+    float vs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long e = eb + 256 * u;
+      fs[u] = e < e1 ? col[e] : -1;
+      vs[u] = e < e1 ? val[e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (fs[u] >= 0 && fs[u] < ncols) atomicAdd(v + fs[u], (double)vs[u] * cr);
+      else if (eb + 256 * u < e1) ca_flag(err, CA_DEV_ERR_ARG);
+    }
+  }
+}
+
 // Self-test of the bounded waits: thread 0 waits on an mbarrier that nothing
 // arrives on; the wait gives up after limit_ns and flags CA_DEV_ERR_TIMEOUT.
 __global__ void k_selftest_wait(unsigned long long limit_ns, unsigned* __restrict__ err) {
@@ -1349,14 +1510,17 @@ void launch_reduce(bool f32_partials, int grid, size_t smem, cudaStream_t st, co
                                                Rs, pvec, Ginv, ndiag, sa, err);
 }
 
+template <typename K, typename... Args>
+cudaError_t launch_programmatic(K kernel, unsigned grid, size_t smem, cudaStream_t st, Args... args);
+
 void launch_chain(int b, size_t smem, cudaStream_t st, const float2* Rs, const double* pvec,
                   const float2* Ginv, const SolveArgs& sa, unsigned* err) {
   if (b <= 8)
-    k_chain<8, 4><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
+    launch_programmatic(k_chain<8, 4>, 1u, smem, st, Rs, pvec, Ginv, sa, err);
   else if (b <= 16)
-    k_chain<16, 3><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
+    launch_programmatic(k_chain<16, 3>, 1u, smem, st, Rs, pvec, Ginv, sa, err);
   else
-    k_chain<32, 2><<<1, 256, smem, st>>>(Rs, pvec, Ginv, sa, err);
+    launch_programmatic(k_chain<32, 2>, 1u, smem, st, Rs, pvec, Ginv, sa, err);
 }
 
 template <typename K, typename... Args>
@@ -1673,8 +1837,25 @@ int launch_chain_batch(int count, int bmax, size_t smem, cudaStream_t st, const 
 void launch_scatter_csr(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
                         long long ncols, long long nlist, const double* coef, double c, double* v,
                         unsigned* err) {
-  launch_programmatic(k_scatter_csr, (unsigned)((nlist + 7) / 8), 0, st, csr.rowptr, csr.col,
-                      csr.val, idx, nrows, ncols, nlist, coef, c, v, err);
+  if (nlist <= 0) return;
+  launch_programmatic(k_scatter_csr_rows, (unsigned)nlist, 0, st, csr.rowptr, csr.col, csr.val,
+                      idx, nrows, ncols, coef, c, v, err);
+}
+
+void launch_csr_proj(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                     long long ncols, int sb, const double* w, double* pvec, unsigned* err) {
+  if (sb <= 0) return;
+  launch_programmatic(k_csr_proj, (unsigned)sb, 0, st, csr.rowptr, csr.col, csr.val, idx, nrows,
+                      ncols, w, pvec, err);
+}
+
+void launch_csr_prep(cudaStream_t st, int num_sms, const ca_csr_dev& csr, long long nrows,
+                     const double* G, const SolveArgs& sa, float2* Rs, float2* Ginv,
+                     unsigned* err) {
+  const long long conv = std::max(1LL, std::min<long long>(((long long)sa.sb * sa.sb + 255) / 256,
+                                                           (long long)num_sms - 1));
+  launch_programmatic(k_csr_prep, (unsigned)(sa.s_cur + conv), 0, st, csr.rowptr, csr.val, sa.idx,
+                      nrows, G, sa, Rs, Ginv, err);
 }
 
 void launch_csr_gram(cudaStream_t st, int num_sms, const ca_csr_dev& csr, const int* idx,

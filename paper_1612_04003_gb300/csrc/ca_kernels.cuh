@@ -190,6 +190,16 @@ void launch_csr_rows(cudaStream_t st, const ca_csr_dev& csr, const int* idx, lon
 void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
                         long long ncols, int sb, int ldr, double* G, const int* dmap,
                         const float* Xd, int fd, bool split);
+// The fast a4 of the sparse dual (b <= 16) in two parts: launch_csr_prep
+// (needs neither w nor alpha: diagonal-block inverses into Ginv and the
+// cG-scaled FP32 pairs Rs of G's strict lower triangle; the diagonal from the
+// CSR rows) and launch_csr_proj (the projections x_{I_p}^T w into pvec), both
+// for the sa.sb sampled rows sa.idx; then the chain (launch_chain).
+void launch_csr_prep(cudaStream_t st, int num_sms, const ca_csr_dev& csr, long long nrows,
+                     const double* G, const SolveArgs& sa, float2* Rs, float2* Ginv,
+                     unsigned* err);
+void launch_csr_proj(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
+                     long long ncols, int sb, const double* w, double* pvec, unsigned* err);
 void launch_csr_gram(cudaStream_t st, int num_sms, const ca_csr_dev& csr, const int* idx,
                      long long nrows, long long ncols, int sb, int ldr, const double* w, double* G,
                      double* pvec, unsigned* err);
