@@ -966,11 +966,15 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       }
       ~SideJoin() { (*this)(); }
     } join{ctx, false};
-    // the fast a4 (b <= 16): the diagonal blocks' inverses and Rs come from
-    // the side stream too, and the library stream runs the projections, the
-    // chain and the scatter
+    // the fast a4 (b <= 16) with s*b >= 128: the diagonal blocks' inverses
+    // and Rs come from the side stream too, and the library stream runs the
+    // projections, the chain and the scatter (below 128 rows the extra
+    // launch on the side stream costs more than the reduction it moves)
+    constexpr int kPrepMinSB = 128;
     const bool f64solve = o->solve == CA_SOLVE_F64;
-    auto fast_step = [&](int sbk) { return two && fast_solve(b, sbk, f64solve) && b <= 16; };
+    auto fast_step = [&](int sbk) {
+      return two && fast_solve(b, sbk, f64solve) && b <= 16 && sbk >= kPrepMinSB;
+    };
     auto step_args = [&](long long kk) {
       const int skk = (int)std::min<long long>(s, o->H - (long long)s * kk);
       return SolveArgs{idx + (size_t)s * kk * b, n, b, skk, skk * b, (int)sbp, 1.0 / ln, 1.0, 1.0,

@@ -77,3 +77,22 @@ def test_split_gram_dual_csr(ctx, case, b, s):
     a_ref, w_ref = oracle.ca_bdcd(A, y, lam, b=b, s=s, H=H, seed=5)
     print(f"{case} b={b} s={s}: a {_rel(a, a_ref):.2e} w {_rel(w, w_ref):.2e}")
     assert _rel(a, a_ref) < TOL64 and _rel(w, w_ref) < TOL64
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_split_gram_dual_csr_short_last_step(ctx, case):
+    """s*b = 128 for the first outer steps (the inverses and Rs formed on the
+    second stream) and 40 for the short last one (the fused reduction on the
+    library stream), with the Gram buffers and Rs alternating by step parity
+    across the switch."""
+    n, d, dens = CASES[case]
+    rowptr, col, val, y = _csr(n, d, dens(d), seed=len(case) + 3)
+    lam, b, s, H = 1e-3, 8, 16, 5 * 16 + 5
+    a = torch.zeros(n, dtype=torch.float64, device="cuda")
+    w = torch.zeros(d, dtype=torch.float64, device="cuda")
+    ctx.ca_bdcd_solve((_dev(rowptr), _dev(col), _dev(val)), _dev(y), a, w, b=b, s=s, H=H,
+                      lam=lam, seed=9, d=d)
+    A = oracle.CSR(rowptr, col, val.astype(np.float64), d)
+    a_ref, w_ref = oracle.ca_bdcd(A, y, lam, b=b, s=s, H=H, seed=9)
+    print(f"{case} short last step: a {_rel(a, a_ref):.2e} w {_rel(w, w_ref):.2e}")
+    assert _rel(a, a_ref) < TOL64 and _rel(w, w_ref) < TOL64
