@@ -296,8 +296,11 @@ def secondary_workloads(ctx, stream):
         run()
         t = _device_time(stream, run, 3)
         out.append({"workload": "sparse dual CA-BDCD, CSR of X^T 16384 x 131072 (0.5%, Pareto "
-                                "nnz per feature), lambda 1e-5, b=8, H=2048, CUDA-core Gram (one warp "
-                                "per row pair for s*b <= 128, tiles of row hash tables above)",
+                                "nnz per feature), lambda 1e-5, b=8, H=2048, CUDA-core FP64 Gram "
+                                "(s*b < 32: one warp per row pair; s*b >= 32: dense part of the "
+                                "features in at least a quarter of the samples + bucketed pair "
+                                "products of the rest), next step's w-independent part on a "
+                                "second stream",
                     "nnz": int(sp.rowptr[-1]), "s": s_, "ms_per_solve": t,
                     "block_updates_per_s": h_sp / (t * 1e-3),
                     "us_per_outer_step": t * 1e3 / -(-h_sp // s_)})

@@ -855,8 +855,11 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     // dense map, and Xd (nrows x fd FP32, 64 MB at most)
     constexpr int kSplitMinSB = 32;  // below it the pair kernel is as fast
     const bool split = sbm >= kSplitMinSB && sbm <= 4096;
-    const int fdmax = (int)std::min<long long>(CA_CSR_DENSE_MAX, (64LL << 20) / (4 * std::max(1LL, n)));
-    if (split) need += 2 * align256((size_t)d * 4) + align256((size_t)n * fdmax * 4) + 512;
+    // (a multiple of 8: Xd's rows are zero-padded to 16-byte multiples)
+    const int fdmax = (int)std::min<long long>(
+        CA_CSR_DENSE_MAX, ((64LL << 20) / (4 * std::max(1LL, n))) & ~7LL);
+    if (split) need += 2 * align256((size_t)d * 4) + align256((size_t)n * std::max(fdmax, 8) * 4) + 512;
+    need += align256((size_t)n * 8);  // row norms
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
     bool st;
@@ -878,6 +881,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
     double* Gbuf[2] = {cv.take<double>(sbp * sbp), cv.take<double>(sbp * sbp)};
     float2* RsB[2] = {Rs, cv.take<float2>(sbp * sbp)};
     float2* GinvB[2] = {Ginv, cv.take<float2>(sbp * CA_FAST_B)};
+    double* rn = cv.take<double>((size_t)n);  // row norms (the Grams' diagonals)
     double* pp1 = cv.take<double>(sbp);       // its projections
     CA_TRY_CUDA(cudaMemsetAsync(ctx->d_err, 0, 33 * sizeof(unsigned), ctx->stream));
     double* rq = nullptr;
@@ -928,9 +932,9 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       }
       std::vector<int> hm((size_t)d, -1);
       for (size_t j = 0; j < cand.size(); ++j) hm[(size_t)cand[j]] = (int)j;
-      fd = (int)cand.size();
+      fd = ((int)cand.size() + 7) & ~7;  // row length of Xd; the padding stays zero
       CA_TRY_CUDA(cudaMemcpy(dmap, hm.data(), (size_t)d * 4, cudaMemcpyHostToDevice));
-      Xd = cv.take<float>((size_t)n * std::max(fd, 1));
+      Xd = cv.take<float>((size_t)n * std::max(fd, 8));
       if (fd > 0) {
         CA_TRY_CUDA(cudaMemsetAsync(Xd, 0, (size_t)n * fd * 4, ctx->stream));
         launch_csr_prepare(ctx->stream, ctx->num_sms, cdev, n, d, nnz, nullptr, dmap, fd, Xd, true);
@@ -988,11 +992,15 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
                          fd, sp);
       ctx->prof.kernel_launches += sbk <= 1 ? 0 : (sp ? 2 : 1);
       if (fast_step(sbk)) {
-        launch_csr_prep(ctx->side, ctx->num_sms, cdev, n, Gbuf[kk & 1], sk_args, RsB[kk & 1],
+        launch_csr_prep(ctx->side, ctx->num_sms, rn, n, Gbuf[kk & 1], sk_args, RsB[kk & 1],
                         GinvB[kk & 1], ctx->d_err);
         ctx->prof.kernel_launches += 1;
       }
     };
+    if (fast_step(sbm)) {  // before the side stream starts
+      launch_csr_rownorm(ctx->stream, cdev, n, rn);
+      ctx->prof.kernel_launches += 1;
+    }
     if (two && n_outer > 0) {
       CA_TRY_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
       CA_TRY_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev[0], 0));

@@ -913,19 +913,39 @@ k_csr_proj(const long long* __restrict__ rowptr, const int* __restrict__ col,
     pvec[r] = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
 }
 
+// rn[r] = x_r^T x_r for every row of the CSR (exact products, FP64 sums),
+// one warp per row: the diagonal of every Gram, formed once per solve.
+__global__ void __launch_bounds__(256)
+k_csr_rownorm(const long long* __restrict__ rowptr, const float* __restrict__ val,
+              long long nrows, double* __restrict__ rn) {
+  const int lane = threadIdx.x & 31;
+  const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nrows) return;
+  const long long e1 = rowptr[r + 1];
+  double sd = 0.0;
+  for (long long eb = rowptr[r] + lane; eb < e1; eb += 8 * 32) {
+    float vs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) vs[u] = eb + 32 * u < e1 ? val[eb + 32 * u] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sd = fma((double)vs[u], (double)vs[u], sd);
+  }
+  for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  if (lane == 0) rn[r] = sd;
+}
+
 // The part of a4's input that depends on neither w nor alpha (so it can be
 // formed while the previous outer step still runs): CTAs 0 .. s'-1 take the
-// diagonal block j: the sums of squares of its b sampled rows (exact
-// products, FP64 sums), the strict lower part from G, Gamma_j = cG G_jj +
-// cI I in double-float and its inverse (cta_sweep_inverse) into Ginv[j];
+// diagonal block j: the diagonal from the row norms rn (k_csr_rownorm), the
+// strict lower part from G, Gamma_j = cG G_jj + cI I in double-float and its
+// inverse (cta_sweep_inverse) into Ginv[j];
 // the other CTAs write Rs = cG G (FP32 pairs) over the strict lower
 // triangle, in G's transposed layout (entry (i, c), i > c, at c * ldr + i),
 // which is the layout the chain reads.  b <= 16.
 __global__ void __launch_bounds__(256)
-k_csr_prep(const long long* __restrict__ rowptr, const float* __restrict__ val,
-           const int* __restrict__ idx, long long nrows, const double* __restrict__ G,
-           SolveArgs sa, float2* __restrict__ Rs, float2* __restrict__ Ginv,
-           unsigned* __restrict__ err) {
+k_csr_prep(const double* __restrict__ rn, const int* __restrict__ idx, long long nrows,
+           const double* __restrict__ G, SolveArgs sa, float2* __restrict__ Rs,
+           float2* __restrict__ Ginv, unsigned* __restrict__ err) {
   __shared__ double dsum[16];
   __shared__ float2 Mb[256];
   __shared__ float2 colbuf[66];
@@ -936,23 +956,11 @@ k_csr_prep(const long long* __restrict__ rowptr, const float* __restrict__ val,
   const float2 cG2 = split_f64(sa.cG), cI2 = split_f64(sa.cI);
   if ((int)blockIdx.x < sa.s_cur) {
     const int jb = (int)blockIdx.x * b;
-    for (int q = warp; q < b; q += 8) {  // a warp per row
-      const int ir = idx[jb + q];
-      double sd = 0.0;
-      if (ir >= 0 && ir < nrows) {
-        const long long e1 = rowptr[ir + 1];
-        for (long long eb = rowptr[ir] + lane; eb < e1; eb += 8 * 32) {
-          float vs[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) vs[u] = eb + 32 * u < e1 ? val[eb + 32 * u] : 0.f;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) sd = fma((double)vs[u], (double)vs[u], sd);
-        }
-      } else if (lane == 0) {
-        ca_flag(err, CA_DEV_ERR_ARG);
-      }
-      for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
-      if (lane == 0) dsum[q] = sd;
+    if (tid < b) {
+      const int ir = idx[jb + tid];
+      const bool ok = ir >= 0 && ir < nrows;
+      if (!ok) ca_flag(err, CA_DEV_ERR_ARG);
+      dsum[tid] = ok ? rn[ir] : 0.0;
     }
     __syncthreads();
     if (tid < b * b) {
@@ -1219,17 +1227,21 @@ constexpr int kCsrDenseMax = CA_CSR_DENSE_MAX;  // dense features at most
 
 // G[q][p] (q < p, transposed: at G[q * ldr + p]) = x_{I_p}^T x_{I_q} over the
 // dense features: exact products summed in double-float.  One CTA per 16 x 16
-// tile of the lower triangle (tile pairs qb <= pb); fd = 0 writes zeros.
+// tile of the lower triangle (tile pairs qb <= pb); fd = 0 writes zeros.  fd
+// is a multiple of 8 (Xd's zero-padded row length, 16-byte rows).
 __global__ void __launch_bounds__(256)
 k_dgram(const float* __restrict__ Xd, int fd, const int* __restrict__ idx, int sb,
         long long nrows, int ldr, double* __restrict__ G) {
-  extern __shared__ float dg_smem[];  // [2 kDgT][fd + 1]: rows p, then rows q
+  extern __shared__ float4 dg_smem4[];  // [2 kDgT][(fd + 4) / 4]: rows p, then rows q
+  float* dg_smem = reinterpret_cast<float*>(dg_smem4);
   pdl_wait();  // the previous use of G
   pdl_trigger();
   int pb, qb;
   tri_decode(blockIdx.x, pb, qb);
-  const int ld = fd + 1;
-  // the 2 kDgT rows into shared memory: every 4-byte copy in flight at once
+  // row stride fd + 4 floats: 16-byte rows whose 16-byte loads by 8
+  // consecutive rows fall in distinct bank groups
+  const int ld = fd + 4, n4 = fd >> 2;
+  // the 2 kDgT rows into shared memory: every 16-byte copy in flight at once
   // (cp.async), rows outside the sample zero
   const uint32_t sm0 = smem_u32(dg_smem);
   for (int s = threadIdx.x >> 5; s < 2 * kDgT; s += 8) {  // a warp per row
@@ -1237,10 +1249,11 @@ k_dgram(const float* __restrict__ Xd, int fd, const int* __restrict__ idx, int s
     const int i = r < sb ? idx[r] : -1;
     if (i >= 0 && i < nrows) {
       const float* src = Xd + (long long)i * fd;
-      for (int f = threadIdx.x & 31; f < fd; f += 32)
-        cp_async_4(sm0 + 4u * (uint32_t)(s * ld + f), src + f);
+      for (int f4 = threadIdx.x & 31; f4 < n4; f4 += 32)
+        cp_async_16_zfill(sm0 + 4u * (uint32_t)(s * ld + 4 * f4), src + 4 * f4, 16u);
     } else {
-      for (int f = threadIdx.x & 31; f < fd; f += 32) dg_smem[s * ld + f] = 0.f;
+      for (int f4 = threadIdx.x & 31; f4 < n4; f4 += 32)
+        dg_smem4[(s * ld >> 2) + f4] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   cp_async_commit();
@@ -1249,17 +1262,18 @@ k_dgram(const float* __restrict__ Xd, int fd, const int* __restrict__ idx, int s
   const int ty = threadIdx.x / kDgT, tx = threadIdx.x % kDgT;
   const int p = pb * kDgT + ty, q = qb * kDgT + tx;
   if (p < sb && q < p) {
-    const float* yp = dg_smem + ty * ld;
-    const float* yq = dg_smem + (kDgT + tx) * ld;
+    const float4* yp = dg_smem4 + (ty * ld >> 2);
+    const float4* yq = dg_smem4 + ((kDgT + tx) * ld >> 2);
     // four independent double-float sums (features f = u mod 4): four
-    // dependency chains in flight instead of one
+    // dependency chains in flight instead of one; 16-byte loads
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    int f = 0;
-    for (; f + 4 <= fd; f += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) df_dot_acc(yp[f + u], yq[f + u], 0.f, hi[u], lo[u]);
+    for (int f4 = 0; f4 < n4; ++f4) {
+      const float4 x = yp[f4], y = yq[f4];
+      df_dot_acc(x.x, y.x, 0.f, hi[0], lo[0]);
+      df_dot_acc(x.y, y.y, 0.f, hi[1], lo[1]);
+      df_dot_acc(x.z, y.z, 0.f, hi[2], lo[2]);
+      df_dot_acc(x.w, y.w, 0.f, hi[3], lo[3]);
     }
-    for (; f < fd; ++f) df_dot_acc(yp[f], yq[f], 0.f, hi[0], lo[0]);
     const float2 s2 = df_add(df_add(df_norm(hi[0], lo[0]), df_norm(hi[1], lo[1])),
                              df_add(df_norm(hi[2], lo[2]), df_norm(hi[3], lo[3])));
     G[(long long)q * ldr + p] = (double)s2.x + (double)s2.y;
@@ -1849,13 +1863,18 @@ void launch_csr_proj(cudaStream_t st, const ca_csr_dev& csr, const int* idx, lon
                       ncols, w, pvec, err);
 }
 
-void launch_csr_prep(cudaStream_t st, int num_sms, const ca_csr_dev& csr, long long nrows,
+void launch_csr_rownorm(cudaStream_t st, const ca_csr_dev& csr, long long nrows, double* rn) {
+  if (nrows > 0)
+    k_csr_rownorm<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(csr.rowptr, csr.val, nrows, rn);
+}
+
+void launch_csr_prep(cudaStream_t st, int num_sms, const double* rn, long long nrows,
                      const double* G, const SolveArgs& sa, float2* Rs, float2* Ginv,
                      unsigned* err) {
   const long long conv = std::max(1LL, std::min<long long>(((long long)sa.sb * sa.sb + 255) / 256,
                                                            (long long)num_sms - 1));
-  launch_programmatic(k_csr_prep, (unsigned)(sa.s_cur + conv), 0, st, csr.rowptr, csr.val, sa.idx,
-                      nrows, G, sa, Rs, Ginv, err);
+  launch_programmatic(k_csr_prep, (unsigned)(sa.s_cur + conv), 0, st, rn, sa.idx, nrows, G, sa,
+                      Rs, Ginv, err);
 }
 
 void launch_csr_gram(cudaStream_t st, int num_sms, const ca_csr_dev& csr, const int* idx,
@@ -1913,7 +1932,7 @@ void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, 
     return;
   }
   const int nb = (sb + kDgT - 1) / kDgT;
-  launch_programmatic(k_dgram, (unsigned)(nb * (nb + 1) / 2), (size_t)2 * kDgT * (fd + 1) * 4, st,
+  launch_programmatic(k_dgram, (unsigned)(nb * (nb + 1) / 2), (size_t)2 * kDgT * (fd + 4) * 4, st,
                       Xd, fd, idx, sb, nrows, ldr, G);
   launch_programmatic(k_sgram, (unsigned)((ncols + kSgFR - 1) / kSgFR), (size_t)kSgSmem, st,
                       csr.rowptr, csr.col, csr.val, idx, nrows, ncols, sb, dmap, ldr, G);
@@ -1938,7 +1957,7 @@ int launch_reduce_chain_f64(int grid, size_t smem, cudaStream_t st, const double
 int set_solve_smem_limit(int bytes) {
   cudaError_t e[15] = {set_dyn_smem(k_solve, bytes), set_dyn_smem(k_csr_gram, kCsrSmem),
                       set_dyn_smem(k_sgram, kSgSmem),
-                      set_dyn_smem(k_dgram, 2 * kDgT * (kCsrDenseMax + 1) * 4),
+                      set_dyn_smem(k_dgram, 2 * kDgT * (kCsrDenseMax + 4) * 4),
                       set_dyn_smem(k_chain<8, 4>, bytes),
                       set_dyn_smem(k_chain<16, 3>, bytes),
                       set_dyn_smem(k_chain<32, 2>, bytes),

@@ -173,7 +173,9 @@ struct ca_csr_dev;
 // at least a quarter of the rows, CA_CSR_DENSE_MAX at most) get a column of
 // the dense nrows x fd matrix Xd.  launch_csr_prepare: fill = false counts
 // each column's entries into cnt (zero on entry); fill = true scatters the
-// mapped entries into Xd (zero on entry).  The split Gram of a step: the
+// mapped entries into Xd (zero on entry; fd, the row length of Xd, a
+// multiple of 8 with the columns past the mapped ones left zero).  The split
+// Gram of a step: the
 // Gram of the sampled rows of Xd (k_dgram, writes the strict lower
 // triangle), then the remaining features' pair products (k_sgram, FP64
 // atomics); sb <= 4096.
@@ -193,9 +195,11 @@ void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, 
 // The fast a4 of the sparse dual (b <= 16) in two parts: launch_csr_prep
 // (needs neither w nor alpha: diagonal-block inverses into Ginv and the
 // cG-scaled FP32 pairs Rs of G's strict lower triangle; the diagonal from the
-// CSR rows) and launch_csr_proj (the projections x_{I_p}^T w into pvec), both
-// for the sa.sb sampled rows sa.idx; then the chain (launch_chain).
-void launch_csr_prep(cudaStream_t st, int num_sms, const ca_csr_dev& csr, long long nrows,
+// row norms rn of launch_csr_rownorm, formed once per solve) and
+// launch_csr_proj (the projections x_{I_p}^T w into pvec), both for the sa.sb
+// sampled rows sa.idx; then the chain (launch_chain).
+void launch_csr_rownorm(cudaStream_t st, const ca_csr_dev& csr, long long nrows, double* rn);
+void launch_csr_prep(cudaStream_t st, int num_sms, const double* rn, long long nrows,
                      const double* G, const SolveArgs& sa, float2* Rs, float2* Ginv,
                      unsigned* err);
 void launch_csr_proj(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
