@@ -860,6 +860,10 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
         CA_CSR_DENSE_MAX, ((64LL << 20) / (4 * std::max(1LL, n))) & ~7LL);
     if (split) need += 2 * align256((size_t)d * 4) + align256((size_t)n * std::max(fdmax, 8) * 4) + 512;
     need += align256((size_t)n * 8);  // row norms
+    // where each feature range starts in every row (256 MB at most, else searched)
+    const size_t roff_bytes = csr_rangeoff_bytes(n, d);
+    const bool use_roff = split && roff_bytes <= ((size_t)256 << 20);
+    if (use_roff) need += align256(roff_bytes);
     CA_TRY(ensure_arena(ctx, need));
     Carve cv{static_cast<char*>(ctx->arena)};
     bool st;
@@ -941,6 +945,12 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       }
       ctx->prof.kernel_launches += fd > 0 ? 2 : 1;
     }
+    int* roff = nullptr;
+    if (use_roff) {
+      roff = cv.take<int>(roff_bytes / sizeof(int));
+      launch_csr_rangeoff(ctx->stream, cdev, n, d, roff);
+      ctx->prof.kernel_launches += 1;
+    }
     const int b = o->b, s = o->s;
     const long long n_outer = (o->H + s - 1) / s;
     ctx->info = ca_info{o->H, 0, 0.0, 0.0, 0.0, 0.0, -1.0};
@@ -989,7 +999,7 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       const int sbk = sk_args.sb;
       const bool sp = split && sbk >= kSplitMinSB;
       launch_csr_offdiag(ctx->side, cdev, sk_args.idx, n, d, sbk, (int)sbp, Gbuf[kk & 1], dmap, Xd,
-                         fd, sp);
+                         fd, sp, roff);
       ctx->prof.kernel_launches += sbk <= 1 ? 0 : (sp ? 2 : 1);
       if (fast_step(sbk)) {
         launch_csr_prep(ctx->side, ctx->num_sms, rn, n, Gbuf[kk & 1], sk_args, RsB[kk & 1],

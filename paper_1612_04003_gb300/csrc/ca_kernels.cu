@@ -1284,12 +1284,37 @@ constexpr int kSgFR = 512;    // features per CTA of k_sgram
 constexpr int kSgCap = 4096;  // entries per pass (a range with more is split)
 constexpr int kSgSmem = 3 * (kSgFR + 1) * 4 + kSgCap * (4 + 4 + 2) + kSgCap * (4 + 4) + 64;
 
+// roff[r (nr + 1) + c] = the offset within row r of its first entry with
+// column >= c kSgFR (the row's length when it has none), c = 0 .. nr: where
+// each feature range of k_sgram starts in every row, formed once per solve
+// so that k_sgram needs no search.  One warp per row.
+__global__ void __launch_bounds__(256)
+k_csr_rangeoff(const long long* __restrict__ rowptr, const int* __restrict__ col,
+               long long nrows, int nr, int* __restrict__ roff) {
+  const int lane = threadIdx.x & 31;
+  const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nrows) return;
+  const long long e0 = rowptr[r], e1 = rowptr[r + 1];
+  int* out = roff + r * (nr + 1);
+  auto range_of = [&](int f) { return f < 0 ? -1 : min(f / kSgFR, nr); };
+  for (long long e = e0 + lane; e < e1; e += 32) {
+    const int c = range_of(col[e]);
+    const int cp = e == e0 ? -1 : range_of(col[e - 1]);
+    for (int q = cp + 1; q <= c; ++q) out[q] = (int)(e - e0);
+  }
+  const int cl = e1 > e0 ? range_of(col[e1 - 1]) : -1;  // ranges after the last entry's
+  for (int q = cl + 1 + lane; q <= nr; q += 32) out[q] = (int)(e1 - e0);
+}
+
 // G[q][p] (q < p) += products of the sampled rows' entries in the features
-// dmap[f] < 0, FP64 atomics (G holds the dense part on entry).
+// dmap[f] < 0, FP64 atomics (G holds the dense part on entry).  roff (when
+// not null, nr + 1 offsets a row, k_csr_rangeoff) gives where the CTA's
+// range starts in each row; otherwise a binary search finds it.
 __global__ void __launch_bounds__(256)
 k_sgram(const long long* __restrict__ rowptr, const int* __restrict__ col,
         const float* __restrict__ val, const int* __restrict__ idx, long long nrows,
-        long long ncols, int sb, const int* __restrict__ dmap, int ldr, double* __restrict__ G) {
+        long long ncols, int sb, const int* __restrict__ dmap, int ldr, double* __restrict__ G,
+        const int* __restrict__ roff, int nr) {
   extern __shared__ int sg_smem[];
   int* cntf = sg_smem;                   // [kSgFR + 1] entries per feature
   int* off = cntf + (kSgFR + 1);         // [kSgFR + 1] their start (then a fill cursor)
@@ -1317,9 +1342,13 @@ k_sgram(const long long* __restrict__ rowptr, const int* __restrict__ col,
         if (i < 0 || i >= nrows) continue;
         long long lo = rowptr[i], hi = rowptr[i + 1];
         const long long end = hi;
-        while (lo < hi) {  // first entry with column >= fa
-          const long long mid = (lo + hi) >> 1;
-          if (col[mid] < fa) lo = mid + 1; else hi = mid;
+        if (roff && fa == f0) {
+          lo += roff[(long long)i * (nr + 1) + blockIdx.x];
+        } else {
+          while (lo < hi) {  // first entry with column >= fa
+            const long long mid = (lo + hi) >> 1;
+            if (col[mid] < fa) lo = mid + 1; else hi = mid;
+          }
         }
         for (long long e = lo; e < end; ++e) {
           const int f = col[e];
@@ -1921,9 +1950,20 @@ void launch_csr_rows(cudaStream_t st, const ca_csr_dev& csr, const int* idx, lon
                       idx, nrows, ncols, sb, ldr, w, G, pvec, err);
 }
 
+size_t csr_rangeoff_bytes(long long nrows, long long ncols) {
+  return (size_t)nrows * (size_t)((ncols + kSgFR - 1) / kSgFR + 1) * sizeof(int);
+}
+
+void launch_csr_rangeoff(cudaStream_t st, const ca_csr_dev& csr, long long nrows, long long ncols,
+                         int* roff) {
+  if (nrows > 0)
+    k_csr_rangeoff<<<(unsigned)((nrows + 7) / 8), 256, 0, st>>>(
+        csr.rowptr, csr.col, nrows, (int)((ncols + kSgFR - 1) / kSgFR), roff);
+}
+
 void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
                         long long ncols, int sb, int ldr, double* G, const int* dmap,
-                        const float* Xd, int fd, bool split) {
+                        const float* Xd, int fd, bool split, const int* roff) {
   if (sb <= 1) return;
   if (!split) {
     const long long npairs = (long long)sb * (sb - 1) / 2;
@@ -1934,8 +1974,9 @@ void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, 
   const int nb = (sb + kDgT - 1) / kDgT;
   launch_programmatic(k_dgram, (unsigned)(nb * (nb + 1) / 2), (size_t)2 * kDgT * (fd + 4) * 4, st,
                       Xd, fd, idx, sb, nrows, ldr, G);
-  launch_programmatic(k_sgram, (unsigned)((ncols + kSgFR - 1) / kSgFR), (size_t)kSgSmem, st,
-                      csr.rowptr, csr.col, csr.val, idx, nrows, ncols, sb, dmap, ldr, G);
+  const int nr = (int)((ncols + kSgFR - 1) / kSgFR);
+  launch_programmatic(k_sgram, (unsigned)nr, (size_t)kSgSmem, st, csr.rowptr, csr.col, csr.val,
+                      idx, nrows, ncols, sb, dmap, ldr, G, roff, nr);
 }
 
 int launch_reduce_chain_f64(int grid, size_t smem, cudaStream_t st, const double* part,

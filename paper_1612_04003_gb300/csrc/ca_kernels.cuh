@@ -191,7 +191,13 @@ void launch_csr_rows(cudaStream_t st, const ca_csr_dev& csr, const int* idx, lon
                      unsigned* err);
 void launch_csr_offdiag(cudaStream_t st, const ca_csr_dev& csr, const int* idx, long long nrows,
                         long long ncols, int sb, int ldr, double* G, const int* dmap,
-                        const float* Xd, int fd, bool split);
+                        const float* Xd, int fd, bool split, const int* roff);
+// Where each feature range of the split's sparse part starts in every row
+// (csr_rangeoff_bytes of int offsets, formed once per solve; roff = nullptr
+// in launch_csr_offdiag makes it search instead).
+size_t csr_rangeoff_bytes(long long nrows, long long ncols);
+void launch_csr_rangeoff(cudaStream_t st, const ca_csr_dev& csr, long long nrows, long long ncols,
+                         int* roff);
 // The fast a4 of the sparse dual (b <= 16) in two parts: launch_csr_prep
 // (needs neither w nor alpha: diagonal-block inverses into Ginv and the
 // cG-scaled FP32 pairs Rs of G's strict lower triangle; the diagonal from the
