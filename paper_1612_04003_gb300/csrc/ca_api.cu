@@ -1023,7 +1023,9 @@ int ca_bdcd_solve(ca_ctx* ctx, int xfmt, const void* XT, long long d, long long 
       const int sb = sk * b;
       const int* ik = idx + (size_t)s * k * b;
       double* Gt = Gbuf[k & 1];
-      // a2+a3: the Gram (row hash tables) and the projections
+      // a2+a3: the projections here (with the diagonal when s*b < 128); the
+      // rest of the Gram comes from the side stream (all of it, by the row
+      // hash tables, when s*b > 4096)
       const bool fk = fast_step(sb);
       prof_mark(ctx, PC_GRAM);
       if (fk) {

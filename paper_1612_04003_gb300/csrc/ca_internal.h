@@ -34,9 +34,9 @@ struct Profile {
 struct ca_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  // the sparse dual's second stream (the next step's off-diagonal Gram runs
-  // on it while the current step's solves run) and its events; made on
-  // first use
+  // the sparse dual's second stream (the next step's off-diagonal Gram, and
+  // for s*b >= 128 its diagonal-block inverses and Rs, run on it while the
+  // current step's solves run) and its events; made on first use
   cudaStream_t side = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   size_t scratch_max = 0;
