@@ -403,7 +403,9 @@ def sparse_small():
     return synth.sparse_dual(d=4000, n=600, density=0.01, seed=3)
 
 
-@pytest.mark.parametrize("b,s", [(8, 1), (8, 8), (8, 32), (5, 3)])
+# (s*b >= 128 runs the diagonal-block inverses on the second stream and the
+# chain alone on the library stream: b = 8, 13, 16 there)
+@pytest.mark.parametrize("b,s", [(8, 1), (8, 8), (8, 32), (5, 3), (16, 8), (13, 12), (16, 16)])
 def test_dual_csr(ctx, sparse_small, b, s):
     sp = sparse_small
     rp, col, val = _dev(sp.rowptr), _dev(sp.col), _dev(sp.val)
